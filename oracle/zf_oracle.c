@@ -1,0 +1,590 @@
+/*
+ * zf_oracle.c -- plain, slow CPU oracle for the compressed-column codecs.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the package smoke check and the
+ * benchmark's CPU-baseline leg may load this file's library.  It shares no
+ * code, header, table or constant with the GPU library: it re-implements the
+ * container format from its written description, and every codec from the
+ * paper's definitions:
+ *
+ *   Bit-packing / Frame of Reference   Section 2.1 ("Bit-packing and FOR")
+ *   Dictionary encoding                Section 2.1; Section 3.1, Fig. 6(a)
+ *   Delta encoding                     Section 2.1 ("Delta encoding")
+ *   Run-length encoding, presum        Section 2.1 ("RLE"); Section 3.2
+ *   LZ77 back-references               Section 2.1 ("LZ77-based algorithms")
+ *   Independent chunks                 Section 3.1 (Non-Parallel "file chunking")
+ *
+ * Decoders are the definitions written out: values are read bit by bit,
+ * delta adds each difference to the previous value, RLE expands each run at
+ * its presum, and LZ77 copies a back-reference byte by byte.
+ *
+ * Parity: every function here is pinned by the not-gpu tests (closed forms,
+ * brute force, hand-worked byte examples, library routines on special cases).
+ *
+ * Container format v1 (little-endian):
+ *   column  = 64-byte column header, n_chunks x 32-byte chunk directory, chunk blobs
+ *   chunk   = 64-byte chunk header, up to three sections, each 16-byte aligned,
+ *             zero padding, blob length a multiple of 16
+ * The layout constants below are typed in from that description.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- status codes (values of the library's zf_status) ---- */
+enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_ECORRUPT = 4 };
+/* ---- schemes and dtypes ---- */
+enum { ORC_RAW = 0, ORC_FOR_BP = 1, ORC_DICT_BP = 2, ORC_DELTA_BP = 3, ORC_RLE = 4, ORC_LZ77 = 5 };
+enum { ORC_I32 = 0, ORC_I64 = 1, ORC_BYTES = 2 };
+
+#define COL_MAGIC 0x4C4F435Au   /* "ZCOL" */
+#define CHK_MAGIC 0x4B48435Au   /* "ZCHK" */
+#define DELTA_BLOCK 1024u
+#define RLE_DIR_ROWS 1024u
+#define LZ_HASH_BITS 14
+#define LZ_MIN_MATCH 4u
+#define LZ_MAX_OFFSET 65535u
+
+/* ------------------------------------------------------------------------- */
+/* little-endian byte helpers                                                */
+/* ------------------------------------------------------------------------- */
+static void put_u16(uint8_t* p, uint32_t v) { p[0] = (uint8_t)v; p[1] = (uint8_t)(v >> 8); }
+static void put_u32(uint8_t* p, uint32_t v) { for (int i = 0; i < 4; i++) p[i] = (uint8_t)(v >> (8 * i)); }
+static void put_u64(uint8_t* p, uint64_t v) { for (int i = 0; i < 8; i++) p[i] = (uint8_t)(v >> (8 * i)); }
+static uint32_t get_u16(const uint8_t* p) { return (uint32_t)p[0] | ((uint32_t)p[1] << 8); }
+static uint32_t get_u32(const uint8_t* p) { uint32_t v = 0; for (int i = 0; i < 4; i++) v |= (uint32_t)p[i] << (8 * i); return v; }
+static uint64_t get_u64(const uint8_t* p) { uint64_t v = 0; for (int i = 0; i < 8; i++) v |= (uint64_t)p[i] << (8 * i); return v; }
+static uint64_t align16(uint64_t x) { return (x + 15) / 16 * 16; }
+
+/* number of bits needed for x: 0 for x == 0, else floor(log2 x) + 1 */
+uint32_t orc_bits(uint64_t x) {
+    uint32_t b = 0;
+    while (x) { b++; x >>= 1; }
+    return b;
+}
+
+static unsigned width_of(int dtype) { return dtype == ORC_I64 ? 64u : 32u; }
+static unsigned size_of(int dtype) { return dtype == ORC_I64 ? 8u : (dtype == ORC_I32 ? 4u : 1u); }
+static uint64_t mask_of(unsigned w) { return w >= 64 ? ~0ull : ((1ull << w) - 1); }
+
+/* value i of a typed array as a sign-extended 64-bit integer */
+static int64_t load_val(const void* data, int dtype, uint64_t i) {
+    if (dtype == ORC_I64) return ((const int64_t*)data)[i];
+    return (int64_t)((const int32_t*)data)[i];
+}
+static void store_val(void* data, int dtype, uint64_t i, uint64_t v) {
+    if (dtype == ORC_I64) ((int64_t*)data)[i] = (int64_t)v;
+    else ((int32_t*)data)[i] = (int32_t)(uint32_t)v;
+}
+/* reinterpret the low w bits of v as a signed w-bit integer */
+static int64_t sext(uint64_t v, unsigned w) {
+    if (w >= 64) return (int64_t)v;
+    v &= mask_of(w);
+    if (v >> (w - 1)) return (int64_t)(v | ~mask_of(w));
+    return (int64_t)v;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Bit-packing (Section 2.1): value i occupies stream bits [i*b, i*b+b),     */
+/* least significant bit first; stream bit k is bit (k mod 8) of byte k/8.   */
+/* ------------------------------------------------------------------------- */
+uint64_t orc_packed_bytes(uint64_t n, uint32_t b) { return (n * (uint64_t)b + 7) / 8; }
+
+/* writes exactly ceil(n*b/8) bytes; `out` must hold them and is overwritten */
+uint64_t orc_pack(const uint64_t* u, uint64_t n, uint32_t b, uint8_t* out) {
+    uint64_t nbytes = orc_packed_bytes(n, b);
+    memset(out, 0, nbytes);
+    for (uint64_t i = 0; i < n; i++)
+        for (uint32_t k = 0; k < b; k++)
+            if ((u[i] >> k) & 1ull) {
+                uint64_t bit = i * b + k;
+                out[bit / 8] |= (uint8_t)(1u << (bit % 8));
+            }
+    return nbytes;
+}
+
+uint64_t orc_unpack_one(const uint8_t* in, uint64_t i, uint32_t b) {
+    uint64_t v = 0;
+    for (uint32_t k = 0; k < b; k++) {
+        uint64_t bit = i * b + k;
+        if ((in[bit / 8] >> (bit % 8)) & 1u) v |= 1ull << k;
+    }
+    return v;
+}
+
+/* ------------------------------------------------------------------------- */
+/* chunk assembly                                                            */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    uint8_t* p;       /* chunk start */
+    uint64_t end;     /* bytes used so far (relative to chunk start) */
+} chunk_w;
+
+/* start section s at the next 16-byte boundary; returns its offset */
+static uint64_t sec_begin(chunk_w* w, int s, uint64_t len) {
+    uint64_t off = align16(w->end);
+    put_u32(w->p + 24 + 4 * s, (uint32_t)off);
+    put_u32(w->p + 36 + 4 * s, (uint32_t)len);
+    w->end = off + len;
+    return off;
+}
+
+static void chunk_header(uint8_t* p, int scheme, int dtype, uint32_t bw, uint32_t flags,
+                         uint32_t rows, uint32_t n_aux, uint64_t ref) {
+    memset(p, 0, 64);
+    put_u32(p + 0, CHK_MAGIC);
+    p[4] = (uint8_t)scheme;
+    p[5] = (uint8_t)dtype;
+    p[6] = (uint8_t)bw;
+    p[7] = (uint8_t)flags;
+    put_u32(p + 8, rows);
+    put_u32(p + 12, n_aux);
+    put_u64(p + 16, ref);
+}
+
+/* upper bound of one chunk's blob */
+static uint64_t chunk_bound(int scheme, int dtype, uint64_t rows) {
+    uint64_t sz = size_of(dtype);
+    uint64_t b = 64 + 3 * 16;
+    switch (scheme) {
+    case ORC_RAW: case ORC_FOR_BP: return b + rows * sz;
+    case ORC_DICT_BP: return b + rows * sz + rows * 2 + 16;
+    case ORC_DELTA_BP: return b + (rows / DELTA_BLOCK + 1) * (24 + 16) + rows * sz + 16;
+    case ORC_RLE: return b + rows * (sz + 4) + (rows / RLE_DIR_ROWS + 1) * 8;
+    case ORC_LZ77: return b + rows + rows / 8 + 64;
+    }
+    return 0;
+}
+
+/* ---- RAW ---- */
+static uint64_t enc_raw(uint8_t* p, int dtype, const void* x, uint32_t m) {
+    chunk_w w = {p, 64};
+    chunk_header(p, ORC_RAW, dtype, 0, 0, m, 0, 0);
+    uint64_t off = sec_begin(&w, 0, (uint64_t)m * size_of(dtype));
+    memcpy(p + off, x, (uint64_t)m * size_of(dtype));
+    return align16(w.end);
+}
+
+/* ---- FOR + bit-packing: reference = chunk minimum, b from max - min ---- */
+static uint64_t enc_for(uint8_t* p, int dtype, const void* x, uint32_t m) {
+    unsigned w_ = width_of(dtype);
+    int64_t mn = 0, mx = 0;
+    for (uint32_t i = 0; i < m; i++) {
+        int64_t v = load_val(x, dtype, i);
+        if (i == 0 || v < mn) mn = v;
+        if (i == 0 || v > mx) mx = v;
+    }
+    uint32_t b = orc_bits(((uint64_t)mx - (uint64_t)mn) & mask_of(w_));
+    uint64_t* u = (uint64_t*)malloc(sizeof(uint64_t) * (m ? m : 1));
+    for (uint32_t i = 0; i < m; i++) u[i] = ((uint64_t)load_val(x, dtype, i) - (uint64_t)mn) & mask_of(w_);
+    chunk_w w = {p, 64};
+    chunk_header(p, ORC_FOR_BP, dtype, b, 0, m, 0, (uint64_t)mn);
+    uint64_t off = sec_begin(&w, 0, orc_packed_bytes(m, b));
+    orc_pack(u, m, b, p + off);
+    free(u);
+    return align16(w.end);
+}
+
+/* ---- dictionary: sorted distinct values, code = rank, bit-packed ---- */
+static int cmp_i64(const void* a, const void* b) {
+    int64_t x = *(const int64_t*)a, y = *(const int64_t*)b;
+    return (x > y) - (x < y);
+}
+static uint64_t enc_dict(uint8_t* p, int dtype, const void* x, uint32_t m, int* err) {
+    int64_t* s = (int64_t*)malloc(sizeof(int64_t) * (m ? m : 1));
+    for (uint32_t i = 0; i < m; i++) s[i] = load_val(x, dtype, i);
+    qsort(s, m, sizeof(int64_t), cmp_i64);
+    uint32_t nd = 0;
+    for (uint32_t i = 0; i < m; i++)
+        if (i == 0 || s[i] != s[nd - 1]) s[nd++] = s[i];
+    if (nd > 65536) { free(s); *err = ORC_EINVAL; return 0; }
+    uint32_t b = nd > 0 ? orc_bits(nd - 1) : 0;
+    uint64_t* code = (uint64_t*)malloc(sizeof(uint64_t) * (m ? m : 1));
+    for (uint32_t i = 0; i < m; i++) {
+        int64_t v = load_val(x, dtype, i);
+        uint32_t lo = 0, hi = nd;          /* lower bound of v in the dictionary */
+        while (lo < hi) { uint32_t mid = (lo + hi) / 2; if (s[mid] < v) lo = mid + 1; else hi = mid; }
+        code[i] = lo;
+    }
+    chunk_w w = {p, 64};
+    chunk_header(p, ORC_DICT_BP, dtype, b, 0, m, nd, 0);
+    uint64_t doff = sec_begin(&w, 0, (uint64_t)nd * size_of(dtype));
+    for (uint32_t k = 0; k < nd; k++) store_val(p + doff, dtype, k, (uint64_t)s[k]);
+    uint64_t coff = sec_begin(&w, 1, orc_packed_bytes(m, b));
+    orc_pack(code, m, b, p + coff);
+    free(s); free(code);
+    return align16(w.end);
+}
+
+/* ---- delta: per 1024-row block, base + differences (+ FOR on the differences) ---- */
+static uint64_t enc_delta(uint8_t* p, int dtype, const void* x, uint32_t m) {
+    unsigned wd = width_of(dtype);
+    uint64_t msk = mask_of(wd);
+    uint32_t nb = (m + DELTA_BLOCK - 1) / DELTA_BLOCK;
+    chunk_w w = {p, 64};
+    chunk_header(p, ORC_DELTA_BP, dtype, 0, 0, m, nb, 0);
+    uint64_t toff = sec_begin(&w, 0, (uint64_t)nb * 24);
+    /* first pass: widths, to size the payload section */
+    uint64_t* u = (uint64_t*)malloc(sizeof(uint64_t) * DELTA_BLOCK);
+    uint64_t payload_total = 0;
+    for (int pass = 0; pass < 2; pass++) {
+        uint64_t poff = 0, sec1 = 0;
+        if (pass == 1) sec1 = sec_begin(&w, 1, payload_total);
+        for (uint32_t k = 0; k < nb; k++) {
+            uint32_t r0 = k * DELTA_BLOCK;
+            uint32_t mk = m - r0 < DELTA_BLOCK ? m - r0 : DELTA_BLOCK;
+            int64_t base = load_val(x, dtype, r0);
+            int64_t min_d = 0;
+            for (uint32_t j = 1; j < mk; j++) {
+                int64_t d = sext((uint64_t)load_val(x, dtype, r0 + j) - (uint64_t)load_val(x, dtype, r0 + j - 1), wd);
+                if (j == 1 || d < min_d) min_d = d;
+            }
+            uint64_t umax = 0;
+            u[0] = 0;
+            for (uint32_t j = 1; j < mk; j++) {
+                int64_t d = sext((uint64_t)load_val(x, dtype, r0 + j) - (uint64_t)load_val(x, dtype, r0 + j - 1), wd);
+                u[j] = ((uint64_t)d - (uint64_t)min_d) & msk;
+                if (u[j] > umax) umax = u[j];
+            }
+            uint32_t b = orc_bits(umax);
+            uint64_t len = align16(orc_packed_bytes(mk, b));
+            if (pass == 1) {
+                uint8_t* e = p + toff + 24ull * k;
+                put_u64(e + 0, (uint64_t)base);
+                put_u64(e + 8, (uint64_t)min_d);
+                put_u32(e + 16, (uint32_t)poff);
+                e[20] = (uint8_t)b; e[21] = e[22] = e[23] = 0;
+                memset(p + sec1 + poff, 0, len);
+                orc_pack(u, mk, b, p + sec1 + poff);
+            }
+            poff += len;
+        }
+        payload_total = poff;
+    }
+    free(u);
+    return align16(w.end);
+}
+
+/* ---- RLE: maximal runs (value, count) + a row directory every 1024 rows ---- */
+static uint64_t enc_rle(uint8_t* p, int dtype, const void* x, uint32_t m) {
+    uint32_t R = 0;
+    for (uint32_t i = 0; i < m; i++)
+        if (i == 0 || load_val(x, dtype, i) != load_val(x, dtype, i - 1)) R++;
+    uint32_t ntiles = (m + RLE_DIR_ROWS - 1) / RLE_DIR_ROWS;
+    chunk_w w = {p, 64};
+    chunk_header(p, ORC_RLE, dtype, 0, 0, m, R, 0);
+    uint64_t voff = sec_begin(&w, 0, (uint64_t)R * size_of(dtype));
+    uint64_t loff = sec_begin(&w, 1, (uint64_t)R * 4);
+    uint64_t doff = sec_begin(&w, 2, (uint64_t)ntiles * 8);
+    uint32_t r = 0, run_start = 0;
+    for (uint32_t i = 0; i < m; i++) {
+        if (i > 0 && load_val(x, dtype, i) != load_val(x, dtype, i - 1)) {
+            put_u32(p + loff + 4ull * r, i - run_start);
+            r++;
+            run_start = i;
+        }
+        if (i == run_start) store_val(p + voff, dtype, r, (uint64_t)load_val(x, dtype, i));
+        if (i % RLE_DIR_ROWS == 0) {
+            put_u32(p + doff + 8ull * (i / RLE_DIR_ROWS), r);
+            put_u32(p + doff + 8ull * (i / RLE_DIR_ROWS) + 4, i - run_start);
+        }
+    }
+    if (m > 0) put_u32(p + loff + 4ull * r, m - run_start);
+    return align16(w.end);
+}
+
+/* ---- LZ77: greedy, 4-byte hash of the last position, 64 KiB window ---- */
+static uint32_t leb128_put(uint8_t* p, uint32_t v) {
+    uint32_t n = 0;
+    do { uint8_t c = v & 0x7F; v >>= 7; p[n++] = c | (v ? 0x80 : 0); } while (v);
+    return n;
+}
+static uint32_t lz_hash(const uint8_t* s) {
+    uint32_t v = (uint32_t)s[0] | ((uint32_t)s[1] << 8) | ((uint32_t)s[2] << 16) | ((uint32_t)s[3] << 24);
+    return (v * 2654435761u) >> (32 - LZ_HASH_BITS);
+}
+static uint64_t enc_lz(uint8_t* p, const uint8_t* src, uint32_t m) {
+    uint8_t* tok = (uint8_t*)malloc(3ull * m + 16);
+    uint8_t* lit = (uint8_t*)malloc((uint64_t)m + 16);
+    int32_t* table = (int32_t*)malloc(sizeof(int32_t) << LZ_HASH_BITS);
+    for (uint32_t i = 0; i < (1u << LZ_HASH_BITS); i++) table[i] = -1;
+    uint32_t nt = 0, ntok = 0, nlit = 0, lit_start = 0, pos = 0;
+    while (pos + LZ_MIN_MATCH <= m) {
+        uint32_t h = lz_hash(src + pos);
+        int32_t cand = table[h];
+        table[h] = (int32_t)pos;
+        if (cand >= 0 && pos - (uint32_t)cand <= LZ_MAX_OFFSET &&
+            memcmp(src + cand, src + pos, LZ_MIN_MATCH) == 0) {
+            uint32_t len = LZ_MIN_MATCH;
+            while (pos + len < m && src[cand + len] == src[pos + len]) len++;
+            uint32_t ll = pos - lit_start;
+            nt += leb128_put(tok + nt, ll);
+            memcpy(lit + nlit, src + lit_start, ll);
+            nlit += ll;
+            put_u16(tok + nt, pos - (uint32_t)cand);
+            nt += 2;
+            nt += leb128_put(tok + nt, len - LZ_MIN_MATCH);
+            ntok++;
+            pos += len;
+            lit_start = pos;
+        } else {
+            pos++;
+        }
+    }
+    /* final token: the remaining literals, no match */
+    uint32_t ll = m - lit_start;
+    nt += leb128_put(tok + nt, ll);
+    memcpy(lit + nlit, src + lit_start, ll);
+    nlit += ll;
+    ntok++;
+    chunk_w w = {p, 64};
+    if ((uint64_t)nt + nlit >= m) {          /* does not compress: store the block raw */
+        chunk_header(p, ORC_LZ77, ORC_BYTES, 0, 1, m, 0, 0);
+        uint64_t off = sec_begin(&w, 0, m);
+        memcpy(p + off, src, m);
+    } else {
+        chunk_header(p, ORC_LZ77, ORC_BYTES, 0, 0, m, ntok, 0);
+        uint64_t toff = sec_begin(&w, 0, nt);
+        memcpy(p + toff, tok, nt);
+        uint64_t loff = sec_begin(&w, 1, nlit);
+        memcpy(p + loff, lit, nlit);
+    }
+    free(tok); free(lit); free(table);
+    return align16(w.end);
+}
+
+/* ------------------------------------------------------------------------- */
+/* column encoder                                                            */
+/* ------------------------------------------------------------------------- */
+uint64_t orc_encode_bound(int scheme, int dtype, uint64_t n, uint32_t chunk_rows) {
+    if (chunk_rows == 0) return 0;
+    uint64_t nch = (n + chunk_rows - 1) / chunk_rows;
+    return 64 + 32 * nch + nch * chunk_bound(scheme, dtype, chunk_rows) + 64;
+}
+
+static int scheme_ok(int scheme, int dtype) {
+    if (dtype == ORC_BYTES) return scheme == ORC_RAW || scheme == ORC_LZ77;
+    if (dtype != ORC_I32 && dtype != ORC_I64) return 0;
+    return scheme >= ORC_RAW && scheme <= ORC_RLE;
+}
+
+/* Encode n values (BYTES: n bytes) in chunks of chunk_rows rows.
+ * `out` must hold orc_encode_bound(...) bytes.  *out_len receives the size. */
+int orc_encode(int scheme, int dtype, const void* data, uint64_t n, uint32_t chunk_rows,
+               uint8_t* out, uint64_t cap, uint64_t* out_len) {
+    if (!scheme_ok(scheme, dtype) || chunk_rows == 0) return ORC_EINVAL;
+    if (cap < orc_encode_bound(scheme, dtype, n, chunk_rows)) return ORC_EINVAL;
+    uint64_t nch = (n + chunk_rows - 1) / chunk_rows;
+    uint64_t sz = size_of(dtype);
+    memset(out, 0, cap);               /* every padding byte is zero */
+    uint64_t pos = 64 + 32 * nch;
+    for (uint64_t c = 0; c < nch; c++) {
+        uint64_t r0 = c * chunk_rows;
+        uint32_t m = (uint32_t)(n - r0 < chunk_rows ? n - r0 : chunk_rows);
+        const uint8_t* x = (const uint8_t*)data + r0 * sz;
+        uint8_t* p = out + pos;
+        int err = ORC_OK;
+        uint64_t len = 0;
+        switch (scheme) {
+        case ORC_RAW: len = enc_raw(p, dtype, x, m); break;
+        case ORC_FOR_BP: len = enc_for(p, dtype, x, m); break;
+        case ORC_DICT_BP: len = enc_dict(p, dtype, x, m, &err); break;
+        case ORC_DELTA_BP: len = enc_delta(p, dtype, x, m); break;
+        case ORC_RLE: len = enc_rle(p, dtype, x, m); break;
+        case ORC_LZ77: len = enc_lz(p, x, m); break;
+        }
+        if (err) return err;
+        uint8_t* d = out + 64 + 32 * c;
+        put_u64(d + 0, pos);
+        put_u64(d + 8, len);
+        put_u64(d + 16, r0);
+        put_u32(d + 24, m);
+        put_u32(d + 28, 0);
+        pos += len;
+    }
+    put_u32(out + 0, COL_MAGIC);
+    put_u16(out + 4, 1);
+    out[6] = (uint8_t)scheme;
+    out[7] = (uint8_t)dtype;
+    put_u32(out + 8, (uint32_t)nch);
+    put_u32(out + 12, chunk_rows);
+    put_u64(out + 16, n);
+    put_u64(out + 24, n * sz);
+    put_u64(out + 32, pos);
+    *out_len = pos;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* decoders                                                                  */
+/* ------------------------------------------------------------------------- */
+/* a section lies inside the blob */
+static int sec_ok(const uint8_t* c, uint64_t len, int s) {
+    uint64_t off = get_u32(c + 24 + 4 * s), l = get_u32(c + 36 + 4 * s);
+    return off >= 64 && off % 16 == 0 && off + l <= len;
+}
+
+/* Decode one chunk blob into `out` (rows values).  Returns ORC_ECORRUPT for a
+ * malformed blob. */
+int orc_decode_chunk(const uint8_t* c, uint64_t len, void* out, uint64_t out_cap) {
+    if (len < 64 || get_u32(c) != CHK_MAGIC) return ORC_ECORRUPT;
+    int scheme = c[4], dtype = c[5];
+    uint32_t b = c[6], flags = c[7], m = get_u32(c + 8), n_aux = get_u32(c + 12);
+    uint64_t ref = get_u64(c + 16);
+    if (!scheme_ok(scheme, dtype)) return ORC_ECORRUPT;
+    unsigned wd = width_of(dtype);
+    uint64_t msk = mask_of(wd), sz = size_of(dtype);
+    if ((uint64_t)m * sz > out_cap) return ORC_EINVAL;
+    const uint8_t* s0 = c + get_u32(c + 24);
+    const uint8_t* s1 = c + get_u32(c + 28);
+    const uint8_t* s2 = c + get_u32(c + 32);
+    uint32_t l0 = get_u32(c + 36), l1 = get_u32(c + 40), l2 = get_u32(c + 44);
+    switch (scheme) {
+    case ORC_RAW:
+        if (!sec_ok(c, len, 0) || l0 != (uint64_t)m * sz) return ORC_ECORRUPT;
+        memcpy(out, s0, (uint64_t)m * sz);
+        return ORC_OK;
+    case ORC_FOR_BP:
+        /* x_i = reference + unpacked value i */
+        if (!sec_ok(c, len, 0) || b > wd || l0 != orc_packed_bytes(m, b)) return ORC_ECORRUPT;
+        for (uint32_t i = 0; i < m; i++) store_val(out, dtype, i, (ref + orc_unpack_one(s0, i, b)) & msk);
+        return ORC_OK;
+    case ORC_DICT_BP:
+        /* x_i = dictionary[code_i] */
+        if (!sec_ok(c, len, 0) || !sec_ok(c, len, 1) || b > 16 || l0 != (uint64_t)n_aux * sz ||
+            l1 != orc_packed_bytes(m, b)) return ORC_ECORRUPT;
+        for (uint32_t i = 0; i < m; i++) {
+            uint64_t code = orc_unpack_one(s1, i, b);
+            if (code >= n_aux) return ORC_ECORRUPT;
+            store_val(out, dtype, i, (uint64_t)load_val(s0, dtype, code));
+        }
+        return ORC_OK;
+    case ORC_DELTA_BP: {
+        /* x_0 = base; x_j = x_{j-1} + (min_d + u_j) */
+        uint32_t nb = n_aux;
+        if (!sec_ok(c, len, 0) || !sec_ok(c, len, 1) || nb != (m + DELTA_BLOCK - 1) / DELTA_BLOCK ||
+            l0 != 24ull * nb) return ORC_ECORRUPT;
+        for (uint32_t k = 0; k < nb; k++) {
+            const uint8_t* e = s0 + 24ull * k;
+            uint64_t base = get_u64(e), min_d = get_u64(e + 8);
+            uint32_t poff = get_u32(e + 16), bk = e[20];
+            uint32_t r0 = k * DELTA_BLOCK;
+            uint32_t mk = m - r0 < DELTA_BLOCK ? m - r0 : DELTA_BLOCK;
+            if (bk > wd || (uint64_t)poff + orc_packed_bytes(mk, bk) > l1) return ORC_ECORRUPT;
+            uint64_t prev = base & msk;
+            store_val(out, dtype, r0, prev);
+            for (uint32_t j = 1; j < mk; j++) {
+                prev = (prev + min_d + orc_unpack_one(s1 + poff, j, bk)) & msk;
+                store_val(out, dtype, r0 + j, prev);
+            }
+        }
+        return ORC_OK;
+    }
+    case ORC_RLE: {
+        /* presum = exclusive prefix sum of counts; run r fills [presum_r, presum_r + count_r) */
+        uint32_t R = n_aux;
+        if (!sec_ok(c, len, 0) || !sec_ok(c, len, 1) || !sec_ok(c, len, 2) ||
+            l0 != (uint64_t)R * sz || l1 != 4ull * R) return ORC_ECORRUPT;
+        uint64_t presum = 0;
+        for (uint32_t r = 0; r < R; r++) {
+            uint32_t cnt = get_u32(s1 + 4ull * r);
+            if (cnt == 0 || presum + cnt > m) return ORC_ECORRUPT;
+            uint64_t v = (uint64_t)load_val(s0, dtype, r);
+            for (uint32_t k = 0; k < cnt; k++) store_val(out, dtype, presum + k, v);
+            presum += cnt;
+        }
+        if (presum != m) return ORC_ECORRUPT;
+        (void)s2; (void)l2;
+        return ORC_OK;
+    }
+    case ORC_LZ77: {
+        uint8_t* o = (uint8_t*)out;
+        if (flags & 1) {
+            if (!sec_ok(c, len, 0) || l0 != m) return ORC_ECORRUPT;
+            memcpy(o, s0, m);
+            return ORC_OK;
+        }
+        if (!sec_ok(c, len, 0) || !sec_ok(c, len, 1)) return ORC_ECORRUPT;
+        uint32_t tp = 0, lp = 0, op = 0;
+        for (uint32_t t = 0; t < n_aux; t++) {
+            uint32_t ll = 0, sh = 0;
+            for (;;) {
+                if (tp >= l0 || sh > 28) return ORC_ECORRUPT;
+                uint8_t byte = s0[tp++];
+                ll |= (uint32_t)(byte & 0x7F) << sh;
+                sh += 7;
+                if (!(byte & 0x80)) break;
+            }
+            if ((uint64_t)lp + ll > l1 || (uint64_t)op + ll > m) return ORC_ECORRUPT;
+            for (uint32_t k = 0; k < ll; k++) o[op++] = s1[lp++];
+            if (t + 1 == n_aux) break;
+            if (tp + 2 > l0) return ORC_ECORRUPT;
+            uint32_t off = get_u16(s0 + tp);
+            tp += 2;
+            uint32_t ml = 0;
+            sh = 0;
+            for (;;) {
+                if (tp >= l0 || sh > 28) return ORC_ECORRUPT;
+                uint8_t byte = s0[tp++];
+                ml |= (uint32_t)(byte & 0x7F) << sh;
+                sh += 7;
+                if (!(byte & 0x80)) break;
+            }
+            ml += LZ_MIN_MATCH;
+            if (off == 0 || off > op || (uint64_t)op + ml > m) return ORC_ECORRUPT;
+            /* back-reference: byte by byte, so a source that overlaps the output repeats */
+            for (uint32_t k = 0; k < ml; k++) { o[op] = o[op - off]; op++; }
+        }
+        if (op != m || tp != l0 || lp != l1) return ORC_ECORRUPT;
+        return ORC_OK;
+    }
+    }
+    return ORC_ECORRUPT;
+}
+
+/* header fields of a serialized column */
+int orc_column_info(const uint8_t* buf, uint64_t len, uint32_t* scheme, uint32_t* dtype,
+                    uint64_t* n_rows, uint32_t* n_chunks, uint64_t* total) {
+    if (len < 64 || get_u32(buf) != COL_MAGIC || get_u16(buf + 4) != 1) return ORC_ECORRUPT;
+    *scheme = buf[6];
+    *dtype = buf[7];
+    *n_chunks = get_u32(buf + 8);
+    *n_rows = get_u64(buf + 16);
+    *total = get_u64(buf + 32);
+    return ORC_OK;
+}
+
+/* Decode a serialized column into `out`. */
+int orc_decode(const uint8_t* buf, uint64_t len, void* out, uint64_t out_cap) {
+    uint32_t scheme, dtype, nch;
+    uint64_t n, total;
+    int st = orc_column_info(buf, len, &scheme, &dtype, &n, &nch, &total);
+    if (st) return st;
+    uint64_t sz = size_of((int)dtype);
+    if (total > len || 64 + 32ull * nch > total) return ORC_ECORRUPT;
+    if (n * sz > out_cap) return ORC_EINVAL;
+    uint64_t rows_seen = 0;
+    for (uint32_t c = 0; c < nch; c++) {
+        const uint8_t* d = buf + 64 + 32ull * c;
+        uint64_t off = get_u64(d), l = get_u64(d + 8), r0 = get_u64(d + 16);
+        uint32_t m = get_u32(d + 24);
+        if (off + l > total || r0 != rows_seen || r0 + m > n) return ORC_ECORRUPT;
+        if (get_u32(buf + off + 8) != m) return ORC_ECORRUPT;
+        st = orc_decode_chunk(buf + off, l, (uint8_t*)out + r0 * sz, (n - r0) * sz);
+        if (st) return st;
+        rows_seen += m;
+    }
+    return rows_seen == n ? ORC_OK : ORC_ECORRUPT;
+}
+
+/* Byte offset and length of chunk c of a serialized column. */
+int orc_chunk_span(const uint8_t* buf, uint64_t len, uint32_t c, uint64_t* off, uint64_t* l,
+                   uint64_t* row0, uint32_t* rows) {
+    if (len < 64 || get_u32(buf) != COL_MAGIC || c >= get_u32(buf + 8)) return ORC_EINVAL;
+    const uint8_t* d = buf + 64 + 32ull * c;
+    *off = get_u64(d);
+    *l = get_u64(d + 8);
+    *row0 = get_u64(d + 16);
+    *rows = get_u32(d + 24);
+    return ORC_OK;
+}

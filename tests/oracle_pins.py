@@ -1,0 +1,377 @@
+"""Pins of the CPU oracle: facts fixed by the paper's definitions and by
+mathematics, not by the oracle itself.
+
+Each ``pin_*`` function takes a loaded oracle and raises AssertionError when
+the oracle breaks the fact.  ``test_oracle_pins.py`` runs them on the oracle;
+``test_oracle_mutants.py`` runs them on copies of the oracle with a planted
+mistake and checks that every mistake is caught.
+"""
+from __future__ import annotations
+
+import os
+import struct
+
+import numpy as np
+
+import oracle as O
+import zf_workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+I32_MIN, I32_MAX = -(1 << 31), (1 << 31) - 1
+I64_MIN, I64_MAX = -(1 << 63), (1 << 63) - 1
+
+
+# ---------------------------------------------------------------------------
+# a reader of the chunk layout, typed in from the format description
+# ---------------------------------------------------------------------------
+def parse_chunk(blob: bytes) -> dict:
+    magic, scheme, dtype, bw, flags, rows, n_aux, ref = struct.unpack_from("<IBBBBIIq", blob, 0)
+    offs = struct.unpack_from("<3I", blob, 24)
+    lens = struct.unpack_from("<3I", blob, 36)
+    assert magic == 0x4B48435A
+    secs = [bytes(blob[o:o + l]) if (o or l) else b"" for o, l in zip(offs, lens)]
+    return dict(scheme=scheme, dtype=dtype, bw=bw, flags=flags, rows=rows, n_aux=n_aux, ref=ref,
+                offs=offs, lens=lens, secs=secs)
+
+
+def chunks_of(orc, buf: bytes):
+    info = orc.column_info(buf)
+    out = []
+    for c in range(info["n_chunks"]):
+        off, ln, r0, rows = orc.chunk_span(buf, c)
+        out.append((off, ln, r0, rows, parse_chunk(buf[off:off + ln])))
+    return out
+
+
+def bigint_pack(vals, b: int) -> bytes:
+    """Bit-packing as arithmetic: the stream is sum(u_i * 2**(i*b)), little-endian."""
+    acc = 0
+    for i, v in enumerate(vals):
+        acc |= int(v) << (i * b)
+    n = (len(vals) * b + 7) // 8
+    return acc.to_bytes(n, "little") if n else b""
+
+
+# ---------------------------------------------------------------------------
+# pins
+# ---------------------------------------------------------------------------
+def pin_bits(orc):
+    rng = np.random.default_rng(5)
+    xs = [0, 1, 2, 3, 4095, 4096, (1 << 32) - 1, 1 << 32, (1 << 63), (1 << 64) - 1]
+    xs += [int(v) for v in rng.integers(0, 1 << 63, 200, dtype=np.int64)]
+    for x in xs:
+        assert orc.bits(x) == int(x).bit_length(), x
+
+
+def pin_pack_hand(orc):
+    for line in open(os.path.join(GOLDEN, "bitpack_hand.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        kv = dict(t.split("=", 1) for t in line.split())
+        vals = [int(v) for v in kv["values"].split(",")]
+        b = int(kv["b"])
+        assert orc.pack(vals, b).hex() == kv["bytes"], line
+        assert list(orc.unpack(bytes.fromhex(kv["bytes"]), len(vals), b)) == vals, line
+
+
+def pin_pack_bruteforce(orc):
+    rng = np.random.default_rng(7)
+    for b in range(0, 65):
+        for n in (0, 1, 2, 3, 7, 8, 9, 31, 33, 64, 70):
+            hi = (1 << b) - 1
+            vals = [int(v) & hi for v in rng.integers(0, 1 << 63, n, dtype=np.int64) * 2 + rng.integers(0, 2, n)]
+            if n >= 2:
+                vals[0], vals[-1] = hi, 0
+            got = orc.pack(vals, b)
+            assert len(got) == (n * b + 7) // 8, (n, b)
+            assert got == bigint_pack(vals, b), (n, b)
+            if n:
+                assert [int(v) for v in orc.unpack(got, n, b)] == vals, (n, b)
+
+
+def _hand_lines():
+    for line in open(os.path.join(GOLDEN, "codecs_hand.txt")):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            lhs, rhs = line.split("|")
+            scheme, dt, data = lhs.split()
+            exp = dict(t.split("=", 1) for t in rhs.split())
+            yield scheme, dt, data, exp
+
+
+def pin_codecs_hand(orc):
+    for scheme, dt, data, exp in _hand_lines():
+        if dt == "bytes":
+            x = np.frombuffer(data.encode(), np.uint8).copy()
+        else:
+            x = np.array([int(v) for v in data.split(",")], np.int32 if dt == "i32" else np.int64)
+        buf = orc.encode(x, O.SCHEMES[scheme], 1 << 20)
+        (off, ln, r0, rows, ch), = chunks_of(orc, buf)
+        assert ch["scheme"] == O.SCHEMES[scheme] and ch["rows"] == len(x)
+        for k, v in exp.items():
+            if k.startswith("sec"):
+                assert ch["secs"][int(k[3])].hex() == v, (scheme, k, ch["secs"][int(k[3])].hex(), v)
+            else:
+                assert ch[k] == int(v), (scheme, k, ch[k], v)
+        assert np.array_equal(orc.decode(buf), x)
+
+
+def pin_for_closed_form(orc):
+    # 16 chunks of 65,536 values uniform on [0, 4096): 12-bit packing, 98,304 bytes per chunk.
+    x = W.uniform_int(1, 0, 0, 1 << 20, 0, 4096).astype(np.int32)
+    buf = orc.encode(x, O.FOR_BP, 65536)
+    chs = chunks_of(orc, buf)
+    assert len(chs) == 16
+    total = 0
+    for off, ln, r0, rows, ch in chs:
+        seg = x[r0:r0 + rows]
+        assert ch["bw"] == int(int(seg.max()) - int(seg.min())).bit_length() == 12
+        assert ch["ref"] == int(seg.min())
+        assert ch["lens"][0] == 98304
+        total += ch["lens"][0]
+    assert total == 1572864
+    assert np.array_equal(orc.decode(buf), x)
+    # constant chunk: b = 0, empty payload, every value is the reference
+    c = np.full(1000, -77, np.int32)
+    (_, _, _, _, ch), = chunks_of(orc, orc.encode(c, O.FOR_BP, 4096))
+    assert ch["bw"] == 0 and ch["lens"][0] == 0 and ch["ref"] == -77
+    assert np.array_equal(orc.decode(orc.encode(c, O.FOR_BP, 4096)), c)
+    # extremes: the full range needs the full width
+    for dt, lo, hi, w in ((np.int32, I32_MIN, I32_MAX, 32), (np.int64, I64_MIN, I64_MAX, 64)):
+        e = np.array([hi, lo, 0, -1, 1, hi, lo], dt)
+        buf = orc.encode(e, O.FOR_BP, 5)
+        assert chunks_of(orc, buf)[0][4]["bw"] == w
+        assert np.array_equal(orc.decode(buf), e)
+    # random widths: b equals the bit length of max - min
+    rng = np.random.default_rng(3)
+    for w in (1, 5, 17, 31, 33, 47, 62):
+        v = rng.integers(-(1 << 62), (1 << 62) - (1 << w), 1).item()
+        e = (v + rng.integers(0, 1 << w, 777, dtype=np.int64)).astype(np.int64)
+        buf = orc.encode(e, O.FOR_BP, 256)
+        for off, ln, r0, rows, ch in chunks_of(orc, buf):
+            seg = e[r0:r0 + rows]
+            assert ch["bw"] == int(int(seg.max()) - int(seg.min())).bit_length()
+            assert ch["lens"][0] == (rows * ch["bw"] + 7) // 8
+        assert np.array_equal(orc.decode(buf), e)
+
+
+def pin_dict(orc):
+    x = W.dict_codes(1, 7, 0, 200000)
+    buf = orc.encode(x, O.DICT_BP, 65536)
+    for off, ln, r0, rows, ch in chunks_of(orc, buf):
+        seg = x[r0:r0 + rows]
+        uniq = np.unique(seg)
+        assert ch["n_aux"] == len(uniq)
+        assert np.array_equal(np.frombuffer(ch["secs"][0], np.int32), uniq)
+        assert ch["bw"] == int(len(uniq) - 1).bit_length()
+    assert chunks_of(orc, buf)[0][4]["bw"] == 5  # 25 distinct values
+    assert np.array_equal(orc.decode(buf), x)
+    for dt in (np.int32, np.int64):
+        one = np.full(100, 5, dt)
+        b1 = orc.encode(one, O.DICT_BP, 64)
+        assert chunks_of(orc, b1)[0][4]["bw"] == 0
+        assert np.array_equal(orc.decode(b1), one)
+        e = np.array([I64_MAX, I64_MIN, 0, I64_MAX] if dt is np.int64 else [I32_MAX, I32_MIN, 0, I32_MAX], dt)
+        assert np.array_equal(orc.decode(orc.encode(e, O.DICT_BP, 3)), e)
+    big = np.arange(70000, dtype=np.int32)
+    try:
+        orc.encode(big, O.DICT_BP, 70000)
+    except O.OracleError as err:
+        assert err.code == O.EINVAL
+    else:
+        raise AssertionError("a dictionary above 65,536 entries was accepted")
+
+
+def pin_delta(orc):
+    # arithmetic progression: every difference equals the stride, so b = 0 (DeltaStride, Section 5.3)
+    ap = (5 + 7 * np.arange(5000, dtype=np.int64))
+    buf = orc.encode(ap, O.DELTA_BP, 1 << 20)
+    ch = chunks_of(orc, buf)[0][4]
+    assert ch["n_aux"] == 5
+    for k in range(5):
+        base, min_d, poff, bk = struct.unpack_from("<qqIB", ch["secs"][0], 24 * k)
+        assert base == ap[k * 1024] and min_d == 7 and bk == 0
+    assert ch["lens"][1] == 0
+    assert np.array_equal(orc.decode(buf), ap)
+    # sorted keys: round trip; the last value is the base plus the sum of the differences
+    keys = W.sorted_keys(2, 300000)
+    buf = orc.encode(keys, O.DELTA_BP, 65536)
+    dec = orc.decode(buf)
+    assert np.array_equal(dec, keys)
+    for off, ln, r0, rows, ch in chunks_of(orc, buf):
+        for k in range(ch["n_aux"]):
+            base, min_d, poff, bk = struct.unpack_from("<qqIB", ch["secs"][0], 24 * k)
+            seg = keys[r0 + 1024 * k: r0 + min(rows, 1024 * (k + 1))]
+            assert base == seg[0]
+            assert base + int(np.diff(seg).sum()) == seg[-1]
+            if len(seg) > 1:
+                d = np.diff(seg)
+                assert min_d == d.min() and bk == int(int(d.max()) - int(d.min())).bit_length()
+    # wrapping differences at the type's extremes
+    for dt, lo, hi in ((np.int32, I32_MIN, I32_MAX), (np.int64, I64_MIN, I64_MAX)):
+        e = np.array([hi, lo, 0, -1, hi, hi, lo, lo, 1], dt)
+        assert np.array_equal(orc.decode(orc.encode(e, O.DELTA_BP, 4)), e)
+    # every int32 array of length <= 3 over a small value set
+    vals = [I32_MIN, -1, 0, 1, 2, I32_MAX]
+    for n in range(1, 4):
+        for idx in np.ndindex(*(len(vals),) * n):
+            e = np.array([vals[i] for i in idx], np.int32)
+            assert np.array_equal(orc.decode(orc.encode(e, O.DELTA_BP, 2)), e), e
+
+
+def _check_rle(orc, x, chunk_rows):
+    buf = orc.encode(x, O.RLE, chunk_rows)
+    total_runs = 0
+    for off, ln, r0, rows, ch in chunks_of(orc, buf):
+        seg = x[r0:r0 + rows]
+        vals = np.frombuffer(ch["secs"][0], seg.dtype)
+        lens = np.frombuffer(ch["secs"][1], np.uint32)
+        assert ch["n_aux"] == len(vals) == len(lens) == np.count_nonzero(np.diff(seg)) + 1
+        assert int(lens.sum()) == rows and lens.min() >= 1
+        assert np.array_equal(np.repeat(vals, lens), seg)
+        starts = np.concatenate([[0], np.cumsum(lens)[:-1]])
+        d = np.frombuffer(ch["secs"][2], np.uint32).reshape(-1, 2)
+        assert len(d) == (rows + 1023) // 1024
+        for t, (fr, skip) in enumerate(d):
+            assert starts[fr] + skip == 1024 * t and skip < lens[fr]
+        total_runs += len(vals)
+    assert np.array_equal(orc.decode(buf), x)
+    return buf, total_runs
+
+
+def pin_rle(orc):
+    # Section 5.2.2 distributions: even-X, random[L,R], outlier, mixed
+    for kind, a, b in (("even", 2, 0), ("even", 8, 0), ("random", 1, 16), ("outlier", 64, 1024),
+                       ("mixed", 4, 32), ("even", 1, 0), ("even", 5000, 0)):
+        x = W.rle_distribution(3, kind, 50000, a, b)
+        _check_rle(orc, x, 16384)
+    # even-8: the count array is 4 bytes per 8 rows = 12.5% of the plain int32 bytes
+    x = W.rle_distribution(3, "even", 1 << 16, 8)
+    buf, runs = _check_rle(orc, x, 1 << 16)
+    ch = chunks_of(orc, buf)[0][4]
+    assert ch["lens"][1] * 8 == x.nbytes  # 12.5 %
+    # runs are split at chunk boundaries
+    y = np.full(3000, 9, np.int64)
+    buf, runs = _check_rle(orc, y, 1000)
+    assert runs == 3
+    _check_rle(orc, W.dates_rle(4, 100000), 32768)
+
+
+def pin_lz(orc):
+    for text in (b"", b"a", b"abc", b"abcd", b"aaaaaaaaaaaaaaaaaaaaaaaaaaaaaaaaaaaaaaaaaaaaaa",
+                 b"abcabcabcabc" * 50, bytes(range(256)) * 10):
+        x = np.frombuffer(text, np.uint8).copy()
+        assert np.array_equal(orc.decode(orc.encode(x, O.LZ77, 65536)), x), text[:20]
+    # random bytes do not compress: every block is stored raw
+    rnd = W.uniform_int(9, 1, 0, 200000, 0, 256).astype(np.uint8)
+    buf = orc.encode(rnd, O.LZ77, 65536)
+    for off, ln, r0, rows, ch in chunks_of(orc, buf):
+        assert ch["flags"] & 1 and ch["secs"][0] == rnd[r0:r0 + rows].tobytes()
+    assert np.array_equal(orc.decode(buf), rnd)
+    # long literal runs need multi-byte varints
+    seg = W.uniform_int(9, 2, 0, 3000, 0, 256).astype(np.uint8)
+    x = np.concatenate([seg, seg, seg[:500], seg])
+    buf = orc.encode(x, O.LZ77, 65536)
+    ch = chunks_of(orc, buf)[0][4]
+    assert not ch["flags"] & 1 and ch["secs"][0][:2] == bytes([3000 & 0x7F | 0x80, 3000 >> 7])
+    assert np.array_equal(orc.decode(buf), x)
+    # text round trip, several blocks, a ragged last block
+    t, _ = W.text_column(5, 300001)
+    buf = orc.encode(t, O.LZ77, 65536)
+    assert len(buf) < len(t)
+    chs = chunks_of(orc, buf)
+    assert len(chs) == 5 and chs[-1][3] == 300001 - 4 * 65536
+    assert np.array_equal(orc.decode(buf), t)
+
+
+def _lz_blob(tokens: bytes, lits: bytes, rows: int, ntok: int) -> bytes:
+    """A hand-built LZ77 chunk: header, tokens at 64, literals at the next 16-byte boundary."""
+    t_off = 64
+    l_off = (t_off + len(tokens) + 15) // 16 * 16
+    end = (l_off + len(lits) + 15) // 16 * 16
+    b = bytearray(end)
+    struct.pack_into("<IBBBBIIq", b, 0, 0x4B48435A, O.LZ77, O.BYTES, 0, 0, rows, ntok, 0)
+    struct.pack_into("<3I3I", b, 24, t_off, l_off, 0, len(tokens), len(lits), 0)
+    b[t_off:t_off + len(tokens)] = tokens
+    b[l_off:l_off + len(lits)] = lits
+    return bytes(b)
+
+
+def pin_lz_hand_streams(orc):
+    # one literal then a back-reference of offset 1: the byte repeats (source overlaps output)
+    blob = _lz_blob(bytes([1, 1, 0, 3, 0]), b"z", 8, 2)
+    assert orc.decode_chunk(blob, np.uint8).tobytes() == b"zzzzzzzz"
+    # offset 2 over "xy": xyxyxyx
+    blob = _lz_blob(bytes([2, 2, 0, 1, 0]), b"xy", 7, 2)
+    assert orc.decode_chunk(blob, np.uint8).tobytes() == b"xyxyxyx"
+    # malformed streams are rejected, not decoded
+    bad = [
+        _lz_blob(bytes([1, 0, 0, 3, 0]), b"z", 8, 2),     # offset 0
+        _lz_blob(bytes([1, 2, 0, 3, 0]), b"z", 8, 2),     # offset beyond the bytes produced
+        _lz_blob(bytes([1, 1, 0, 9, 0]), b"z", 8, 2),     # match runs past the block
+        _lz_blob(bytes([3]), b"z", 3, 1),                 # literals past the literal stream
+        _lz_blob(bytes([1, 1, 0, 3, 0, 0]), b"z", 8, 2),  # unread token bytes
+    ]
+    for blob in bad:
+        try:
+            orc.decode_chunk(blob, np.uint8)
+        except O.OracleError as err:
+            assert err.code == O.ECORRUPT
+        else:
+            raise AssertionError("malformed LZ77 stream accepted")
+
+
+def pin_chunking(orc):
+    x = W.uniform_int(2, 3, 0, 10007, -50, 50).astype(np.int64)
+    for scheme in (O.RAW, O.FOR_BP, O.DICT_BP, O.DELTA_BP, O.RLE):
+        buf = orc.encode(x, scheme, 1000)
+        info = orc.column_info(buf)
+        assert info["n_chunks"] == 11 and info["n_rows"] == 10007 and info["total_bytes"] == len(buf)
+        prev_end = 64 + 32 * 11
+        for c, (off, ln, r0, rows, ch) in enumerate(chunks_of(orc, buf)):
+            assert off == prev_end and off % 16 == 0 and ln % 16 == 0
+            assert r0 == 1000 * c and rows == min(1000, 10007 - r0)
+            assert all(o % 16 == 0 for o, l in zip(ch["offs"], ch["lens"]) if o or l)
+            assert np.array_equal(orc.decode_chunk(buf[off:off + ln], np.int64), x[r0:r0 + rows])
+            prev_end = off + ln
+        assert np.array_equal(orc.decode(buf), x)
+    empty = orc.encode(np.zeros(0, np.int32), O.FOR_BP, 1000)
+    assert orc.column_info(empty)["n_chunks"] == 0 and len(orc.decode(empty)) == 0
+
+
+def pin_rejects_corrupt(orc):
+    x = W.uniform_int(2, 3, 0, 5000, 0, 1000).astype(np.int32)
+    for scheme in (O.FOR_BP, O.DELTA_BP, O.RLE):
+        buf = bytearray(orc.encode(x, scheme, 5000))
+        off, ln, r0, rows, ch = chunks_of(orc, bytes(buf))[0]
+        bad = bytearray(buf)
+        bad[off] ^= 0xFF  # chunk magic
+        try:
+            orc.decode(bytes(bad))
+        except O.OracleError as err:
+            assert err.code == O.ECORRUPT
+        else:
+            raise AssertionError("bad magic accepted")
+    # RLE counts that do not add up to the rows
+    buf = bytearray(orc.encode(x, O.RLE, 5000))
+    off, ln, r0, rows, ch = chunks_of(orc, bytes(buf))[0]
+    lo = off + ch["offs"][1]
+    struct.pack_into("<I", buf, lo, struct.unpack_from("<I", buf, lo)[0] + 1)
+    try:
+        orc.decode(bytes(buf))
+    except O.OracleError as err:
+        assert err.code == O.ECORRUPT
+    else:
+        raise AssertionError("RLE count mismatch accepted")
+
+
+def pin_strings(orc):
+    t, o = W.text_column(6, 200000)
+    buf = orc.encode_strings(t, o)
+    t2, o2 = orc.decode_strings(buf)
+    assert np.array_equal(t2, t) and np.array_equal(o2, o)
+    assert o[0] == 0 and o[-1] == len(t) and np.all(np.diff(o) > 0)
+
+
+PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]
