@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Throughput of compressed-column transfer + decode on GB300.
+
+Workload (one step): a 64M-row int64 sorted key column (gaps geometric, mean
+4) in delta + bit-packing with 1024-row blocks, and a 64M-row int32 date
+column (2,557 distinct days, runs geometric, mean 8) in RLE, both in 1M-row
+chunks (805,306,368 uncompressed bytes per step).
+
+  value   uncompressed GB/s of the decode with the compressed columns already
+          resident in HBM (zf_decompress_resident), CUDA events on the
+          decode stream, L2 flushed before every step.
+  e2e     the same metric end to end through zf_transfer_decompress +
+          zf_sync: pinned-host chunks copied host-to-device, decoded,
+          and the step's status word read back, host wall clock per step.
+  roofline  the dominant kernel (delta decode of the keys) timed alone:
+          algorithmic bytes (compressed read + plain written) per launch over
+          its CUDA-event duration, against the measured HBM copy peak.
+  cpu_baseline  the CPU oracle decoding a bounded sample of the same chunks.
+
+--impl reference times the CPU oracle alone on the same metric.
+With torchrun (--gpus N) every rank decodes its own replica (no collective on
+the data path); value sums the ranks' bytes over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "end-to-end uncompressed GB/s (H2D+decode) vs raw PCIe copy; decode % HBM peak"
+N_ROWS = 1 << 26
+CHUNK_ROWS = 1 << 20
+WORKLOAD = ("group_parallel: 64M int64 sorted keys (gaps geometric mean 4; delta + bit-packing, 1024-row "
+            "blocks) + 64M int32 dates (2,557 days, runs geometric mean 8; RLE), 1M-row chunks")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_workload(seed: int):
+    import zf_workloads as W
+    keys = W.sorted_keys(seed, N_ROWS)
+    dates = W.dates_rle(seed, N_ROWS)
+    return keys, dates
+
+
+def oracle_sample(handles, dtypes, budget_s: float, min_chunks: int = 1):
+    """Decode chunks of each column with the CPU oracle, round-robin, until
+    `budget_s` seconds pass; returns (bytes, seconds, description)."""
+    import oracle
+    import paper_2602_08190_gb300 as zf
+    blobs = []
+    for h, dt in zip(handles, dtypes):
+        b = zf.zf_compressed_bytes(h)
+        info = oracle.column_info(b)
+        blobs.append((b, info["n_chunks"], dt))
+    done_bytes, done_chunks, t0 = 0, 0, time.perf_counter()
+    k = 0
+    while True:
+        for b, nch, dt in blobs:
+            off, ln, r0, rows = oracle.chunk_span(b, k % nch)
+            out = oracle.decode_chunk(b[off:off + ln], dt)
+            done_bytes += out.nbytes
+            done_chunks += 1
+        k += 1
+        if time.perf_counter() - t0 >= budget_s and k >= min_chunks:
+            break
+    dt_s = time.perf_counter() - t0
+    return done_bytes, dt_s, f"{done_chunks} chunks of 1M rows ({k} per column), single thread"
+
+
+def run_reference(args, rank: int):
+    """CPU oracle arm: each step decodes a bounded sample of the workload."""
+    import oracle
+    import paper_2602_08190_gb300 as zf
+    oracle.build()
+    keys, dates = make_workload(1)
+    hk = zf.zf_compress_host(zf.zf_plan(None, zf.Column(keys), scheme=zf.ZF_DELTA_BP, chunk_rows=CHUNK_ROWS),
+                             zf.Column(keys))
+    hd = zf.zf_compress_host(zf.zf_plan(None, zf.Column(dates), scheme=zf.ZF_RLE, chunk_rows=CHUNK_ROWS),
+                             zf.Column(dates))
+    for _ in range(args.warmup):
+        oracle_sample([hk, hd], [np.int64, np.int32], 0.0)
+    tot_b, tot_s = 0, 0.0
+    desc = ""
+    for _ in range(args.steps):
+        b, s, desc = oracle_sample([hk, hd], [np.int64, np.int32], args.ref_step_s)
+        tot_b += b
+        tot_s += s
+    v = tot_b / tot_s / 1e9
+    line = {"metric": METRIC, "value": round(v, 4), "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(tot_s / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64/int32", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": desc},
+            "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    zf.zf_compressed_free(hk)
+    zf.zf_compressed_free(hd)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="zipflow", choices=["zipflow", "reference"])
+    ap.add_argument("--ref-step-s", type=float, default=2.0, help="CPU seconds per reference step")
+    ap.add_argument("--cpu-budget-s", type=float, default=12.0, help="CPU seconds for the cpu_baseline sample")
+    ap.add_argument("--tile-rows", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--stage-mb", type=float, default=0)
+    ap.add_argument("--slots", type=int, default=0)
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
+    args = ap.parse_args()
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, rank)
+        return
+
+    import torch
+    import paper_2602_08190_gb300 as zf
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    keys, dates = make_workload(1 + rank)
+    ck, cd = zf.Column(keys), zf.Column(dates)
+    copy_s, comp_s = torch.cuda.Stream(), torch.cuda.Stream()
+    ctx = zf.zf_ctx_create(local, copy_s.cuda_stream, comp_s.cuda_stream)
+    if any((args.tile_rows, args.threads, args.stage_mb, args.ctas_per_sm)):
+        zf.zf_ctx_set_kcfg(ctx, args.tile_rows, args.threads, args.ctas_per_sm, int(args.stage_mb * (1 << 20)), 0)
+    if args.slots:
+        zf.zf_ctx_set_ring(ctx, args.slots)
+    hk = zf.zf_compress_host(zf.zf_plan(ctx, ck, scheme=zf.ZF_DELTA_BP, chunk_rows=CHUNK_ROWS), ck)
+    hd = zf.zf_compress_host(zf.zf_plan(ctx, cd, scheme=zf.ZF_RLE, chunk_rows=CHUNK_ROWS), cd)
+    raw_k, comp_k, _ = zf.zf_compressed_info(hk)
+    raw_d, comp_d, _ = zf.zf_compressed_info(hd)
+    raw, comp = raw_k + raw_d, comp_k + comp_d
+    out_k = torch.empty(raw_k, dtype=torch.uint8, device="cuda")
+    out_d = torch.empty(raw_d, dtype=torch.uint8, device="cuda")
+    outs, caps = [out_k.data_ptr(), out_d.data_ptr()], [raw_k, raw_d]
+    rk, rd = zf.zf_upload(ctx, hk), zf.zf_upload(ctx, hd)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    def resident_step(cols, o, c):
+        with torch.cuda.stream(comp_s):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(comp_s)
+            zf.zf_decompress_resident(ctx, cols, o, c)
+            e1.record(comp_s)
+        st, stats = zf.zf_sync(ctx)
+        return e0.elapsed_time(e1), stats.n_launches
+
+    def e2e_step():
+        t0 = time.perf_counter()
+        zf.zf_transfer_decompress(ctx, [hk, hd], outs, caps)
+        st, stats = zf.zf_sync(ctx)
+        return (time.perf_counter() - t0) * 1e3, stats
+
+    # correctness of this run's outputs (cheap full compare) before timing
+    zf.zf_transfer_decompress(ctx, [hk, hd], outs, caps)
+    zf.zf_sync(ctx)
+    assert np.array_equal(out_k.cpu().numpy().view(np.int64), keys)
+    assert np.array_equal(out_d.cpu().numpy().view(np.int32), dates)
+
+    for _ in range(args.warmup):
+        resident_step([rk, rd], outs, caps)
+        e2e_step()
+        resident_step([rk], outs[:1], caps[:1])
+
+    launches = 0
+    with Clocks(local) as clk:
+        barrier()
+        dev_ms = []
+        for _ in range(args.steps):
+            ms, nl = resident_step([rk, rd], outs, caps)
+            dev_ms.append(ms)
+            launches += nl
+        barrier()
+        e2e_ms, e2e_ev = [], []
+        for _ in range(args.steps):
+            ms, stats = e2e_step()
+            e2e_ms.append(ms)
+            e2e_ev.append(stats.total_ms)
+            launches += stats.n_launches
+        barrier()
+        kern_ms = []
+        for _ in range(args.steps):
+            ms, nl = resident_step([rk], outs[:1], caps[:1])
+            kern_ms.append(ms)
+            launches += nl
+        barrier()
+
+    # raw link: best-of-10 pinned H2D copy of the same compressed bytes
+    src = torch.empty(comp, dtype=torch.uint8, pin_memory=True)
+    dst = torch.empty(comp, dtype=torch.uint8, device="cuda")
+    best = 1e9
+    for _ in range(10):
+        with torch.cuda.stream(copy_s):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(copy_s)
+            dst.copy_(src, non_blocking=True)
+            e1.record(copy_s)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    link_gbs = comp / best / 1e6
+
+    t_dev = float(np.mean(dev_ms))
+    t_e2e = float(np.mean(e2e_ms))
+    t_kern = float(np.mean(kern_ms))
+    if dist:
+        t = torch.tensor([t_dev, t_e2e, t_kern], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev, t_e2e, t_kern = t.tolist()
+    value = world * raw / (t_dev * 1e-3) / 1e9
+    e2e = world * raw / (t_e2e * 1e-3) / 1e9
+    hbm, peak_kind = peaks()
+    kern_bytes = comp_k + raw_k
+    achieved = kern_bytes / (t_kern * 1e-3) / 1e9
+    cr = raw / comp
+    line = None
+    if rank == 0:
+        import oracle
+        oracle.build()
+        cpu_b, cpu_s, cpu_desc = oracle_sample([hk, hd], [np.int64, np.int32], args.cpu_budget_s)
+        traffic = None
+        prof = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(prof):
+            with open(prof) as f:
+                traffic = json.load(f).get("delta_i64_decode_bytes_per_launch")
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t_dev, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64/int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "raw_bytes_per_step": raw, "comp_bytes_per_step": comp,
+                       "compression_ratio": round(cr, 3), "l2": "flushed (256 MiB write) before every resident step",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "e2e": {"value": round(e2e, 2), "unit": "GB/s", "h2d_bytes_per_step": comp, "d2h_bytes_per_step": 8,
+                    "ms_per_step": round(t_e2e, 4), "event_ms_per_step": round(float(np.mean(e2e_ev)), 4),
+                    "raw_h2d_link_gbs": round(link_gbs, 2), "target_0.9_link_x_cr_gbs": round(0.9 * link_gbs * cr, 2),
+                    "frac_of_link_x_cr": round(e2e / world / (link_gbs * cr), 4)},
+            "roofline": {"bound": "hbm", "kernel": "tiles_kernel<delta_bp, int64>", "achieved": round(achieved, 1),
+                         "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                         "traffic": traffic, "algorithmic_bytes_per_launch": kern_bytes,
+                         "launch_ms": round(t_kern, 4)},
+            "cpu_baseline": {"value": round(cpu_b / cpu_s / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": cpu_desc},
+            "clocks": clk.summary(),
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    zf.zf_resident_free(rk)
+    zf.zf_resident_free(rd)
+    zf.zf_compressed_free(hk)
+    zf.zf_compressed_free(hd)
+    zf.zf_ctx_destroy(ctx)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

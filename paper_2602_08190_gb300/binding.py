@@ -1,0 +1,209 @@
+"""ctypes declarations of the C ABI in include/zf.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libzf.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libzf.so is not built ({LIB_PATH}); run __graft_entry__.build() or "
+                      "python paper_2602_08190_gb300/build.py")
+_L = ctypes.CDLL(LIB_PATH)
+
+__all__ = [
+    "ZF_OK", "ZF_EINVAL", "ZF_ENOMEM", "ZF_ECUDA", "ZF_ECORRUPT", "ZF_ETIMEOUT", "ZF_EUNSUPPORTED", "ZF_EBUSY",
+    "ZF_I32", "ZF_I64", "ZF_BYTES", "ZF_RAW", "ZF_FOR_BP", "ZF_DICT_BP", "ZF_DELTA_BP", "ZF_RLE", "ZF_LZ77",
+    "ZF_KCFG_BATCHED", "ZF_KCFG_GRAPH", "SCHEME_NAMES", "ZfError", "zf_column", "zf_kcfg", "zf_plan_opts",
+    "zf_plan_t", "zf_stats", "Column", "zf_ctx_create", "zf_ctx_destroy", "zf_last_error", "zf_ctx_set_kcfg",
+    "zf_ctx_set_ring", "zf_plan", "zf_compress_host", "zf_compressed_info", "zf_compressed_free",
+    "zf_compressed_bytes", "zf_compressed_from_bytes", "zf_transfer_decompress", "zf_sync", "zf_upload",
+    "zf_resident_free", "zf_decompress_resident", "EXPORTED", "LIB_PATH",
+]
+
+(ZF_OK, ZF_EINVAL, ZF_ENOMEM, ZF_ECUDA, ZF_ECORRUPT, ZF_ETIMEOUT, ZF_EUNSUPPORTED, ZF_EBUSY) = range(8)
+ZF_I32, ZF_I64, ZF_BYTES = range(3)
+ZF_RAW, ZF_FOR_BP, ZF_DICT_BP, ZF_DELTA_BP, ZF_RLE, ZF_LZ77 = range(6)
+ZF_KCFG_BATCHED, ZF_KCFG_GRAPH = 1, 2
+SCHEME_NAMES = ["raw", "for_bp", "dict_bp", "delta_bp", "rle", "lz77"]
+_STATUS = ["ok", "einval", "enomem", "ecuda", "ecorrupt", "etimeout", "eunsupported", "ebusy"]
+
+
+class ZfError(RuntimeError):
+    def __init__(self, status: int, call: str, detail: str = ""):
+        name = _STATUS[status] if 0 <= status < len(_STATUS) else str(status)
+        super().__init__(f"{call} -> {name}" + (f": {detail}" if detail else ""))
+        self.status = status
+
+
+class zf_column(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("data", ctypes.c_void_p), ("n", ctypes.c_uint64),
+                ("offsets", ctypes.c_void_p)]
+
+
+class zf_kcfg(ctypes.Structure):
+    _fields_ = [("tile_rows", ctypes.c_uint32), ("threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
+                ("stage_bytes", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+class zf_plan_opts(ctypes.Structure):
+    _fields_ = [("scheme", ctypes.c_int32), ("chunk_rows", ctypes.c_uint32), ("selector", ctypes.c_int32),
+                ("offsets_scheme", ctypes.c_int32)]
+
+
+class zf_plan_t(ctypes.Structure):
+    _fields_ = [("scheme", ctypes.c_int32), ("chunk_rows", ctypes.c_uint32), ("offsets_scheme", ctypes.c_int32),
+                ("kcfg", zf_kcfg), ("predicted_ms", ctypes.c_float), ("label", ctypes.c_int32)]
+
+
+class zf_stats(ctypes.Structure):
+    _fields_ = [("raw_bytes", ctypes.c_uint64), ("comp_bytes", ctypes.c_uint64), ("n_chunks", ctypes.c_uint32),
+                ("n_stages", ctypes.c_uint32), ("n_launches", ctypes.c_uint32), ("device_error", ctypes.c_uint32),
+                ("total_ms", ctypes.c_float), ("copy_ms", ctypes.c_float), ("decode_ms", ctypes.c_float)]
+
+
+_vp, _u32, _u64, _i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32
+_SIGS = {
+    "zf_ctx_create": [ctypes.c_int, _vp, _vp, ctypes.POINTER(_vp)],
+    "zf_ctx_destroy": [_vp],
+    "zf_ctx_set_kcfg": [_vp, ctypes.POINTER(zf_kcfg)],
+    "zf_ctx_set_ring": [_vp, _u32, _u64],
+    "zf_plan": [_vp, ctypes.POINTER(zf_column), ctypes.POINTER(zf_plan_opts), ctypes.POINTER(zf_plan_t)],
+    "zf_compress_host": [ctypes.POINTER(zf_plan_t), ctypes.POINTER(zf_column), ctypes.POINTER(_vp)],
+    "zf_compressed_info": [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u32)],
+    "zf_compressed_free": [_vp],
+    "zf_compressed_bytes": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_u64)],
+    "zf_compressed_from_bytes": [_vp, _u64, ctypes.POINTER(_vp)],
+    "zf_transfer_decompress": [_vp, ctypes.POINTER(_vp), _u32, ctypes.POINTER(_vp), ctypes.POINTER(_u64)],
+    "zf_sync": [_vp, ctypes.POINTER(zf_stats)],
+    "zf_upload": [_vp, _vp, ctypes.POINTER(_vp)],
+    "zf_resident_free": [_vp],
+    "zf_decompress_resident": [_vp, ctypes.POINTER(_vp), _u32, ctypes.POINTER(_vp), ctypes.POINTER(_u64)],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_L, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+_L.zf_last_error.argtypes = [_vp]
+_L.zf_last_error.restype = ctypes.c_char_p
+EXPORTED = sorted(list(_SIGS) + ["zf_last_error"])
+
+
+def _check(st: int, call: str, ctx=None):
+    if st != ZF_OK:
+        detail = _L.zf_last_error(ctx).decode() if ctx else ""
+        raise ZfError(st, call, detail)
+
+
+class Column:
+    """A host column kept alive for the duration of a call (numpy arrays)."""
+
+    def __init__(self, data: np.ndarray, offsets: np.ndarray | None = None):
+        self.data = np.ascontiguousarray(data)
+        if offsets is None:
+            dt = {np.dtype(np.int32): ZF_I32, np.dtype(np.int64): ZF_I64}[self.data.dtype]
+            self.offsets = None
+            n = len(self.data)
+        else:
+            assert self.data.dtype == np.uint8
+            self.offsets = np.ascontiguousarray(offsets, dtype=np.int32)
+            dt = ZF_BYTES
+            n = len(self.offsets) - 1
+        self.c = zf_column(dt, self.data.ctypes.data if self.data.size else None, n,
+                           self.offsets.ctypes.data if self.offsets is not None else None)
+
+
+def zf_ctx_create(device: int = 0, copy_stream: int | None = None, compute_stream: int | None = None) -> int:
+    out = _vp()
+    _check(_L.zf_ctx_create(device, copy_stream or None, compute_stream or None, ctypes.byref(out)), "zf_ctx_create")
+    return out.value
+
+
+def zf_ctx_destroy(ctx: int) -> None:
+    _check(_L.zf_ctx_destroy(ctx), "zf_ctx_destroy")
+
+
+def zf_last_error(ctx: int) -> str:
+    return _L.zf_last_error(ctx).decode()
+
+
+def zf_ctx_set_kcfg(ctx: int, tile_rows=0, threads=0, ctas_per_sm=0, stage_bytes=0, flags=0) -> None:
+    k = zf_kcfg(tile_rows, threads, ctas_per_sm, stage_bytes, flags)
+    _check(_L.zf_ctx_set_kcfg(ctx, ctypes.byref(k)), "zf_ctx_set_kcfg", ctx)
+
+
+def zf_ctx_set_ring(ctx: int, slots: int, slot_bytes: int = 0) -> None:
+    _check(_L.zf_ctx_set_ring(ctx, slots, slot_bytes), "zf_ctx_set_ring", ctx)
+
+
+def zf_plan(ctx: int | None, col: Column, scheme: int = -1, chunk_rows: int = 0, selector: int = 0,
+            offsets_scheme: int = -1) -> zf_plan_t:
+    o = zf_plan_opts(scheme, chunk_rows, selector, offsets_scheme)
+    p = zf_plan_t()
+    _check(_L.zf_plan(ctx, ctypes.byref(col.c), ctypes.byref(o), ctypes.byref(p)), "zf_plan", ctx)
+    return p
+
+
+def zf_compress_host(plan: zf_plan_t, col: Column) -> int:
+    out = _vp()
+    _check(_L.zf_compress_host(ctypes.byref(plan), ctypes.byref(col.c), ctypes.byref(out)), "zf_compress_host")
+    return out.value
+
+
+def zf_compressed_info(c: int) -> tuple[int, int, int]:
+    raw, comp, n = _u64(), _u64(), _u32()
+    _check(_L.zf_compressed_info(c, ctypes.byref(raw), ctypes.byref(comp), ctypes.byref(n)), "zf_compressed_info")
+    return raw.value, comp.value, n.value
+
+
+def zf_compressed_free(c: int) -> None:
+    _check(_L.zf_compressed_free(c), "zf_compressed_free")
+
+
+def zf_compressed_bytes(c: int) -> bytes:
+    p, n = _vp(), _u64()
+    _check(_L.zf_compressed_bytes(c, ctypes.byref(p), ctypes.byref(n)), "zf_compressed_bytes")
+    return ctypes.string_at(p.value, n.value) if n.value else b""
+
+
+def zf_compressed_from_bytes(data: bytes) -> int:
+    out = _vp()
+    buf = ctypes.create_string_buffer(bytes(data), len(data))
+    _check(_L.zf_compressed_from_bytes(buf, len(data), ctypes.byref(out)), "zf_compressed_from_bytes")
+    return out.value
+
+
+def _arrays(cols, outs, caps):
+    n = len(outs)
+    return ((_vp * max(1, len(cols)))(*cols), (_vp * max(1, n))(*outs), (_u64 * max(1, n))(*caps))
+
+
+def zf_transfer_decompress(ctx: int, cols: list[int], outs: list[int], caps: list[int]) -> None:
+    c, o, k = _arrays(cols, outs, caps)
+    _check(_L.zf_transfer_decompress(ctx, c, len(cols), o, k), "zf_transfer_decompress", ctx)
+
+
+def zf_sync(ctx: int, raise_on_error: bool = True) -> tuple[int, zf_stats]:
+    s = zf_stats()
+    st = _L.zf_sync(ctx, ctypes.byref(s))
+    if raise_on_error:
+        _check(st, "zf_sync", ctx)
+    return st, s
+
+
+def zf_upload(ctx: int, c: int) -> int:
+    out = _vp()
+    _check(_L.zf_upload(ctx, c, ctypes.byref(out)), "zf_upload", ctx)
+    return out.value
+
+
+def zf_resident_free(r: int) -> None:
+    _check(_L.zf_resident_free(r), "zf_resident_free")
+
+
+def zf_decompress_resident(ctx: int, cols: list[int], outs: list[int], caps: list[int]) -> None:
+    c, o, k = _arrays(cols, outs, caps)
+    _check(_L.zf_decompress_resident(ctx, c, len(cols), o, k), "zf_decompress_resident", ctx)

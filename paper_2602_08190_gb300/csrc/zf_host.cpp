@@ -1,0 +1,644 @@
+// zf_host.cpp -- host side of the library: the column encoders that run at
+// compression time (Section 3: data is compressed on the CPU and kept in host
+// memory), the serializer of the container format, and the structural
+// validator used when a serialized column is imported.
+//
+// Codecs (Section 2.1): FOR + bit-packing, dictionary + bit-packing, delta +
+// bit-packing, run-length, LZ77.  Encoding is canonical for all but LZ77, so
+// two correct encoders produce the same bytes.
+#include <cuda_runtime_api.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <functional>
+#include <mutex>
+#include <thread>
+
+#include "zf_internal.h"
+
+namespace zf {
+namespace {
+
+// ---------------------------------------------------------------- byte output
+struct Out {
+    std::vector<uint8_t> b;
+    void put8(uint64_t pos, uint8_t v) { b[pos] = v; }
+    void put32(uint64_t pos, uint32_t v) { memcpy(&b[pos], &v, 4); }
+    void put64(uint64_t pos, uint64_t v) { memcpy(&b[pos], &v, 8); }
+};
+
+// Bit-packing: value i at stream bits [i*b, i*b+b), LSB first.  Writes exactly
+// ceil(n*b/8) bytes at `out`.
+template <class Get>
+void pack_stream(uint64_t n, uint32_t b, Get get, uint8_t* out) {
+    if (b == 0) return;
+    unsigned __int128 acc = 0;
+    uint32_t nacc = 0;
+    uint64_t o = 0;
+    const uint64_t mask = b >= 64 ? ~0ull : ((1ull << b) - 1);
+    for (uint64_t i = 0; i < n; i++) {
+        acc |= (unsigned __int128)(get(i) & mask) << nacc;
+        nacc += b;
+        if (nacc >= 64) {
+            uint64_t w = (uint64_t)acc;
+            memcpy(out + o, &w, 8);
+            o += 8;
+            acc >>= 64;
+            nacc -= 64;
+        }
+    }
+    uint32_t tail = (nacc + 7) / 8;
+    uint64_t w = (uint64_t)acc;
+    for (uint32_t k = 0; k < tail; k++) out[o + k] = (uint8_t)(w >> (8 * k));
+}
+
+struct ChunkWriter {
+    Out& o;
+    uint64_t end = kChunkHeader;
+    explicit ChunkWriter(Out& out) : o(out) {}
+    uint64_t section(int s, uint64_t len) {
+        uint64_t off = align16(end);
+        o.put32(24 + 4 * s, (uint32_t)off);
+        o.put32(36 + 4 * s, (uint32_t)len);
+        end = off + len;
+        return off;
+    }
+    void header(int scheme, int dtype, uint32_t bw, uint32_t flags, uint32_t rows, uint32_t n_aux, uint64_t ref) {
+        o.put32(0, kChunkMagic);
+        o.put8(4, (uint8_t)scheme);
+        o.put8(5, (uint8_t)dtype);
+        o.put8(6, (uint8_t)bw);
+        o.put8(7, (uint8_t)flags);
+        o.put32(8, rows);
+        o.put32(12, n_aux);
+        o.put64(16, ref);
+    }
+};
+
+template <class T> constexpr int dtype_code() { return sizeof(T) == 8 ? ZF_I64 : ZF_I32; }
+
+// ------------------------------------------------------------------ RAW
+template <class T>
+void enc_raw(const T* x, uint32_t m, Out& o) {
+    o.b.assign(align16(kChunkHeader + (uint64_t)m * sizeof(T)), 0);
+    ChunkWriter w(o);
+    w.header(ZF_RAW, dtype_code<T>(), 0, 0, m, 0, 0);
+    uint64_t off = w.section(0, (uint64_t)m * sizeof(T));
+    if (m) memcpy(&o.b[off], x, (uint64_t)m * sizeof(T));
+}
+
+// ------------------------------------------------------------------ FOR + BP
+template <class T>
+void enc_for(const T* x, uint32_t m, Out& o) {
+    using U = typename std::make_unsigned<T>::type;
+    T mn = m ? x[0] : 0, mx = m ? x[0] : 0;
+    for (uint32_t i = 1; i < m; i++) {
+        mn = std::min(mn, x[i]);
+        mx = std::max(mx, x[i]);
+    }
+    uint32_t b = bits_of((uint64_t)(U)((U)mx - (U)mn));
+    uint64_t pb = packed_bytes(m, b);
+    o.b.assign(align16(align16(kChunkHeader) + pb), 0);
+    ChunkWriter w(o);
+    w.header(ZF_FOR_BP, dtype_code<T>(), b, 0, m, 0, (uint64_t)(int64_t)mn);
+    uint64_t off = w.section(0, pb);
+    pack_stream(m, b, [&](uint64_t i) { return (uint64_t)(U)((U)x[i] - (U)mn); }, &o.b[off]);
+}
+
+// ------------------------------------------------------------------ dictionary + BP
+template <class T>
+zf_status enc_dict(const T* x, uint32_t m, Out& o) {
+    std::vector<T> d(x, x + m);
+    std::sort(d.begin(), d.end());
+    d.erase(std::unique(d.begin(), d.end()), d.end());
+    if (d.size() > kMaxDict) return ZF_EINVAL;
+    uint32_t nd = (uint32_t)d.size();
+    uint32_t b = nd ? bits_of(nd - 1) : 0;
+    uint64_t pb = packed_bytes(m, b);
+    uint64_t dict_bytes = (uint64_t)nd * sizeof(T);
+    o.b.assign(align16(align16(kChunkHeader + dict_bytes) + pb), 0);
+    ChunkWriter w(o);
+    w.header(ZF_DICT_BP, dtype_code<T>(), b, 0, m, nd, 0);
+    uint64_t doff = w.section(0, dict_bytes);
+    if (nd) memcpy(&o.b[doff], d.data(), dict_bytes);
+    uint64_t coff = w.section(1, pb);
+    pack_stream(m, b, [&](uint64_t i) {
+        return (uint64_t)(std::lower_bound(d.begin(), d.end(), x[i]) - d.begin());
+    }, &o.b[coff]);
+    return ZF_OK;
+}
+
+// ------------------------------------------------------------------ delta + BP
+template <class T>
+void enc_delta(const T* x, uint32_t m, Out& o) {
+    using U = typename std::make_unsigned<T>::type;
+    uint32_t nb = (m + kDeltaBlock - 1) / kDeltaBlock;
+    struct Blk { T base, min_d; uint32_t b; uint64_t poff, len; };
+    std::vector<Blk> blk(nb);
+    uint64_t payload = 0;
+    for (uint32_t k = 0; k < nb; k++) {
+        uint32_t r0 = k * kDeltaBlock, mk = std::min(kDeltaBlock, m - r0);
+        const T* y = x + r0;
+        T min_d = 0;
+        for (uint32_t j = 1; j < mk; j++) {
+            T d = (T)(U)((U)y[j] - (U)y[j - 1]);
+            if (j == 1 || d < min_d) min_d = d;
+        }
+        U umax = 0;
+        for (uint32_t j = 1; j < mk; j++) {
+            U u = (U)((U)y[j] - (U)y[j - 1]) - (U)min_d;
+            umax = std::max(umax, u);
+        }
+        uint32_t b = bits_of((uint64_t)umax);
+        uint64_t len = align16(packed_bytes(mk, b));
+        blk[k] = {y[0], min_d, b, payload, len};
+        payload += len;
+    }
+    uint64_t table = (uint64_t)nb * kDeltaEntry;
+    o.b.assign(align16(align16(kChunkHeader + table) + payload), 0);
+    ChunkWriter w(o);
+    w.header(ZF_DELTA_BP, dtype_code<T>(), 0, 0, m, nb, 0);
+    uint64_t toff = w.section(0, table);
+    uint64_t poff = w.section(1, payload);
+    for (uint32_t k = 0; k < nb; k++) {
+        uint8_t* e = &o.b[toff + (uint64_t)k * kDeltaEntry];
+        int64_t base = blk[k].base, min_d = blk[k].min_d;
+        uint32_t po = (uint32_t)blk[k].poff;
+        memcpy(e, &base, 8);
+        memcpy(e + 8, &min_d, 8);
+        memcpy(e + 16, &po, 4);
+        e[20] = (uint8_t)blk[k].b;
+        const T* y = x + (uint64_t)k * kDeltaBlock;
+        uint32_t mk = std::min(kDeltaBlock, m - k * kDeltaBlock);
+        U md = (U)blk[k].min_d;
+        pack_stream(mk, blk[k].b, [&](uint64_t j) {
+            return j == 0 ? 0ull : (uint64_t)(U)((U)((U)y[j] - (U)y[j - 1]) - md);
+        }, &o.b[poff + blk[k].poff]);
+    }
+}
+
+// ------------------------------------------------------------------ RLE
+template <class T>
+void enc_rle(const T* x, uint32_t m, Out& o) {
+    uint32_t R = 0;
+    for (uint32_t i = 0; i < m; i++) R += (i == 0 || x[i] != x[i - 1]);
+    uint32_t nt = (m + kRleDirRows - 1) / kRleDirRows;
+    uint64_t vb = (uint64_t)R * sizeof(T), lb = 4ull * R, db = 8ull * nt;
+    o.b.assign(align16(align16(align16(align16(kChunkHeader) + vb) + lb) + db), 0);
+    ChunkWriter w(o);
+    w.header(ZF_RLE, dtype_code<T>(), 0, 0, m, R, 0);
+    uint64_t voff = w.section(0, vb), loff = w.section(1, lb), doff = w.section(2, db);
+    T* vals = reinterpret_cast<T*>(&o.b[voff]);
+    uint32_t* lens = reinterpret_cast<uint32_t*>(&o.b[loff]);
+    uint32_t* dir = reinterpret_cast<uint32_t*>(&o.b[doff]);
+    uint32_t r = 0, start = 0;
+    for (uint32_t i = 0; i < m; i++) {
+        if (i > 0 && x[i] != x[i - 1]) {
+            lens[r++] = i - start;
+            start = i;
+        }
+        if (i == start) vals[r] = x[i];
+        if (i % kRleDirRows == 0) {
+            dir[2 * (i / kRleDirRows)] = r;
+            dir[2 * (i / kRleDirRows) + 1] = i - start;
+        }
+    }
+    if (m) lens[r] = m - start;
+}
+
+// ------------------------------------------------------------------ LZ77
+uint32_t leb128(uint8_t* p, uint32_t v) {
+    uint32_t n = 0;
+    do {
+        uint8_t c = v & 0x7F;
+        v >>= 7;
+        p[n++] = c | (v ? 0x80 : 0);
+    } while (v);
+    return n;
+}
+
+// Greedy LZ77 over one block: a hash of 4 bytes indexes the most recent
+// position; every position, including those inside a match, is inserted.
+void enc_lz(const uint8_t* s, uint32_t m, Out& o) {
+    constexpr int HB = 15;
+    std::vector<int32_t> table(1u << HB, -1);
+    std::vector<uint8_t> tok;
+    std::vector<uint8_t> lit;
+    tok.reserve(m / 2 + 16);
+    lit.reserve(m + 16);
+    auto hash = [&](uint32_t p) {
+        uint32_t v;
+        memcpy(&v, s + p, 4);
+        return (v * 2654435761u) >> (32 - HB);
+    };
+    uint8_t tmp[16];
+    uint32_t ntok = 0, pos = 0, lit_start = 0;
+    while (pos + kLzMinMatch <= m) {
+        uint32_t h = hash(pos);
+        int32_t cand = table[h];
+        table[h] = (int32_t)pos;
+        uint32_t len = 0;
+        if (cand >= 0 && pos - (uint32_t)cand <= kLzMaxOffset && memcmp(s + cand, s + pos, kLzMinMatch) == 0) {
+            len = kLzMinMatch;
+            while (pos + len < m && s[cand + len] == s[pos + len]) len++;
+        }
+        if (!len) {
+            pos++;
+            continue;
+        }
+        uint32_t ll = pos - lit_start;
+        tok.insert(tok.end(), tmp, tmp + leb128(tmp, ll));
+        lit.insert(lit.end(), s + lit_start, s + pos);
+        uint32_t off = pos - (uint32_t)cand;
+        tok.push_back((uint8_t)off);
+        tok.push_back((uint8_t)(off >> 8));
+        tok.insert(tok.end(), tmp, tmp + leb128(tmp, len - kLzMinMatch));
+        ntok++;
+        for (uint32_t q = pos + 1; q < pos + len && q + kLzMinMatch <= m; q++) table[hash(q)] = (int32_t)q;
+        pos += len;
+        lit_start = pos;
+    }
+    uint32_t ll = m - lit_start;
+    tok.insert(tok.end(), tmp, tmp + leb128(tmp, ll));
+    lit.insert(lit.end(), s + lit_start, s + m);
+    ntok++;
+    if (tok.size() + lit.size() >= m) {
+        o.b.assign(align16(kChunkHeader + m), 0);
+        ChunkWriter w(o);
+        w.header(ZF_LZ77, ZF_BYTES, 0, 1, m, 0, 0);
+        uint64_t off = w.section(0, m);
+        if (m) memcpy(&o.b[off], s, m);
+        return;
+    }
+    o.b.assign(align16(align16(kChunkHeader + tok.size()) + lit.size()), 0);
+    ChunkWriter w(o);
+    w.header(ZF_LZ77, ZF_BYTES, 0, 0, m, ntok, 0);
+    uint64_t toff = w.section(0, tok.size());
+    memcpy(&o.b[toff], tok.data(), tok.size());
+    uint64_t loff = w.section(1, lit.size());
+    if (!lit.empty()) memcpy(&o.b[loff], lit.data(), lit.size());
+}
+
+// ------------------------------------------------------------------ column assembly
+struct PartSpec {
+    int scheme, dtype;
+    const uint8_t* data;
+    uint64_t n;
+    uint32_t chunk_rows;
+};
+
+void run_parallel(uint32_t n, const std::function<void(uint32_t)>& f) {
+    unsigned nt = std::max(1u, std::min(std::thread::hardware_concurrency(), n));
+    std::atomic<uint32_t> next{0};
+    auto worker = [&] {
+        for (uint32_t i; (i = next.fetch_add(1)) < n;) f(i);
+    };
+    if (nt <= 1) {
+        worker();
+        return;
+    }
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; t++) th.emplace_back(worker);
+    for (auto& t : th) t.join();
+}
+
+zf_status encode_part(const PartSpec& p, std::vector<Out>& blobs, std::string* why) {
+    uint64_t nch = (p.n + p.chunk_rows - 1) / p.chunk_rows;
+    blobs.assign(nch, Out{});
+    std::atomic<int> err{ZF_OK};
+    uint32_t sz = dtype_size(p.dtype);
+    run_parallel((uint32_t)nch, [&](uint32_t c) {
+        uint64_t r0 = (uint64_t)c * p.chunk_rows;
+        uint32_t m = (uint32_t)std::min<uint64_t>(p.chunk_rows, p.n - r0);
+        const uint8_t* x = p.data + r0 * sz;
+        Out& o = blobs[c];
+        zf_status st = ZF_OK;
+        if (p.dtype == ZF_BYTES) {
+            if (p.scheme == ZF_LZ77) enc_lz(x, m, o);
+            else {  // RAW bytes
+                o.b.assign(align16(kChunkHeader + m), 0);
+                ChunkWriter w(o);
+                w.header(ZF_RAW, ZF_BYTES, 0, 0, m, 0, 0);
+                uint64_t off = w.section(0, m);
+                if (m) memcpy(&o.b[off], x, m);
+            }
+        } else if (p.dtype == ZF_I32) {
+            auto* v = reinterpret_cast<const int32_t*>(x);
+            switch (p.scheme) {
+            case ZF_RAW: enc_raw(v, m, o); break;
+            case ZF_FOR_BP: enc_for(v, m, o); break;
+            case ZF_DICT_BP: st = enc_dict(v, m, o); break;
+            case ZF_DELTA_BP: enc_delta(v, m, o); break;
+            case ZF_RLE: enc_rle(v, m, o); break;
+            }
+        } else {
+            auto* v = reinterpret_cast<const int64_t*>(x);
+            switch (p.scheme) {
+            case ZF_RAW: enc_raw(v, m, o); break;
+            case ZF_FOR_BP: enc_for(v, m, o); break;
+            case ZF_DICT_BP: st = enc_dict(v, m, o); break;
+            case ZF_DELTA_BP: enc_delta(v, m, o); break;
+            case ZF_RLE: enc_rle(v, m, o); break;
+            }
+        }
+        if (st != ZF_OK) err = st;
+    });
+    if (err != ZF_OK) {
+        if (why) *why = "scheme does not fit the column (dictionary above 65,536 entries)";
+        return (zf_status)err.load();
+    }
+    return ZF_OK;
+}
+
+uint64_t part_size(const std::vector<Out>& blobs) {
+    uint64_t s = kColHeader + (uint64_t)kDirEntry * blobs.size();
+    for (auto& b : blobs) s += b.b.size();
+    return s;
+}
+
+void write_part(const PartSpec& p, const std::vector<Out>& blobs, uint8_t* dst, uint32_t flags) {
+    uint64_t nch = blobs.size();
+    uint64_t total = part_size(blobs);
+    memset(dst, 0, kColHeader + kDirEntry * nch);
+    uint32_t magic = kColMagic;
+    uint16_t ver = 1;
+    memcpy(dst, &magic, 4);
+    memcpy(dst + 4, &ver, 2);
+    dst[6] = (uint8_t)p.scheme;
+    dst[7] = (uint8_t)p.dtype;
+    uint32_t n32 = (uint32_t)nch;
+    memcpy(dst + 8, &n32, 4);
+    memcpy(dst + 12, &p.chunk_rows, 4);
+    memcpy(dst + 16, &p.n, 8);
+    uint64_t raw = p.n * dtype_size(p.dtype);
+    memcpy(dst + 24, &raw, 8);
+    memcpy(dst + 32, &total, 8);
+    memcpy(dst + 40, &flags, 4);
+    std::vector<uint64_t> offs(nch);
+    uint64_t pos = kColHeader + kDirEntry * nch;
+    for (uint64_t c = 0; c < nch; c++) {
+        offs[c] = pos;
+        uint8_t* d = dst + kColHeader + kDirEntry * c;
+        uint64_t len = blobs[c].b.size(), r0 = c * p.chunk_rows;
+        uint32_t m = (uint32_t)std::min<uint64_t>(p.chunk_rows, p.n - r0);
+        memcpy(d, &pos, 8);
+        memcpy(d + 8, &len, 8);
+        memcpy(d + 16, &r0, 8);
+        memcpy(d + 24, &m, 4);
+        pos += len;
+    }
+    run_parallel((uint32_t)nch, [&](uint32_t c) {
+        if (!blobs[c].b.empty()) memcpy(dst + offs[c], blobs[c].b.data(), blobs[c].b.size());
+    });
+}
+
+bool scheme_fits(int scheme, int dtype) {
+    if (dtype == ZF_BYTES) return scheme == ZF_RAW || scheme == ZF_LZ77;
+    if (dtype != ZF_I32 && dtype != ZF_I64) return false;
+    return scheme >= ZF_RAW && scheme <= ZF_RLE;
+}
+
+}  // namespace
+
+// Allocate host memory for serialized bytes: pinned when a CUDA device is
+// present, plain memory when the machine has none (host-only use).
+static zf_status alloc_host(zf_compressed* c, uint64_t len) {
+    void* p = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0) {
+        cudaError_t e = cudaHostAlloc(&p, std::max<uint64_t>(len, 16), cudaHostAllocDefault);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return ZF_ENOMEM;
+        }
+        c->pinned = true;
+    } else {
+        cudaGetLastError();
+        p = malloc(std::max<uint64_t>(len, 16));
+        if (!p) return ZF_ENOMEM;
+        c->pinned = false;
+    }
+    c->host = (uint8_t*)p;
+    c->len = len;
+    return ZF_OK;
+}
+
+void free_compressed(zf_compressed* c) {
+    if (!c) return;
+    if (c->host) {
+        if (c->pinned) cudaFreeHost(c->host);
+        else free(c->host);
+    }
+    delete c;
+}
+
+zf_status encode_column(const zf_plan_t& plan, const zf_column& col, zf_compressed** out, std::string* why) {
+    int dt = col.dtype;
+    if (dt != ZF_I32 && dt != ZF_I64 && dt != ZF_BYTES) return ZF_EINVAL;
+    if (col.n && !col.data && !(dt == ZF_BYTES && col.offsets)) return ZF_EINVAL;
+    std::vector<PartSpec> specs;
+    if (dt == ZF_BYTES) {
+        if (!col.offsets) return ZF_EINVAL;
+        if (col.offsets[0] != 0) return ZF_EINVAL;
+        for (uint64_t i = 0; i < col.n; i++)
+            if (col.offsets[i + 1] < col.offsets[i]) return ZF_EINVAL;
+        int bs = plan.scheme == ZF_RAW ? ZF_RAW : ZF_LZ77;
+        int os = plan.offsets_scheme < 0 ? ZF_DELTA_BP : plan.offsets_scheme;
+        if (!scheme_fits(os, ZF_I32)) return ZF_EINVAL;
+        uint64_t nbytes = (uint64_t)(uint32_t)col.offsets[col.n];
+        specs.push_back({bs, ZF_BYTES, (const uint8_t*)col.data, nbytes, kLzBlock});
+        specs.push_back({os, ZF_I32, (const uint8_t*)col.offsets, col.n + 1, 65536});
+    } else {
+        if (!scheme_fits(plan.scheme, dt) || plan.scheme == ZF_LZ77) return ZF_EINVAL;
+        uint32_t cr = plan.chunk_rows ? plan.chunk_rows : (1u << 20);
+        if (cr % 1024 != 0) {
+            if (why) *why = "chunk_rows must be a multiple of 1024";
+            return ZF_EINVAL;
+        }
+        specs.push_back({plan.scheme, dt, (const uint8_t*)col.data, col.n, cr});
+    }
+    std::vector<std::vector<Out>> blobs(specs.size());
+    uint64_t total = 0;
+    for (size_t p = 0; p < specs.size(); p++) {
+        zf_status st = encode_part(specs[p], blobs[p], why);
+        if (st) return st;
+        total += part_size(blobs[p]);
+    }
+    auto* c = new zf_compressed();
+    zf_status st = alloc_host(c, total);
+    if (st) {
+        delete c;
+        return st;
+    }
+    uint64_t pos = 0;
+    for (size_t p = 0; p < specs.size(); p++) {
+        write_part(specs[p], blobs[p], c->host + pos, (specs.size() == 2 && p == 0) ? 1u : 0u);
+        pos += part_size(blobs[p]);
+        std::vector<Out>().swap(blobs[p]);
+    }
+    st = parse_serialized(c, why);
+    if (st) {
+        free_compressed(c);
+        return st;
+    }
+    *out = c;
+    return ZF_OK;
+}
+
+uint32_t tiles_of(const ChunkInfo& ch, uint32_t tile_rows) {
+    if (ch.scheme == ZF_LZ77 || ch.dtype == ZF_BYTES) return 1;
+    return (ch.rows + tile_rows - 1) / tile_rows;
+}
+
+// ------------------------------------------------------------------ validation
+namespace {
+template <class T> T rd(const uint8_t* p) { T v; memcpy(&v, p, sizeof(T)); return v; }
+
+bool fail(std::string* why, const std::string& m) {
+    if (why) *why = m;
+    return false;
+}
+
+bool check_chunk(const uint8_t* c, uint64_t len, int scheme, int dtype, uint32_t rows, std::string* why) {
+    if (len < kChunkHeader || len % 16) return fail(why, "chunk blob too short or not a multiple of 16");
+    if (rd<uint32_t>(c) != kChunkMagic) return fail(why, "bad chunk magic");
+    if (c[4] != scheme || c[5] != dtype) return fail(why, "chunk scheme/dtype differ from the column");
+    if (rd<uint32_t>(c + 8) != rows) return fail(why, "chunk rows differ from the directory");
+    uint32_t b = c[6], n_aux = rd<uint32_t>(c + 12);
+    uint32_t off[3], ln[3];
+    for (int s = 0; s < 3; s++) {
+        off[s] = rd<uint32_t>(c + 24 + 4 * s);
+        ln[s] = rd<uint32_t>(c + 36 + 4 * s);
+    }
+    int nsec = 0;
+    switch (scheme) {
+    case ZF_RAW: case ZF_FOR_BP: nsec = 1; break;
+    case ZF_DICT_BP: nsec = 2; break;
+    case ZF_DELTA_BP: nsec = 2; break;
+    case ZF_RLE: nsec = 3; break;
+    case ZF_LZ77: nsec = (c[7] & 1) ? 1 : 2; break;
+    default: return fail(why, "unknown scheme");
+    }
+    for (int s = 0; s < nsec; s++)
+        if (off[s] < kChunkHeader || off[s] % 16 || (uint64_t)off[s] + ln[s] > len)
+            return fail(why, "section outside the blob or misaligned");
+    uint32_t sz = dtype_size(dtype), wd = 8 * sz;
+    switch (scheme) {
+    case ZF_RAW:
+        if (ln[0] != (uint64_t)rows * sz) return fail(why, "raw section length");
+        break;
+    case ZF_FOR_BP:
+        if (b > wd || ln[0] != packed_bytes(rows, b)) return fail(why, "FOR width or payload length");
+        break;
+    case ZF_DICT_BP:
+        if (n_aux > kMaxDict || (rows && n_aux == 0) || ln[0] != (uint64_t)n_aux * sz ||
+            b != (n_aux ? bits_of(n_aux - 1) : 0) || ln[1] != packed_bytes(rows, b))
+            return fail(why, "dictionary header");
+        break;
+    case ZF_DELTA_BP: {
+        uint32_t nb = (rows + kDeltaBlock - 1) / kDeltaBlock;
+        if (n_aux != nb || ln[0] != (uint64_t)nb * kDeltaEntry) return fail(why, "delta block table");
+        for (uint32_t k = 0; k < nb; k++) {
+            const uint8_t* e = c + off[0] + (uint64_t)k * kDeltaEntry;
+            uint32_t po = rd<uint32_t>(e + 16), bk = e[20];
+            uint32_t mk = std::min(kDeltaBlock, rows - k * kDeltaBlock);
+            if (bk > wd || po % 16 || (uint64_t)po + align16(packed_bytes(mk, bk)) > ln[1])
+                return fail(why, "delta block entry");
+        }
+        break;
+    }
+    case ZF_RLE:
+        if (n_aux > rows || (rows && !n_aux) || ln[0] != (uint64_t)n_aux * sz || ln[1] != 4ull * n_aux ||
+            ln[2] != 8ull * ((rows + kRleDirRows - 1) / kRleDirRows))
+            return fail(why, "RLE sections");
+        break;
+    case ZF_LZ77:
+        if (rows > kLzBlock) return fail(why, "LZ77 block above 64 KiB");
+        if ((c[7] & 1) && ln[0] != rows) return fail(why, "raw LZ77 block length");
+        break;
+    }
+    return true;
+}
+}  // namespace
+
+zf_status parse_serialized(zf_compressed* c, std::string* why) {
+    c->chunks.clear();
+    c->nparts = 0;
+    c->raw_bytes = 0;
+    uint64_t pos = 0;
+    for (int p = 0; p < 2; p++) {
+        const uint8_t* h = c->host + pos;
+        if (pos + kColHeader > c->len || rd<uint32_t>(h) != kColMagic || rd<uint16_t>(h + 4) != 1) {
+            fail(why, "bad column header");
+            return ZF_ECORRUPT;
+        }
+        PartInfo& pi = c->parts[p];
+        pi.off = pos;
+        pi.scheme = h[6];
+        pi.dtype = h[7];
+        uint32_t nch = rd<uint32_t>(h + 8);
+        pi.chunk_rows = rd<uint32_t>(h + 12);
+        pi.n_rows = rd<uint64_t>(h + 16);
+        pi.len = rd<uint64_t>(h + 32);
+        uint32_t flags = rd<uint32_t>(h + 40);
+        if (!scheme_fits(pi.scheme, pi.dtype) || pi.len > c->len - pos ||
+            kColHeader + (uint64_t)kDirEntry * nch > pi.len || pi.chunk_rows == 0 ||
+            (uint64_t)nch != (pi.n_rows + pi.chunk_rows - 1) / pi.chunk_rows ||
+            rd<uint64_t>(h + 24) != pi.n_rows * dtype_size(pi.dtype)) {
+            fail(why, "inconsistent column header");
+            return ZF_ECORRUPT;
+        }
+        if (pi.dtype != ZF_BYTES && pi.chunk_rows % 1024) {
+            fail(why, "chunk_rows must be a multiple of 1024");
+            return ZF_ECORRUPT;
+        }
+        if (pi.dtype == ZF_BYTES && pi.chunk_rows != kLzBlock) {
+            fail(why, "byte chunks must be 65536 bytes");
+            return ZF_ECORRUPT;
+        }
+        pi.first_chunk = (uint32_t)c->chunks.size();
+        pi.n_chunks = nch;
+        uint64_t expect = kColHeader + (uint64_t)kDirEntry * nch;
+        for (uint32_t k = 0; k < nch; k++) {
+            const uint8_t* d = h + kColHeader + (uint64_t)kDirEntry * k;
+            ChunkInfo ch{};
+            ch.off = rd<uint64_t>(d);
+            ch.bytes = rd<uint64_t>(d + 8);
+            ch.row0 = rd<uint64_t>(d + 16);
+            ch.rows = rd<uint32_t>(d + 24);
+            if (ch.off != expect || ch.bytes > pi.len - ch.off || ch.row0 != (uint64_t)k * pi.chunk_rows ||
+                ch.rows != std::min<uint64_t>(pi.chunk_rows, pi.n_rows - ch.row0)) {
+                fail(why, "bad chunk directory entry");
+                return ZF_ECORRUPT;
+            }
+            expect += ch.bytes;
+            if (!check_chunk(h + ch.off, ch.bytes, pi.scheme, pi.dtype, ch.rows, why)) return ZF_ECORRUPT;
+            ch.off += pos;
+            ch.scheme = (uint8_t)pi.scheme;
+            ch.dtype = (uint8_t)pi.dtype;
+            ch.part = (uint8_t)p;
+            c->chunks.push_back(ch);
+        }
+        if (expect != pi.len) {
+            fail(why, "column length differs from its chunks");
+            return ZF_ECORRUPT;
+        }
+        c->raw_bytes += pi.n_rows * dtype_size(pi.dtype);
+        c->nparts = p + 1;
+        pos += pi.len;
+        if (!(pi.dtype == ZF_BYTES && (flags & 1))) break;
+        if (p == 1) break;
+    }
+    if (c->nparts == 2 && (c->parts[1].dtype != ZF_I32 || c->parts[1].n_rows == 0)) {
+        fail(why, "offsets part must be int32");
+        return ZF_ECORRUPT;
+    }
+    if (pos != c->len) {
+        fail(why, "trailing bytes after the column");
+        return ZF_ECORRUPT;
+    }
+    return ZF_OK;
+}
+
+}  // namespace zf

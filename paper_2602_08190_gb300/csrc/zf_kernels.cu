@@ -1,0 +1,305 @@
+// zf_kernels.cu -- decode kernels and their launchers.
+//
+//   tiles_kernel<SCHEME, DT, THREADS>  one (scheme, dtype) per launch; a
+//       persistent grid strides over the tiles of all chunks in the launch.
+//   tiles_kernel<-1, -1, THREADS>     the batched kernel: tiles of chunks of
+//       any scheme and dtype, handed out by an atomic work queue; the last
+//       CTA to finish resets the queue so the launch can be replayed from a
+//       CUDA graph.
+//   lz_kernel                         Non-Parallel pattern: one warp per
+//       64 KiB LZ77 block.
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <unordered_map>
+
+#include "zf_device.cuh"
+#include "zf_launch.h"
+
+namespace {
+
+struct LaunchArgs {
+    const ZfDevChunk* chunks;
+    uint32_t nchunks;
+    uint32_t ntiles;
+    uint32_t tile_rows;
+    uint32_t rle_cap;
+    uint32_t* err;
+    uint32_t* queue;   // [0] next tile, [1] CTAs done; null for static striding
+};
+
+__device__ __forceinline__ uint32_t find_chunk(const ZfDevChunk* ch, uint32_t n, uint32_t tile) {
+    uint32_t a = 0, z = n;
+    while (z - a > 1) {
+        uint32_t mid = (a + z) >> 1;
+        if (__ldg(&ch[mid].tile0) <= tile) a = mid;
+        else z = mid;
+    }
+    return a;
+}
+
+template <int SCHEME, int DT, int THREADS>
+__device__ __forceinline__ void decode_one(const ZfDevChunk& c, const zfd::Hdr& h, uint32_t r0, uint32_t nr,
+                                           uint32_t* sm, uint64_t* scan, const LaunchArgs& a) {
+    if constexpr (DT == ZF_I32) {
+        using T = int32_t;
+        if constexpr (SCHEME == ZF_FOR_BP || SCHEME == ZF_DICT_BP || SCHEME == ZF_RAW)
+            zfd::fp_tile<T, SCHEME>(c, h, r0, nr, sm, a.err);
+        else if constexpr (SCHEME == ZF_DELTA_BP)
+            zfd::delta_tile<T, zf::kDeltaBlock / THREADS>(c, h, r0, nr, sm, scan, a.err);
+        else if constexpr (SCHEME == ZF_RLE)
+            zfd::rle_tile<T>(c, h, r0, nr, sm, scan, a.rle_cap, a.err);
+    } else if constexpr (DT == ZF_I64) {
+        using T = int64_t;
+        if constexpr (SCHEME == ZF_FOR_BP || SCHEME == ZF_DICT_BP || SCHEME == ZF_RAW)
+            zfd::fp_tile<T, SCHEME>(c, h, r0, nr, sm, a.err);
+        else if constexpr (SCHEME == ZF_DELTA_BP)
+            zfd::delta_tile<T, zf::kDeltaBlock / THREADS>(c, h, r0, nr, sm, scan, a.err);
+        else if constexpr (SCHEME == ZF_RLE)
+            zfd::rle_tile<T>(c, h, r0, nr, sm, scan, a.rle_cap, a.err);
+    } else if constexpr (DT == ZF_BYTES && SCHEME == ZF_RAW) {
+        zfd::fp_tile<uint8_t, ZF_RAW>(c, h, r0, nr, sm, a.err);
+    }
+}
+
+template <int THREADS>
+__device__ __noinline__ void decode_mixed(const ZfDevChunk& c, const zfd::Hdr& h, uint32_t r0, uint32_t nr,
+                                          uint32_t* sm, uint64_t* scan, const LaunchArgs& a) {
+    const int key = c.scheme * 4 + c.dtype;
+    switch (key) {
+#define ZF_CASE(S, D) \
+    case S * 4 + D: decode_one<S, D, THREADS>(c, h, r0, nr, sm, scan, a); break;
+        ZF_CASE(ZF_RAW, ZF_I32) ZF_CASE(ZF_RAW, ZF_I64) ZF_CASE(ZF_RAW, ZF_BYTES)
+        ZF_CASE(ZF_FOR_BP, ZF_I32) ZF_CASE(ZF_FOR_BP, ZF_I64)
+        ZF_CASE(ZF_DICT_BP, ZF_I32) ZF_CASE(ZF_DICT_BP, ZF_I64)
+        ZF_CASE(ZF_DELTA_BP, ZF_I32) ZF_CASE(ZF_DELTA_BP, ZF_I64)
+        ZF_CASE(ZF_RLE, ZF_I32) ZF_CASE(ZF_RLE, ZF_I64)
+#undef ZF_CASE
+    default:
+        if (threadIdx.x == 0) zfd::report(a.err, ZF_EINVAL, c.chunk_id);
+    }
+}
+
+template <int SCHEME, int DT, int THREADS>
+__global__ void __launch_bounds__(THREADS) tiles_kernel(LaunchArgs a) {
+    extern __shared__ uint4 smem4[];
+    __shared__ uint64_t scan[33];
+    __shared__ uint32_t s_tile;
+    uint32_t* sm = reinterpret_cast<uint32_t*>(smem4);
+    uint32_t it = 0;
+    for (;;) {
+        uint32_t tile;
+        if (SCHEME < 0) {
+            if (threadIdx.x == 0) s_tile = atomicAdd(&a.queue[0], 1u);
+            __syncthreads();
+            tile = s_tile;
+            __syncthreads();
+        } else {
+            tile = blockIdx.x + it * gridDim.x;
+            it++;
+        }
+        if (tile >= a.ntiles) break;
+        const uint32_t k = find_chunk(a.chunks, a.nchunks, tile);
+        const ZfDevChunk c = a.chunks[k];
+        zfd::Hdr h;
+        zfd::load_hdr(c.blob, h);
+        const uint32_t r0 = (tile - c.tile0) * a.tile_rows;
+        if (h.rows != c.rows || r0 >= c.rows || (uint64_t)c.rows * (c.dtype == ZF_I64 ? 8 : c.dtype == ZF_I32 ? 4 : 1) > c.dst_cap) {
+            if (threadIdx.x == 0) zfd::report(a.err, ZF_ECORRUPT, c.chunk_id);
+            continue;
+        }
+        const uint32_t nr = min(a.tile_rows, c.rows - r0);
+        if constexpr (SCHEME < 0) decode_mixed<THREADS>(c, h, r0, nr, sm, scan, a);
+        else decode_one<SCHEME, DT, THREADS>(c, h, r0, nr, sm, scan, a);
+    }
+    if (SCHEME < 0 && threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&a.queue[1], 1u) == gridDim.x - 1) {
+            a.queue[0] = 0;
+            a.queue[1] = 0;
+            __threadfence();
+        }
+    }
+}
+
+// ---------------------------------------------------------------- LZ77 (Non-Parallel)
+__device__ __forceinline__ bool leb(const uint8_t* s, uint32_t len, uint32_t& p, uint32_t& v) {
+    v = 0;
+    for (uint32_t sh = 0; sh <= 28; sh += 7) {
+        if (p >= len) return false;
+        uint32_t byte = __ldg(s + p++);
+        v |= (byte & 0x7Fu) << sh;
+        if (!(byte & 0x80u)) return true;
+    }
+    return false;
+}
+
+// One warp decodes one block: every lane parses the same token (broadcast
+// loads), then the lanes copy the literals and the match 32 bytes at a time.
+// A match of offset `off` reads out[p - off + (k mod off)], which lies
+// before p, so all lanes copy in parallel even when the match overlaps
+// itself.
+__device__ void lz_block(const ZfDevChunk& c, uint32_t* err) {
+    const uint32_t lane = threadIdx.x & 31;
+    zfd::Hdr h;
+    zfd::load_hdr(c.blob, h);
+    uint8_t* dst = c.dst;
+    if (h.rows != c.rows || h.rows > zf::kLzBlock || h.rows > c.dst_cap) {
+        if (lane == 0) zfd::report(err, ZF_ECORRUPT, c.chunk_id);
+        return;
+    }
+    const uint8_t* s0 = c.blob + h.off[0];
+    if (h.flags & 1) {  // stored raw
+        uint32_t n16 = h.rows >> 4;
+        for (uint32_t i = lane; i < n16; i += 32)
+            reinterpret_cast<uint4*>(dst)[i] = zfd::ldg16(s0 + 16 * i);
+        for (uint32_t i = n16 * 16 + lane; i < h.rows; i += 32) dst[i] = s0[i];
+        return;
+    }
+    const uint8_t* lit = c.blob + h.off[1];
+    const uint32_t tl = h.len[0], ll_total = h.len[1], rows = h.rows;
+    uint32_t tp = 0, lp = 0, op = 0;
+    bool ok = true;
+    for (uint32_t t = 0; t < h.n_aux; t++) {
+        uint32_t ll;
+        if (!leb(s0, tl, tp, ll) || lp + ll > ll_total || op + ll > rows) { ok = false; break; }
+        for (uint32_t i = lane; i < ll; i += 32) dst[op + i] = __ldg(lit + lp + i);
+        op += ll;
+        lp += ll;
+        if (t + 1 == h.n_aux) break;
+        if (tp + 2 > tl) { ok = false; break; }
+        uint32_t off = (uint32_t)__ldg(s0 + tp) | ((uint32_t)__ldg(s0 + tp + 1) << 8);
+        tp += 2;
+        uint32_t ml;
+        if (!leb(s0, tl, tp, ml)) { ok = false; break; }
+        ml += zf::kLzMinMatch;
+        if (off == 0 || off > op || op + ml > rows) { ok = false; break; }
+        __syncwarp();
+        if (off >= ml) {
+            for (uint32_t k = lane; k < ml; k += 32) dst[op + k] = dst[op - off + k];
+        } else {
+            for (uint32_t k = lane; k < ml; k += 32) dst[op + k] = dst[op - off + k % off];
+        }
+        op += ml;
+        __syncwarp();
+    }
+    if (!ok || op != rows || tp != tl || lp != ll_total) {
+        if (lane == 0) zfd::report(err, ZF_ECORRUPT, c.chunk_id);
+    }
+}
+
+__global__ void __launch_bounds__(128) lz_kernel(const ZfDevChunk* chunks, uint32_t n, uint32_t* err) {
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t k = warp; k < n; k += nw) {
+        const ZfDevChunk c = chunks[k];
+        lz_block(c, err);
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------- launch table
+typedef void (*KernelFn)(LaunchArgs);
+
+template <int THREADS>
+KernelFn pick(int scheme, int dtype) {
+    switch (scheme * 4 + dtype) {
+#define ZF_K(S, D) \
+    case S * 4 + D: return tiles_kernel<S, D, THREADS>;
+        ZF_K(ZF_RAW, ZF_I32) ZF_K(ZF_RAW, ZF_I64) ZF_K(ZF_RAW, ZF_BYTES)
+        ZF_K(ZF_FOR_BP, ZF_I32) ZF_K(ZF_FOR_BP, ZF_I64)
+        ZF_K(ZF_DICT_BP, ZF_I32) ZF_K(ZF_DICT_BP, ZF_I64)
+        ZF_K(ZF_DELTA_BP, ZF_I32) ZF_K(ZF_DELTA_BP, ZF_I64)
+        ZF_K(ZF_RLE, ZF_I32) ZF_K(ZF_RLE, ZF_I64)
+#undef ZF_K
+    }
+    if (scheme < 0) return tiles_kernel<-1, -1, THREADS>;
+    return nullptr;
+}
+
+struct OccKey {
+    KernelFn fn;
+    uint32_t smem, threads;
+    bool operator==(const OccKey& o) const { return fn == o.fn && smem == o.smem && threads == o.threads; }
+};
+struct OccHash {
+    size_t operator()(const OccKey& k) const {
+        return std::hash<void*>()((void*)k.fn) ^ (k.smem * 2654435761u) ^ (k.threads * 40503u);
+    }
+};
+std::mutex g_occ_mu;
+std::unordered_map<OccKey, int, OccHash> g_occ;
+std::unordered_map<void*, bool> g_attr_set;
+
+}  // namespace
+
+namespace zf {
+
+uint32_t smem_bytes(int scheme, int dtype, uint32_t tile_rows) {
+    uint32_t sz = dtype == ZF_I64 ? 8 : dtype == ZF_I32 ? 4 : 1;
+    switch (scheme) {
+    case ZF_RAW: return 16;
+    case ZF_FOR_BP: case ZF_DICT_BP: return tile_rows * sz + 48;    // widest packing: b = 8*sz bits
+    case ZF_DELTA_BP: return kDeltaBlock * sz + 48;
+    case ZF_RLE: {
+        uint32_t cap = tile_rows + 1;
+        return ((cap + 3) & ~3u) * 4 + cap * sz + 16;
+    }
+    }
+    return 16;
+}
+
+uint32_t rle_cap(uint32_t tile_rows) { return tile_rows + 1; }
+
+cudaError_t launch_tiles(const TileLaunch& L, cudaStream_t s) {
+    KernelFn fn = nullptr;
+    switch (L.threads) {
+    case 128: fn = pick<128>(L.scheme, L.dtype); break;
+    case 256: fn = pick<256>(L.scheme, L.dtype); break;
+    case 512: fn = pick<512>(L.scheme, L.dtype); break;
+    default: return cudaErrorInvalidValue;
+    }
+    if (!fn) return cudaErrorInvalidValue;
+    int per_sm = (int)L.ctas_per_sm;
+    {
+        std::lock_guard<std::mutex> g(g_occ_mu);
+        if (!g_attr_set.count((void*)fn)) {
+            // allow the largest dynamic shared memory any launch of this kernel may ask for
+            int dev = 0, optin = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 optin - (int)(2 * 1024));
+            if (e != cudaSuccess) return e;
+            g_attr_set[(void*)fn] = true;
+        }
+        OccKey key{fn, L.smem, L.threads};
+        auto it = g_occ.find(key);
+        if (it == g_occ.end()) {
+            int occ = 0;
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, (int)L.threads, L.smem);
+            if (e != cudaSuccess) return e;
+            it = g_occ.emplace(key, occ).first;
+        }
+        if (per_sm <= 0 || per_sm > it->second) per_sm = it->second;
+    }
+    if (per_sm <= 0) return cudaErrorInvalidConfiguration;
+    uint64_t grid = (uint64_t)per_sm * (uint64_t)L.num_sms;
+    if (grid > L.ntiles) grid = L.ntiles;
+    if (grid == 0) return cudaSuccess;
+    LaunchArgs a{L.chunks, L.nchunks, L.ntiles, L.tile_rows, rle_cap(L.tile_rows), L.err,
+                 L.scheme < 0 ? L.queue : nullptr};
+    fn<<<(unsigned)grid, L.threads, L.smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lz(const ZfDevChunk* chunks, uint32_t n, uint32_t* err, int num_sms, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    uint32_t blocks = (n + 3) / 4;
+    uint32_t cap = (uint32_t)num_sms * 16;
+    if (blocks > cap) blocks = cap;
+    lz_kernel<<<blocks, 128, 0, s>>>(chunks, n, err);
+    return cudaGetLastError();
+}
+
+}  // namespace zf

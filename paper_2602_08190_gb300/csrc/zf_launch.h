@@ -1,0 +1,27 @@
+// zf_launch.h -- host-side launch descriptions of the decode kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "zf_internal.h"
+
+namespace zf {
+
+struct TileLaunch {
+    const ZfDevChunk* chunks;   // device descriptors of this launch
+    uint32_t nchunks;
+    uint32_t ntiles;
+    int scheme, dtype;          // -1, -1 for the batched work-queue kernel
+    uint32_t tile_rows;
+    uint32_t threads;
+    uint32_t ctas_per_sm;       // 0 = occupancy limit
+    uint32_t smem;
+    int num_sms;
+    uint32_t* err;
+    uint32_t* queue;
+};
+
+uint32_t smem_bytes(int scheme, int dtype, uint32_t tile_rows);
+cudaError_t launch_tiles(const TileLaunch& L, cudaStream_t s);
+cudaError_t launch_lz(const ZfDevChunk* chunks, uint32_t n, uint32_t* err, int num_sms, cudaStream_t s);
+
+}  // namespace zf

@@ -1,0 +1,636 @@
+// zf_runtime.cu -- the C ABI: contexts, the pinned-host chunk pipeline
+// (Section 3.3) and device-resident decode.
+//
+// Pipeline of zf_transfer_decompress: the chunks of all columns are cut into
+// stages of about kcfg.stage_bytes compressed bytes.  Stage s is copied by
+// cudaMemcpyAsync on the copy stream into staging slot s % nslots, after the
+// decode of the stage that last used the slot has finished (event
+// slot_free); the compute stream waits for the copy (event slot_copied) and
+// decodes the stage into the caller's buffers.  Copies of stage s+1.. run
+// while stage s decodes.  All descriptors of a call are built on the host and
+// copied once, ahead of the first stage.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "zf_internal.h"
+#include "zf_launch.h"
+
+namespace {
+constexpr uint32_t kMaxSlots = 8;
+}
+
+struct zf_resident {
+    uint8_t* d = nullptr;
+    uint64_t len = 0;
+    int device = 0;
+    int nparts = 0;
+    zf::PartInfo parts[2];
+    std::vector<zf::ChunkInfo> chunks;
+    uint64_t raw_bytes = 0;
+};
+
+struct zf_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t copy = nullptr, compute = nullptr;
+    bool own_copy = false, own_compute = false;
+    uint32_t nslots = 2;
+    uint64_t slot_req = 0;
+    uint8_t* slots[kMaxSlots] = {};
+    uint64_t slot_cap = 0;
+    cudaEvent_t ev_copied[kMaxSlots] = {}, ev_free[kMaxSlots] = {};
+    cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;
+    uint32_t* d_err = nullptr;     // [0] status bits, [1] first failing chunk, [2..3] work queue
+    uint32_t* h_err = nullptr;     // pinned copy of d_err[0..1]
+    ZfDevChunk* d_desc = nullptr;
+    ZfDevChunk* h_desc = nullptr;  // pinned
+    size_t desc_cap = 0;
+    std::vector<ZfDevChunk> resident_cache;   // descriptors last uploaded for resident decode
+    zf_kcfg kcfg{4096, 256, 0, 8u << 20, 0};
+    bool busy = false;
+    zf_status host_err = ZF_OK;
+    std::string last_error;
+    zf_stats st{};
+};
+
+namespace {
+
+zf_status cuda_fail(zf_ctx* ctx, cudaError_t e, const char* what) {
+    if (ctx) ctx->last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return ZF_ECUDA;
+}
+
+#define ZF_CU(ctx, call)                                   \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+zf_kcfg effective_kcfg(const zf_ctx* ctx) {
+    zf_kcfg k = ctx->kcfg;
+    if (!k.tile_rows) k.tile_rows = 4096;
+    if (!k.threads) k.threads = 256;
+    if (!k.stage_bytes) k.stage_bytes = 8u << 20;
+    return k;
+}
+
+bool kcfg_valid(const zf_kcfg& k) {
+    return k.tile_rows % 1024 == 0 && k.tile_rows >= 1024 && k.tile_rows <= zf::kMaxTileRows &&
+           (k.threads == 128 || k.threads == 256 || k.threads == 512) && k.ctas_per_sm <= 64;
+}
+
+// One decode unit of a call: a chunk with its host source, device output and part.
+struct Work {
+    const uint8_t* host;      // serialized bytes (transfer) or null (resident)
+    const uint8_t* dev;       // device address of the chunk blob (slot or resident copy)
+    const zf::ChunkInfo* ch;
+    uint8_t* dst;
+    uint64_t cap;
+    uint32_t id;
+};
+
+// Build the output mapping for the columns of one call.
+template <class Col>
+zf_status map_outputs(zf_ctx* ctx, const Col* const* cols, uint32_t ncols, void* const* d_out,
+                      const uint64_t* d_out_bytes, std::vector<Work>& work, uint64_t* raw, uint64_t* comp,
+                      const uint8_t* (*hostp)(const Col*), const uint8_t* (*devp)(const Col*)) {
+    uint32_t o = 0;
+    uint32_t id = 0;
+    for (uint32_t c = 0; c < ncols; c++) {
+        const Col* col = cols[c];
+        if (!col) {
+            ctx->last_error = "null column";
+            return ZF_EINVAL;
+        }
+        for (int p = 0; p < col->nparts; p++, o++) {
+            const zf::PartInfo& pi = col->parts[p];
+            uint8_t* out = (uint8_t*)d_out[o];
+            uint64_t need = pi.n_rows * zf::dtype_size(pi.dtype);
+            if (need && (!out || d_out_bytes[o] < need || ((uintptr_t)out & 15))) {
+                ctx->last_error = "output buffer missing, too small or not 16-byte aligned";
+                return ZF_EINVAL;
+            }
+            for (uint32_t k = 0; k < pi.n_chunks; k++) {
+                const zf::ChunkInfo& ch = col->chunks[pi.first_chunk + k];
+                uint64_t off = ch.row0 * zf::dtype_size(pi.dtype);
+                const uint8_t* dv = devp(col);
+                work.push_back({hostp(col), dv ? dv + ch.off : nullptr, &ch, out + off, d_out_bytes[o] - off, id++});
+                *comp += ch.bytes;
+            }
+            *raw += need;
+        }
+    }
+    return ZF_OK;
+}
+
+const uint8_t* host_of(const zf_compressed* c) { return c->host; }
+const uint8_t* nodev_of(const zf_compressed*) { return nullptr; }
+const uint8_t* nohost_of(const zf_resident*) { return nullptr; }
+const uint8_t* dev_of(const zf_resident* r) { return r->d; }
+
+zf_status ensure_desc(zf_ctx* ctx, size_t n) {
+    if (n <= ctx->desc_cap) return ZF_OK;
+    size_t cap = std::max<size_t>(n, 2 * ctx->desc_cap);
+    if (ctx->d_desc) cudaFree(ctx->d_desc);
+    if (ctx->h_desc) cudaFreeHost(ctx->h_desc);
+    ctx->d_desc = nullptr;
+    ctx->h_desc = nullptr;
+    ctx->desc_cap = 0;
+    ctx->resident_cache.clear();
+    if (cudaMalloc(&ctx->d_desc, cap * sizeof(ZfDevChunk)) != cudaSuccess ||
+        cudaHostAlloc(&ctx->h_desc, cap * sizeof(ZfDevChunk), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->last_error = "descriptor buffers";
+        return ZF_ENOMEM;
+    }
+    ctx->desc_cap = cap;
+    return ZF_OK;
+}
+
+zf_status ensure_slots(zf_ctx* ctx, uint64_t bytes) {
+    if (bytes <= ctx->slot_cap) return ZF_OK;
+    for (uint32_t s = 0; s < kMaxSlots; s++)
+        if (ctx->slots[s]) {
+            cudaFree(ctx->slots[s]);
+            ctx->slots[s] = nullptr;
+        }
+    ctx->slot_cap = 0;
+    for (uint32_t s = 0; s < ctx->nslots; s++)
+        if (cudaMalloc(&ctx->slots[s], bytes) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->last_error = "staging slots";
+            return ZF_ENOMEM;
+        }
+    ctx->slot_cap = bytes;
+    return ZF_OK;
+}
+
+// A group of chunks decoded by one launch.
+struct Group {
+    int scheme, dtype;   // (-1, -1): batched work-queue kernel; (LZ77, BYTES): LZ kernel
+    uint32_t first, count, ntiles;
+};
+
+// Append descriptors of works[b, e) to `desc`, grouped for launching.
+void build_groups(const std::vector<Work>& w, size_t b, size_t e, const zf_kcfg& k, std::vector<ZfDevChunk>& desc,
+                  std::vector<Group>& groups) {
+    const bool batched = k.flags & ZF_KCFG_BATCHED;
+    std::vector<std::pair<int, int>> keys;
+    for (size_t i = b; i < e; i++) {
+        int s = w[i].ch->scheme, d = w[i].ch->dtype;
+        if (s == ZF_LZ77) {
+            d = ZF_BYTES;
+        } else if (batched) {
+            s = -1;
+            d = -1;
+        }
+        if (std::find(keys.begin(), keys.end(), std::make_pair(s, d)) == keys.end()) keys.push_back({s, d});
+    }
+    for (auto& key : keys) {
+        Group g{key.first, key.second, (uint32_t)desc.size(), 0, 0};
+        for (size_t i = b; i < e; i++) {
+            int s = w[i].ch->scheme, d = w[i].ch->dtype;
+            bool lz = s == ZF_LZ77;
+            bool match = lz ? key.first == ZF_LZ77 : (key.first < 0 ? true : (key.first == s && key.second == d));
+            if (!match || (key.first < 0 && lz)) continue;
+            ZfDevChunk dc{};
+            dc.blob = w[i].dev;
+            dc.dst = w[i].dst;
+            dc.dst_cap = w[i].cap;
+            dc.rows = w[i].ch->rows;
+            dc.tile0 = g.ntiles;
+            dc.ntiles = zf::tiles_of(*w[i].ch, k.tile_rows);
+            dc.blob_bytes = (uint32_t)w[i].ch->bytes;
+            dc.chunk_id = w[i].id;
+            dc.scheme = (uint8_t)s;
+            dc.dtype = (uint8_t)d;
+            g.ntiles += dc.ntiles;
+            desc.push_back(dc);
+            g.count++;
+        }
+        if (g.count) groups.push_back(g);
+    }
+}
+
+zf_status launch_groups(zf_ctx* ctx, const std::vector<Group>& groups, const std::vector<ZfDevChunk>& desc,
+                        const zf_kcfg& k) {
+    for (const Group& g : groups) {
+        const ZfDevChunk* dchunks = ctx->d_desc + g.first;
+        cudaError_t e;
+        if (g.scheme == ZF_LZ77) {
+            e = zf::launch_lz(dchunks, g.count, ctx->d_err, ctx->num_sms, ctx->compute);
+        } else {
+            uint32_t smem = 16;
+            if (g.scheme < 0) {
+                for (uint32_t i = g.first; i < g.first + g.count; i++)
+                    smem = std::max(smem, zf::smem_bytes(desc[i].scheme, desc[i].dtype, k.tile_rows));
+            } else {
+                smem = zf::smem_bytes(g.scheme, g.dtype, k.tile_rows);
+            }
+            zf::TileLaunch L{dchunks, g.count, g.ntiles, g.scheme, g.dtype, k.tile_rows, k.threads,
+                             k.ctas_per_sm, smem, ctx->num_sms, ctx->d_err, ctx->d_err + 2};
+            e = zf::launch_tiles(L, ctx->compute);
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "decode launch");
+        ctx->st.n_launches++;
+    }
+    return ZF_OK;
+}
+
+zf_status begin_call(zf_ctx* ctx) {
+    if (ctx->busy) {
+        ctx->last_error = "previous call not synced";
+        return ZF_EBUSY;
+    }
+    ZF_CU(ctx, cudaSetDevice(ctx->device));
+    ctx->st = zf_stats{};
+    ctx->host_err = ZF_OK;
+    return ZF_OK;
+}
+
+zf_status finish_enqueue(zf_ctx* ctx) {
+    ZF_CU(ctx, cudaMemcpyAsync(ctx->h_err, ctx->d_err, 8, cudaMemcpyDeviceToHost, ctx->compute));
+    ZF_CU(ctx, cudaEventRecord(ctx->ev_t1, ctx->compute));
+    ctx->busy = true;
+    return ZF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+zf_status zf_ctx_create(int device, void* copy_stream, void* compute_stream, zf_ctx** out) {
+    if (!out) return ZF_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return ZF_ECUDA;
+    }
+    zf_ctx* ctx = new (std::nothrow) zf_ctx();
+    if (!ctx) return ZF_ENOMEM;
+    ctx->device = device;
+    auto fail = [&](zf_status s) {
+        zf_ctx_destroy(ctx);
+        return s;
+    };
+    if (cudaSetDevice(device) != cudaSuccess) return fail(ZF_ECUDA);
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (copy_stream) ctx->copy = (cudaStream_t)copy_stream;
+    else if (cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking) == cudaSuccess) ctx->own_copy = true;
+    else return fail(ZF_ECUDA);
+    if (compute_stream) ctx->compute = (cudaStream_t)compute_stream;
+    else if (cudaStreamCreateWithFlags(&ctx->compute, cudaStreamNonBlocking) == cudaSuccess) ctx->own_compute = true;
+    else return fail(ZF_ECUDA);
+    for (uint32_t s = 0; s < kMaxSlots; s++)
+        if (cudaEventCreateWithFlags(&ctx->ev_copied[s], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev_free[s], cudaEventDisableTiming) != cudaSuccess)
+            return fail(ZF_ECUDA);
+    if (cudaEventCreate(&ctx->ev_t0) != cudaSuccess || cudaEventCreate(&ctx->ev_t1) != cudaSuccess)
+        return fail(ZF_ECUDA);
+    if (cudaMalloc(&ctx->d_err, 64) != cudaSuccess || cudaMemset(ctx->d_err, 0, 64) != cudaSuccess)
+        return fail(ZF_ENOMEM);
+    uint32_t init[2] = {0, 0xFFFFFFFFu};
+    if (cudaMemcpy(ctx->d_err, init, 8, cudaMemcpyHostToDevice) != cudaSuccess) return fail(ZF_ECUDA);
+    if (cudaHostAlloc(&ctx->h_err, 64, cudaHostAllocDefault) != cudaSuccess) return fail(ZF_ENOMEM);
+    memset(ctx->h_err, 0, 64);
+    *out = ctx;
+    return ZF_OK;
+}
+
+zf_status zf_ctx_destroy(zf_ctx* ctx) {
+    if (!ctx) return ZF_OK;
+    cudaSetDevice(ctx->device);
+    if (ctx->compute) cudaStreamSynchronize(ctx->compute);
+    if (ctx->copy) cudaStreamSynchronize(ctx->copy);
+    for (uint32_t s = 0; s < kMaxSlots; s++) {
+        if (ctx->slots[s]) cudaFree(ctx->slots[s]);
+        if (ctx->ev_copied[s]) cudaEventDestroy(ctx->ev_copied[s]);
+        if (ctx->ev_free[s]) cudaEventDestroy(ctx->ev_free[s]);
+    }
+    if (ctx->ev_t0) cudaEventDestroy(ctx->ev_t0);
+    if (ctx->ev_t1) cudaEventDestroy(ctx->ev_t1);
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->h_err) cudaFreeHost(ctx->h_err);
+    if (ctx->d_desc) cudaFree(ctx->d_desc);
+    if (ctx->h_desc) cudaFreeHost(ctx->h_desc);
+    if (ctx->own_copy) cudaStreamDestroy(ctx->copy);
+    if (ctx->own_compute) cudaStreamDestroy(ctx->compute);
+    delete ctx;
+    return ZF_OK;
+}
+
+const char* zf_last_error(const zf_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+zf_status zf_ctx_set_kcfg(zf_ctx* ctx, const zf_kcfg* k) {
+    if (!ctx || !k) return ZF_EINVAL;
+    zf_kcfg n = *k;
+    if (!n.tile_rows) n.tile_rows = 4096;
+    if (!n.threads) n.threads = 256;
+    if (!n.stage_bytes) n.stage_bytes = 8u << 20;
+    if (!kcfg_valid(n)) {
+        ctx->last_error = "invalid kernel geometry";
+        return ZF_EINVAL;
+    }
+    ctx->kcfg = n;
+    return ZF_OK;
+}
+
+zf_status zf_ctx_set_ring(zf_ctx* ctx, uint32_t slots, uint64_t slot_bytes) {
+    if (!ctx || slots < 2 || slots > kMaxSlots) return ZF_EINVAL;
+    if (ctx->busy) return ZF_EBUSY;
+    cudaSetDevice(ctx->device);
+    for (uint32_t s = 0; s < kMaxSlots; s++)
+        if (ctx->slots[s]) {
+            cudaFree(ctx->slots[s]);
+            ctx->slots[s] = nullptr;
+        }
+    ctx->slot_cap = 0;
+    ctx->nslots = slots;
+    ctx->slot_req = slot_bytes;
+    return ZF_OK;
+}
+
+zf_status zf_compress_host(const zf_plan_t* plan, const zf_column* col, zf_compressed** out) {
+    if (!plan || !col || !out) return ZF_EINVAL;
+    *out = nullptr;
+    std::string why;
+    return zf::encode_column(*plan, *col, out, &why);
+}
+
+zf_status zf_compressed_info(const zf_compressed* c, uint64_t* raw, uint64_t* comp, uint32_t* nch) {
+    if (!c) return ZF_EINVAL;
+    if (raw) *raw = c->raw_bytes;
+    if (comp) *comp = c->len;
+    if (nch) *nch = (uint32_t)c->chunks.size();
+    return ZF_OK;
+}
+
+zf_status zf_compressed_free(zf_compressed* c) {
+    zf::free_compressed(c);
+    return ZF_OK;
+}
+
+zf_status zf_compressed_bytes(const zf_compressed* c, const uint8_t** data, uint64_t* len) {
+    if (!c || !data || !len) return ZF_EINVAL;
+    *data = c->host;
+    *len = c->len;
+    return ZF_OK;
+}
+
+zf_status zf_compressed_from_bytes(const uint8_t* data, uint64_t len, zf_compressed** out) {
+    if (!data || !out || len < zf::kColHeader) return ZF_EINVAL;
+    *out = nullptr;
+    auto* c = new (std::nothrow) zf_compressed();
+    if (!c) return ZF_ENOMEM;
+    int ndev = 0;
+    void* p = nullptr;
+    if (cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0) {
+        if (cudaHostAlloc(&p, len, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return ZF_ENOMEM;
+        }
+        c->pinned = true;
+    } else {
+        cudaGetLastError();
+        p = malloc(len);
+        if (!p) {
+            delete c;
+            return ZF_ENOMEM;
+        }
+    }
+    c->host = (uint8_t*)p;
+    c->len = len;
+    memcpy(c->host, data, len);
+    std::string why;
+    zf_status st = zf::parse_serialized(c, &why);
+    if (st) {
+        zf::free_compressed(c);
+        return st;
+    }
+    *out = c;
+    return ZF_OK;
+}
+
+zf_status zf_transfer_decompress(zf_ctx* ctx, const zf_compressed* const* cols, uint32_t ncols,
+                                 void* const* d_out, const uint64_t* d_out_bytes) {
+    if (!ctx || (ncols && (!cols || !d_out || !d_out_bytes))) return ZF_EINVAL;
+    zf_status st = begin_call(ctx);
+    if (st) return st;
+    const zf_kcfg k = effective_kcfg(ctx);
+    std::vector<Work> work;
+    uint64_t raw = 0, comp = 0;
+    st = map_outputs<zf_compressed>(ctx, cols, ncols, d_out, d_out_bytes, work, &raw, &comp, host_of, nodev_of);
+    if (st) return st;
+    // Stages: consecutive chunks up to stage_bytes of compressed bytes.
+    std::vector<std::pair<size_t, size_t>> stages;
+    uint64_t max_stage = 0;
+    for (size_t i = 0; i < work.size();) {
+        size_t j = i;
+        uint64_t bytes = 0;
+        while (j < work.size() && (j == i || bytes + work[j].ch->bytes <= k.stage_bytes)) bytes += work[j++].ch->bytes;
+        stages.push_back({i, j});
+        max_stage = std::max(max_stage, bytes);
+        i = j;
+    }
+    st = ensure_slots(ctx, std::max<uint64_t>(std::max(max_stage, ctx->slot_req), 16));
+    if (st) return st;
+    // Copy plan: runs of chunks contiguous in one host buffer become one copy;
+    // each chunk's blob lands at its offset inside the stage's slot.
+    struct Piece { const uint8_t* src; uint64_t bytes; uint64_t slot_off; };
+    std::vector<std::vector<Piece>> pieces(stages.size());
+    for (size_t s = 0; s < stages.size(); s++) {
+        auto [b, e] = stages[s];
+        uint8_t* slot = ctx->slots[s % ctx->nslots];
+        uint64_t pos = 0;
+        for (size_t i = b; i < e;) {
+            size_t j = i + 1;
+            while (j < e && work[j].host == work[i].host && work[j].ch->off == work[j - 1].ch->off + work[j - 1].ch->bytes) j++;
+            uint64_t bytes = work[j - 1].ch->off + work[j - 1].ch->bytes - work[i].ch->off;
+            pieces[s].push_back({work[i].host + work[i].ch->off, bytes, pos});
+            for (size_t q = i; q < j; q++) work[q].dev = slot + pos + (work[q].ch->off - work[i].ch->off);
+            pos += bytes;
+            i = j;
+        }
+    }
+    std::vector<ZfDevChunk> desc;
+    std::vector<std::vector<Group>> groups(stages.size());
+    for (size_t s = 0; s < stages.size(); s++) build_groups(work, stages[s].first, stages[s].second, k, desc, groups[s]);
+    st = ensure_desc(ctx, std::max<size_t>(desc.size(), 1));
+    if (st) return st;
+    ctx->resident_cache.clear();
+    if (!desc.empty()) memcpy(ctx->h_desc, desc.data(), desc.size() * sizeof(ZfDevChunk));
+    ZF_CU(ctx, cudaEventRecord(ctx->ev_t0, ctx->copy));
+    ZF_CU(ctx, cudaMemsetAsync(ctx->d_err, 0, 4, ctx->copy));
+    ZF_CU(ctx, cudaMemsetAsync(ctx->d_err + 1, 0xFF, 4, ctx->copy));
+    if (!desc.empty())
+        ZF_CU(ctx, cudaMemcpyAsync(ctx->d_desc, ctx->h_desc, desc.size() * sizeof(ZfDevChunk),
+                                   cudaMemcpyHostToDevice, ctx->copy));
+    if (stages.empty()) ZF_CU(ctx, cudaEventRecord(ctx->ev_copied[0], ctx->copy));
+    if (stages.empty()) ZF_CU(ctx, cudaStreamWaitEvent(ctx->compute, ctx->ev_copied[0], 0));
+    for (size_t s = 0; s < stages.size(); s++) {
+        uint32_t slot = (uint32_t)(s % ctx->nslots);
+        if (s >= ctx->nslots) ZF_CU(ctx, cudaStreamWaitEvent(ctx->copy, ctx->ev_free[slot], 0));
+        for (const Piece& p : pieces[s])
+            ZF_CU(ctx, cudaMemcpyAsync(ctx->slots[slot] + p.slot_off, p.src, p.bytes, cudaMemcpyHostToDevice,
+                                       ctx->copy));
+        ZF_CU(ctx, cudaEventRecord(ctx->ev_copied[slot], ctx->copy));
+        ZF_CU(ctx, cudaStreamWaitEvent(ctx->compute, ctx->ev_copied[slot], 0));
+        st = launch_groups(ctx, groups[s], desc, k);
+        if (st) {
+            // nothing may still read the descriptor or staging buffers after an error return
+            cudaStreamSynchronize(ctx->copy);
+            cudaStreamSynchronize(ctx->compute);
+            return st;
+        }
+        ZF_CU(ctx, cudaEventRecord(ctx->ev_free[slot], ctx->compute));
+    }
+    ctx->st.raw_bytes = raw;
+    ctx->st.comp_bytes = comp;
+    ctx->st.n_chunks = (uint32_t)work.size();
+    ctx->st.n_stages = (uint32_t)stages.size();
+    return finish_enqueue(ctx);
+}
+
+zf_status zf_sync(zf_ctx* ctx, zf_stats* stats) {
+    if (!ctx) return ZF_EINVAL;
+    if (!ctx->busy) {
+        if (stats) *stats = ctx->st;
+        return ctx->host_err;
+    }
+    cudaSetDevice(ctx->device);
+    ctx->busy = false;
+    cudaError_t e = cudaEventSynchronize(ctx->ev_t1);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "zf_sync");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ctx->ev_t0, ctx->ev_t1);
+    ctx->st.total_ms = ms;
+    ctx->st.device_error = ctx->h_err[0];
+    if (stats) *stats = ctx->st;
+    if (ctx->h_err[0]) {
+        uint32_t bits = ctx->h_err[0];
+        ctx->last_error = "device decoder reported an error in chunk " + std::to_string(ctx->h_err[1]);
+        if (bits & (1u << ZF_ECORRUPT)) return ZF_ECORRUPT;
+        if (bits & (1u << ZF_ETIMEOUT)) return ZF_ETIMEOUT;
+        return ZF_EINVAL;
+    }
+    return ZF_OK;
+}
+
+zf_status zf_upload(zf_ctx* ctx, const zf_compressed* c, zf_resident** out) {
+    if (!ctx || !c || !out) return ZF_EINVAL;
+    *out = nullptr;
+    if (ctx->busy) return ZF_EBUSY;
+    ZF_CU(ctx, cudaSetDevice(ctx->device));
+    auto* r = new (std::nothrow) zf_resident();
+    if (!r) return ZF_ENOMEM;
+    if (cudaMalloc(&r->d, std::max<uint64_t>(c->len, 16)) != cudaSuccess) {
+        cudaGetLastError();
+        delete r;
+        ctx->last_error = "device memory for a resident column";
+        return ZF_ENOMEM;
+    }
+    cudaError_t e = cudaMemcpy(r->d, c->host, c->len, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(r->d);
+        delete r;
+        return cuda_fail(ctx, e, "zf_upload copy");
+    }
+    r->len = c->len;
+    r->device = ctx->device;
+    r->nparts = c->nparts;
+    r->parts[0] = c->parts[0];
+    r->parts[1] = c->parts[1];
+    r->chunks = c->chunks;
+    r->raw_bytes = c->raw_bytes;
+    *out = r;
+    return ZF_OK;
+}
+
+zf_status zf_resident_free(zf_resident* r) {
+    if (!r) return ZF_OK;
+    cudaSetDevice(r->device);
+    if (r->d) cudaFree(r->d);
+    delete r;
+    return ZF_OK;
+}
+
+zf_status zf_decompress_resident(zf_ctx* ctx, const zf_resident* const* cols, uint32_t ncols,
+                                 void* const* d_out, const uint64_t* d_out_bytes) {
+    if (!ctx || (ncols && (!cols || !d_out || !d_out_bytes))) return ZF_EINVAL;
+    zf_status st = begin_call(ctx);
+    if (st) return st;
+    const zf_kcfg k = effective_kcfg(ctx);
+    std::vector<Work> work;
+    uint64_t raw = 0, comp = 0;
+    st = map_outputs<zf_resident>(ctx, cols, ncols, d_out, d_out_bytes, work, &raw, &comp, nohost_of, dev_of);
+    if (st) return st;
+    std::vector<ZfDevChunk> desc;
+    std::vector<Group> groups;
+    build_groups(work, 0, work.size(), k, desc, groups);
+    ZF_CU(ctx, cudaEventRecord(ctx->ev_t0, ctx->compute));
+    ZF_CU(ctx, cudaMemsetAsync(ctx->d_err, 0, 4, ctx->compute));
+    ZF_CU(ctx, cudaMemsetAsync(ctx->d_err + 1, 0xFF, 4, ctx->compute));
+    bool same = desc.size() == ctx->resident_cache.size() &&
+                (desc.empty() || memcmp(desc.data(), ctx->resident_cache.data(), desc.size() * sizeof(ZfDevChunk)) == 0);
+    if (!same) {
+        st = ensure_desc(ctx, std::max<size_t>(desc.size(), 1));
+        if (st) return st;
+        if (!desc.empty()) {
+            memcpy(ctx->h_desc, desc.data(), desc.size() * sizeof(ZfDevChunk));
+            ZF_CU(ctx, cudaMemcpyAsync(ctx->d_desc, ctx->h_desc, desc.size() * sizeof(ZfDevChunk),
+                                       cudaMemcpyHostToDevice, ctx->compute));
+        }
+        ctx->resident_cache = desc;
+    }
+    st = launch_groups(ctx, groups, desc, k);
+    if (st) {
+        cudaStreamSynchronize(ctx->compute);
+        return st;
+    }
+    ctx->st.raw_bytes = raw;
+    ctx->st.comp_bytes = comp;
+    ctx->st.n_chunks = (uint32_t)work.size();
+    ctx->st.n_stages = 1;
+    return finish_enqueue(ctx);
+}
+
+}  // extern "C"
+
+namespace zf {
+int heuristic_scheme(const zf_column& col, uint32_t chunk_rows);
+}
+
+extern "C" zf_status zf_plan(zf_ctx* ctx, const zf_column* col, const zf_plan_opts* opts, zf_plan_t* out) {
+    if (!col || !out) return ZF_EINVAL;
+    if (col->dtype != ZF_I32 && col->dtype != ZF_I64 && col->dtype != ZF_BYTES) return ZF_EINVAL;
+    zf_plan_opts o{-1, 0, 0, -1};
+    if (opts) o = *opts;
+    zf_plan_t p{};
+    p.label = -1;
+    p.offsets_scheme = o.offsets_scheme < 0 ? ZF_DELTA_BP : o.offsets_scheme;
+    p.chunk_rows = col->dtype == ZF_BYTES ? zf::kLzBlock : (o.chunk_rows ? o.chunk_rows : (1u << 20));
+    if (col->dtype != ZF_BYTES && (p.chunk_rows % 1024 || p.chunk_rows > (1u << 30))) {
+        if (ctx) ctx->last_error = "chunk_rows must be a multiple of 1024 and at most 2^30";
+        return ZF_EINVAL;
+    }
+    p.kcfg = ctx ? ctx->kcfg : zf_kcfg{4096, 256, 0, 8u << 20, 0};
+    if (o.scheme >= 0) {
+        if (o.scheme >= ZF_NSCHEMES) return ZF_EINVAL;
+        p.scheme = o.scheme;
+    } else if (o.selector == 0) {
+        p.scheme = zf::heuristic_scheme(*col, p.chunk_rows);
+    } else {
+        if (ctx) ctx->last_error = "selector not available";
+        return ZF_EUNSUPPORTED;
+    }
+    *out = p;
+    return ZF_OK;
+}

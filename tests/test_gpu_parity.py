@@ -1,0 +1,225 @@
+"""GPU decode parity: every decode through the C ABI equals the original
+column and the oracle's decode, element by element (bit-exact integers)."""
+import numpy as np
+import pytest
+
+import oracle
+import zf_workloads as W
+from gpu_helpers import Gpu, compress, out_specs
+
+zf = pytest.importorskip("paper_2602_08190_gb300")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    g = Gpu()
+    yield g
+    g.close()
+
+
+def _cases():
+    I32, I64 = np.int32, np.int64
+    rng = np.random.default_rng(21)
+    yield "uniform12", W.uniform_int(1, 0, 0, 300001, 0, 4096).astype(I32), 65536
+    yield "keys", W.sorted_keys(3, 400000), 131072
+    yield "dates", W.dates_rle(3, 400000), 131072
+    yield "dict25", W.dict_codes(3, 7, 0, 150000), 32768
+    yield "lognormal", W.lognormal_cents(3, 9, 0, 150000), 32768
+    yield "i32_extremes", np.array([2**31 - 1, -2**31, 0, -1, 5] * 999, I32), 1024
+    yield "i64_extremes", np.array([2**63 - 1, -2**63, 0, -1, 5] * 999, I64), 2048
+    yield "wide64", (rng.integers(-2**62, 2**62, 20000, dtype=I64) * 2 + 1), 8192
+    yield "ragged", rng.integers(-1000, 1000, 12345).astype(I64), 4096
+    yield "constant", np.full(5000, 42, I32), 1024
+    yield "one_row", np.array([7], I64), 1024
+    yield "outlier_runs", W.rle_distribution(2, "outlier", 70000, 64, 1024), 16384
+    yield "mixed_runs", W.rle_distribution(2, "mixed", 70000, 4, 32), 16384
+    yield "random_runs", W.rle_distribution(2, "random", 70000, 1, 64), 16384
+    yield "one_long_run", np.full(300000, -9, I32), 131072
+
+
+CASES = list(_cases())
+
+
+@pytest.mark.parametrize("scheme", ["raw", "for_bp", "dict_bp", "delta_bp", "rle"])
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c[0])
+def test_decode_equals_oracle(gpu, scheme, case):
+    name, x, cr = case
+    s = oracle.SCHEMES[scheme]
+    try:
+        h = compress(x, s, cr)
+    except zf.ZfError:
+        assert scheme == "dict_bp"
+        return
+    try:
+        got, = gpu.decode([h], out_specs(x))
+        ref = oracle.decode(zf.zf_compressed_bytes(h))
+        assert np.array_equal(ref, x)
+        assert np.array_equal(got, ref)
+    finally:
+        zf.zf_compressed_free(h)
+
+
+def test_oracle_encoded_streams_decode_on_gpu(gpu):
+    for name, x, cr in CASES[:6]:
+        for s in (oracle.FOR_BP, oracle.DELTA_BP, oracle.RLE):
+            h = zf.zf_compressed_from_bytes(oracle.encode(x, s, cr))
+            got, = gpu.decode([h], out_specs(x))
+            zf.zf_compressed_free(h)
+            assert np.array_equal(got, x), (name, s)
+
+
+def test_lz77_strings(gpu):
+    t, o = W.text_column(7, 1000003)
+    for enc in ("library", "oracle"):
+        if enc == "library":
+            h = compress(t, zf.ZF_LZ77, offsets=o)
+        else:
+            h = zf.zf_compressed_from_bytes(oracle.encode_strings(t, o))
+        got_t, got_o = gpu.decode([h], out_specs(t, o))
+        zf.zf_compressed_free(h)
+        assert np.array_equal(got_t, t), enc
+        assert np.array_equal(got_o, o), enc
+
+
+def test_lz77_edge_blocks(gpu):
+    cases = [
+        np.frombuffer(b"a" * 70000, np.uint8),                            # one long overlapping run
+        np.frombuffer((b"abc" * 40000)[:100000], np.uint8),               # offset 3 overlap
+        W.uniform_int(9, 1, 0, 150000, 0, 256).astype(np.uint8),          # incompressible: raw blocks
+        np.frombuffer(b"xyz", np.uint8),                                   # tiny
+    ]
+    for t in cases:
+        t = np.ascontiguousarray(t)
+        o = np.array([0, len(t)], np.int32)
+        h = compress(t, zf.ZF_LZ77, offsets=o)
+        got_t, got_o = gpu.decode([h], out_specs(t, o))
+        zf.zf_compressed_free(h)
+        assert np.array_equal(got_t, t)
+        assert np.array_equal(got_o, o)
+
+
+def test_empty_column(gpu):
+    x = np.zeros(0, np.int32)
+    h = compress(x, zf.ZF_FOR_BP, 1024)
+    got, = gpu.decode([h], [(np.int32, 0)])
+    zf.zf_compressed_free(h)
+    assert len(got) == 0
+
+
+@pytest.mark.parametrize("tile_rows,threads", [(1024, 128), (2048, 256), (4096, 512), (8192, 256), (16384, 512)])
+def test_schedule_invariance(tile_rows, threads):
+    """Every kernel geometry decodes the same bytes (Section 4: a <L,S,C>
+    tuple changes the schedule, not the computation)."""
+    g = Gpu(tile_rows=tile_rows, threads=threads, stage_bytes=1 << 20)
+    try:
+        for name, x, cr in (CASES[0], CASES[1], CASES[2], CASES[11], CASES[4]):
+            for s in (zf.ZF_FOR_BP, zf.ZF_DELTA_BP, zf.ZF_RLE):
+                h = compress(x, s, cr)
+                got, = g.decode([h], out_specs(x))
+                zf.zf_compressed_free(h)
+                assert np.array_equal(got, x), (name, s, tile_rows, threads)
+    finally:
+        g.close()
+
+
+def test_batched_mixed_columns_and_resident():
+    cols = [(CASES[0][1], zf.ZF_FOR_BP), (CASES[1][1], zf.ZF_DELTA_BP), (CASES[2][1], zf.ZF_RLE),
+            (CASES[3][1], zf.ZF_DICT_BP), (CASES[4][1], zf.ZF_FOR_BP), (CASES[5][1], zf.ZF_RAW)]
+    handles = [compress(x, s, 65536) for x, s in cols]
+    specs = [sp for x, s in cols for sp in out_specs(x)]
+    try:
+        for flags, resident in ((0, False), (zf.ZF_KCFG_BATCHED, False), (zf.ZF_KCFG_BATCHED, True), (0, True)):
+            g = Gpu(stage_bytes=1 << 19, flags=flags)
+            try:
+                got = g.decode(handles, specs, resident=resident)
+                for (x, s), y in zip(cols, got):
+                    assert np.array_equal(y, x), (flags, resident, s)
+            finally:
+                g.close()
+    finally:
+        for h in handles:
+            zf.zf_compressed_free(h)
+
+
+def test_ring_slots_and_small_stages():
+    x = W.sorted_keys(5, 1 << 20)
+    h = compress(x, zf.ZF_DELTA_BP, 65536)
+    try:
+        for slots in (2, 3, 8):
+            g = Gpu(stage_bytes=40000)
+            zf.zf_ctx_set_ring(g.ctx, slots)
+            got, = g.decode([h], out_specs(x))
+            assert g.last_stats.n_stages > slots
+            g.close()
+            assert np.array_equal(got, x)
+    finally:
+        zf.zf_compressed_free(h)
+
+
+def test_api_misuse(gpu):
+    torch = gpu.torch
+    x = W.sorted_keys(5, 10000)
+    h = compress(x, zf.ZF_DELTA_BP, 4096)
+    buf = torch.empty(x.nbytes + 16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(zf.ZfError) as e:  # too small
+        zf.zf_transfer_decompress(gpu.ctx, [h], [buf.data_ptr()], [x.nbytes - 8])
+    assert e.value.status == zf.ZF_EINVAL
+    with pytest.raises(zf.ZfError) as e:  # misaligned
+        zf.zf_transfer_decompress(gpu.ctx, [h], [buf.data_ptr() + 4], [x.nbytes])
+    assert e.value.status == zf.ZF_EINVAL
+    zf.zf_transfer_decompress(gpu.ctx, [h], [buf.data_ptr()], [buf.numel()])
+    with pytest.raises(zf.ZfError) as e:  # not synced
+        zf.zf_transfer_decompress(gpu.ctx, [h], [buf.data_ptr()], [buf.numel()])
+    assert e.value.status == zf.ZF_EBUSY
+    zf.zf_sync(gpu.ctx)
+    zf.zf_compressed_free(h)
+    assert np.array_equal(buf[: x.nbytes].cpu().numpy().view(np.int64), x)
+
+
+def _corrupt(b: bytes, fn) -> bytes:
+    bb = bytearray(b)
+    fn(bb)
+    return bytes(bb)
+
+
+def test_device_detects_corrupt_streams(gpu):
+    """Streams that pass the host's structural checks but whose data is
+    inconsistent make the decoder report ZF_ECORRUPT, without a fault."""
+    import struct
+    from oracle_pins import chunks_of
+    x = W.dates_rle(9, 50000)
+    b = oracle.encode(x, oracle.RLE, 16384)
+    off, ln, r0, rows, ch = chunks_of(oracle.default(), b)[1]
+    lo = off + ch["offs"][1]
+    bad = _corrupt(b, lambda bb: struct.pack_into("<I", bb, lo + 8, struct.unpack_from("<I", bb, lo + 8)[0] + 1))
+    h = zf.zf_compressed_from_bytes(bad)
+    gpu.decode([h], out_specs(x), expect=zf.ZF_ECORRUPT)
+    zf.zf_compressed_free(h)
+    # a zero run length
+    bad = _corrupt(b, lambda bb: struct.pack_into("<I", bb, lo + 4, 0))
+    h = zf.zf_compressed_from_bytes(bad)
+    gpu.decode([h], out_specs(x), expect=zf.ZF_ECORRUPT)
+    zf.zf_compressed_free(h)
+    # a dictionary code past the dictionary (3 values -> b = 2 -> code 3 is free)
+    d = np.array([10, 20, 30, 10] * 1000, np.int32)
+    b = oracle.encode(d, oracle.DICT_BP, 4096)
+    off, ln, r0, rows, ch = chunks_of(oracle.default(), b)[0]
+    bad = _corrupt(b, lambda bb: bb.__setitem__(off + ch["offs"][1], 0xFF))
+    h = zf.zf_compressed_from_bytes(bad)
+    gpu.decode([h], out_specs(d), expect=zf.ZF_ECORRUPT)
+    zf.zf_compressed_free(h)
+    # an LZ77 offset beyond the bytes produced so far
+    t = np.frombuffer(b"abcdabcdabcdabcd" * 100, np.uint8).copy()
+    o = np.array([0, len(t)], np.int32)
+    b = oracle.encode_strings(t, o)
+    off, ln, r0, rows, ch = chunks_of(oracle.default(), b)[0]
+    bad = _corrupt(b, lambda bb: struct.pack_into("<H", bb, off + ch["offs"][0] + 1, 9000))
+    h = zf.zf_compressed_from_bytes(bad)
+    gpu.decode([h], out_specs(t, o), expect=zf.ZF_ECORRUPT)
+    zf.zf_compressed_free(h)
+    # the context stays usable after a reported error
+    h = compress(x, zf.ZF_RLE, 16384)
+    got, = gpu.decode([h], out_specs(x))
+    zf.zf_compressed_free(h)
+    assert np.array_equal(got, x)
