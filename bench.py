@@ -106,10 +106,10 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def make_workload(seed: int):
+def make_workload(seed: int, rows: int = N_ROWS):
     import zf_workloads as W
-    keys = W.sorted_keys(seed, N_ROWS)
-    dates = W.dates_rle(seed, N_ROWS)
+    keys = W.sorted_keys(seed, rows)
+    dates = W.dates_rle(seed, rows)
     return keys, dates
 
 
@@ -169,6 +169,42 @@ def run_reference(args, rank: int):
     print(json.dumps(line), flush=True)
 
 
+def run_profile(args, zf, torch):
+    """Resident decode of one workload column, nothing else (ncu target)."""
+    keys, dates = make_workload(1, args.rows)
+    ctx = zf.zf_ctx_create(0)
+    if any((args.tile_rows, args.threads, args.ctas_per_sm)):
+        zf.zf_ctx_set_kcfg(ctx, args.tile_rows, args.threads, args.ctas_per_sm, 0, 0)
+    hs, outs, caps, bufs = [], [], [], []
+    for x, s, on in ((keys, zf.ZF_DELTA_BP, args.profile in ("keys", "both")),
+                     (dates, zf.ZF_RLE, args.profile in ("dates", "both"))):
+        if not on:
+            continue
+        c = zf.Column(x)
+        h = zf.zf_compress_host(zf.zf_plan(ctx, c, scheme=s, chunk_rows=CHUNK_ROWS), c)
+        hs.append(h)
+        b = torch.empty(x.nbytes, dtype=torch.uint8, device="cuda")
+        bufs.append(b)
+        outs.append(b.data_ptr())
+        caps.append(x.nbytes)
+    rs = [zf.zf_upload(ctx, h) for h in hs]
+    ms = []
+    for i in range(args.warmup + args.steps):
+        zf.zf_decompress_resident(ctx, rs, outs, caps)
+        st, stats = zf.zf_sync(ctx)
+        if i >= args.warmup:
+            ms.append(stats.total_ms)
+    raw = sum(caps)
+    comp = sum(zf.zf_compressed_info(h)[1] for h in hs)
+    print(json.dumps({"profile": args.profile, "rows": args.rows, "raw_bytes": raw, "comp_bytes": comp,
+                      "ms": round(float(np.median(ms)), 4), "gbs": round(raw / np.median(ms) / 1e6, 1)}))
+    for r in rs:
+        zf.zf_resident_free(r)
+    for h in hs:
+        zf.zf_compressed_free(h)
+    zf.zf_ctx_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -182,8 +218,11 @@ def main():
     ap.add_argument("--stage-mb", type=float, default=0)
     ap.add_argument("--slots", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--profile", choices=["keys", "dates", "both"], default=None,
+                    help="only decode the resident column(s) --steps times (for ncu captures)")
+    ap.add_argument("--rows", type=int, default=N_ROWS, help="rows per column (profile runs)")
     args = ap.parse_args()
-    assert args.warmup >= 3, "at least 3 warm-up steps"
+    assert args.warmup >= 3 or args.profile, "at least 3 warm-up steps"
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -201,6 +240,9 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
+    if args.profile:
+        assert world == 1
+        return run_profile(args, zf, torch)
     keys, dates = make_workload(1 + rank)
     ck, cd = zf.Column(keys), zf.Column(dates)
     copy_s, comp_s = torch.cuda.Stream(), torch.cuda.Stream()

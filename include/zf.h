@@ -103,7 +103,8 @@ typedef struct {
  * C = values a thread handles per 16-byte store, L = tile_rows / (S*C)
  * loop iterations per tile.  Zero fields take the tuned or built-in value. */
 typedef struct {
-    uint32_t tile_rows;       /* rows per tile: a multiple of 1024, <= 16384 */
+    uint32_t tile_rows;       /* rows per CTA tile: a multiple of 1024, <= 65536; raised to
+                                 1024 x threads/32 (one 1024-row warp tile per warp) */
     uint32_t threads;         /* 128, 256 or 512 */
     uint32_t ctas_per_sm;     /* persistent grid = ctas_per_sm x SM count (0 = occupancy limit) */
     uint32_t stage_bytes;     /* pipeline stage: compressed bytes per H2D copy + decode step */

@@ -500,7 +500,9 @@ bool fail(std::string* why, const std::string& m) {
     return false;
 }
 
-bool check_chunk(const uint8_t* c, uint64_t len, int scheme, int dtype, uint32_t rows, std::string* why) {
+bool check_chunk(const uint8_t* c, uint64_t len, int scheme, int dtype, uint32_t rows, uint8_t* bmax,
+                 std::string* why) {
+    *bmax = 0;
     if (len < kChunkHeader || len % 16) return fail(why, "chunk blob too short or not a multiple of 16");
     if (rd<uint32_t>(c) != kChunkMagic) return fail(why, "bad chunk magic");
     if (c[4] != scheme || c[5] != dtype) return fail(why, "chunk scheme/dtype differ from the column");
@@ -530,11 +532,13 @@ bool check_chunk(const uint8_t* c, uint64_t len, int scheme, int dtype, uint32_t
         break;
     case ZF_FOR_BP:
         if (b > wd || ln[0] != packed_bytes(rows, b)) return fail(why, "FOR width or payload length");
+        *bmax = (uint8_t)b;
         break;
     case ZF_DICT_BP:
         if (n_aux > kMaxDict || (rows && n_aux == 0) || ln[0] != (uint64_t)n_aux * sz ||
             b != (n_aux ? bits_of(n_aux - 1) : 0) || ln[1] != packed_bytes(rows, b))
             return fail(why, "dictionary header");
+        *bmax = (uint8_t)b;
         break;
     case ZF_DELTA_BP: {
         uint32_t nb = (rows + kDeltaBlock - 1) / kDeltaBlock;
@@ -545,6 +549,7 @@ bool check_chunk(const uint8_t* c, uint64_t len, int scheme, int dtype, uint32_t
             uint32_t mk = std::min(kDeltaBlock, rows - k * kDeltaBlock);
             if (bk > wd || po % 16 || (uint64_t)po + align16(packed_bytes(mk, bk)) > ln[1])
                 return fail(why, "delta block entry");
+            *bmax = (uint8_t)std::max<uint32_t>(*bmax, bk);
         }
         break;
     }
@@ -613,7 +618,7 @@ zf_status parse_serialized(zf_compressed* c, std::string* why) {
                 return ZF_ECORRUPT;
             }
             expect += ch.bytes;
-            if (!check_chunk(h + ch.off, ch.bytes, pi.scheme, pi.dtype, ch.rows, why)) return ZF_ECORRUPT;
+            if (!check_chunk(h + ch.off, ch.bytes, pi.scheme, pi.dtype, ch.rows, &ch.bmax, why)) return ZF_ECORRUPT;
             ch.off += pos;
             ch.scheme = (uint8_t)pi.scheme;
             ch.dtype = (uint8_t)pi.dtype;

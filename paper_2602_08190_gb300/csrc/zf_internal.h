@@ -21,7 +21,7 @@ constexpr uint32_t kLzBlock = 65536;           // bytes per LZ77 block
 constexpr uint32_t kLzMinMatch = 4;
 constexpr uint32_t kLzMaxOffset = 65535;
 constexpr uint32_t kMaxDict = 65536;
-constexpr uint32_t kMaxTileRows = 16384;
+constexpr uint32_t kMaxTileRows = 65536;
 
 inline uint64_t align16(uint64_t x) { return (x + 15) & ~uint64_t(15); }
 inline uint32_t bits_of(uint64_t x) { return x ? 64u - (uint32_t)__builtin_clzll(x) : 0u; }
@@ -34,7 +34,8 @@ struct ChunkInfo {
     uint64_t bytes;   // blob length
     uint64_t row0;    // first row within its part
     uint32_t rows;
-    uint8_t scheme, dtype, part, pad;
+    uint8_t scheme, dtype, part;
+    uint8_t bmax;     // widest bit width in the chunk (FOR/DICT: b; DELTA: widest block)
 };
 
 struct PartInfo {

@@ -22,10 +22,10 @@ struct LaunchArgs {
     const ZfDevChunk* chunks;
     uint32_t nchunks;
     uint32_t ntiles;
-    uint32_t tile_rows;
-    uint32_t rle_cap;
+    uint32_t tile_rows;    // rows of one CTA tile (a multiple of 1024)
+    uint32_t warp_smem;    // bytes of shared memory per warp
     uint32_t* err;
-    uint32_t* queue;   // [0] next tile, [1] CTAs done; null for static striding
+    uint32_t* queue;       // [0] next tile, [1] CTAs done; null for static striding
 };
 
 __device__ __forceinline__ uint32_t find_chunk(const ZfDevChunk* ch, uint32_t n, uint32_t tile) {
@@ -38,37 +38,35 @@ __device__ __forceinline__ uint32_t find_chunk(const ZfDevChunk* ch, uint32_t n,
     return a;
 }
 
-template <int SCHEME, int DT, int THREADS>
+template <int SCHEME, int DT>
 __device__ __forceinline__ void decode_one(const ZfDevChunk& c, const zfd::Hdr& h, uint32_t r0, uint32_t nr,
-                                           uint32_t* sm, uint64_t* scan, const LaunchArgs& a) {
-    if constexpr (DT == ZF_I32) {
-        using T = int32_t;
+                                           uint32_t* wsm, uint32_t* err) {
+    if constexpr (DT == ZF_I32 || DT == ZF_I64) {
+        using T = typename std::conditional<DT == ZF_I64, int64_t, int32_t>::type;
         if constexpr (SCHEME == ZF_FOR_BP || SCHEME == ZF_DICT_BP || SCHEME == ZF_RAW)
-            zfd::fp_tile<T, SCHEME>(c, h, r0, nr, sm, a.err);
+            zfd::fp_warp<T, SCHEME>(c, h, r0, nr, wsm, err);
         else if constexpr (SCHEME == ZF_DELTA_BP)
-            zfd::delta_tile<T, zf::kDeltaBlock / THREADS>(c, h, r0, nr, sm, scan, a.err);
+            zfd::delta_warp<T>(c, h, r0, nr, wsm, err);
         else if constexpr (SCHEME == ZF_RLE)
-            zfd::rle_tile<T>(c, h, r0, nr, sm, scan, a.rle_cap, a.err);
-    } else if constexpr (DT == ZF_I64) {
-        using T = int64_t;
-        if constexpr (SCHEME == ZF_FOR_BP || SCHEME == ZF_DICT_BP || SCHEME == ZF_RAW)
-            zfd::fp_tile<T, SCHEME>(c, h, r0, nr, sm, a.err);
-        else if constexpr (SCHEME == ZF_DELTA_BP)
-            zfd::delta_tile<T, zf::kDeltaBlock / THREADS>(c, h, r0, nr, sm, scan, a.err);
-        else if constexpr (SCHEME == ZF_RLE)
-            zfd::rle_tile<T>(c, h, r0, nr, sm, scan, a.rle_cap, a.err);
+            zfd::rle_warp<T>(c, h, r0, nr, wsm, err);
     } else if constexpr (DT == ZF_BYTES && SCHEME == ZF_RAW) {
-        zfd::fp_tile<uint8_t, ZF_RAW>(c, h, r0, nr, sm, a.err);
+        // raw bytes: 16-byte copies
+        const uint32_t lane = threadIdx.x & 31;
+        const uint8_t* src = c.blob + h.off[0] + r0;
+        uint8_t* dst = c.dst + r0;
+        for (uint32_t i0 = lane * 16; i0 < nr; i0 += 512) {
+            if (i0 + 16 <= nr) reinterpret_cast<uint4*>(dst + i0)[0] = zfd::ldg16(src + i0);
+            else
+                for (uint32_t i = i0; i < nr; i++) dst[i] = src[i];
+        }
     }
 }
 
-template <int THREADS>
 __device__ __noinline__ void decode_mixed(const ZfDevChunk& c, const zfd::Hdr& h, uint32_t r0, uint32_t nr,
-                                          uint32_t* sm, uint64_t* scan, const LaunchArgs& a) {
-    const int key = c.scheme * 4 + c.dtype;
-    switch (key) {
+                                          uint32_t* wsm, uint32_t* err) {
+    switch (c.scheme * 4 + c.dtype) {
 #define ZF_CASE(S, D) \
-    case S * 4 + D: decode_one<S, D, THREADS>(c, h, r0, nr, sm, scan, a); break;
+    case S * 4 + D: decode_one<S, D>(c, h, r0, nr, wsm, err); break;
         ZF_CASE(ZF_RAW, ZF_I32) ZF_CASE(ZF_RAW, ZF_I64) ZF_CASE(ZF_RAW, ZF_BYTES)
         ZF_CASE(ZF_FOR_BP, ZF_I32) ZF_CASE(ZF_FOR_BP, ZF_I64)
         ZF_CASE(ZF_DICT_BP, ZF_I32) ZF_CASE(ZF_DICT_BP, ZF_I64)
@@ -76,24 +74,29 @@ __device__ __noinline__ void decode_mixed(const ZfDevChunk& c, const zfd::Hdr& h
         ZF_CASE(ZF_RLE, ZF_I32) ZF_CASE(ZF_RLE, ZF_I64)
 #undef ZF_CASE
     default:
-        if (threadIdx.x == 0) zfd::report(a.err, ZF_EINVAL, c.chunk_id);
+        if ((threadIdx.x & 31) == 0) zfd::report(err, ZF_EINVAL, c.chunk_id);
     }
 }
 
+// A CTA decodes CTA tiles (tile_rows rows of one chunk); its warps take the
+// tile's 1024-row warp tiles in turn.  Specialized launches stride over the
+// tiles statically; the batched launch pops them from a work queue.
+// At least 32 resident warps per SM: registers are capped at 64 per thread.
 template <int SCHEME, int DT, int THREADS>
-__global__ void __launch_bounds__(THREADS) tiles_kernel(LaunchArgs a) {
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) tiles_kernel(LaunchArgs a) {
     extern __shared__ uint4 smem4[];
-    __shared__ uint64_t scan[33];
     __shared__ uint32_t s_tile;
-    uint32_t* sm = reinterpret_cast<uint32_t*>(smem4);
+    constexpr uint32_t NW = THREADS / 32;
+    const uint32_t warp = threadIdx.x >> 5;
+    uint32_t* wsm = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(smem4) + warp * a.warp_smem);
     uint32_t it = 0;
     for (;;) {
         uint32_t tile;
-        if (SCHEME < 0) {
+        if constexpr (SCHEME < 0) {
+            __syncthreads();
             if (threadIdx.x == 0) s_tile = atomicAdd(&a.queue[0], 1u);
             __syncthreads();
             tile = s_tile;
-            __syncthreads();
         } else {
             tile = blockIdx.x + it * gridDim.x;
             it++;
@@ -103,21 +106,28 @@ __global__ void __launch_bounds__(THREADS) tiles_kernel(LaunchArgs a) {
         const ZfDevChunk c = a.chunks[k];
         zfd::Hdr h;
         zfd::load_hdr(c.blob, h);
-        const uint32_t r0 = (tile - c.tile0) * a.tile_rows;
-        if (h.rows != c.rows || r0 >= c.rows || (uint64_t)c.rows * (c.dtype == ZF_I64 ? 8 : c.dtype == ZF_I32 ? 4 : 1) > c.dst_cap) {
+        const uint32_t rc = (tile - c.tile0) * a.tile_rows;
+        const uint32_t sz = c.dtype == ZF_I64 ? 8 : c.dtype == ZF_I32 ? 4 : 1;
+        if (h.rows != c.rows || rc >= c.rows || (uint64_t)c.rows * sz > c.dst_cap) {
             if (threadIdx.x == 0) zfd::report(a.err, ZF_ECORRUPT, c.chunk_id);
             continue;
         }
-        const uint32_t nr = min(a.tile_rows, c.rows - r0);
-        if constexpr (SCHEME < 0) decode_mixed<THREADS>(c, h, r0, nr, sm, scan, a);
-        else decode_one<SCHEME, DT, THREADS>(c, h, r0, nr, sm, scan, a);
+        for (uint32_t sub = warp; sub * zfd::kWarpRows < a.tile_rows; sub += NW) {
+            const uint32_t r0 = rc + sub * zfd::kWarpRows;
+            if (r0 >= c.rows) break;
+            const uint32_t nr = min(zfd::kWarpRows, c.rows - r0);
+            if constexpr (SCHEME < 0) decode_mixed(c, h, r0, nr, wsm, a.err);
+            else decode_one<SCHEME, DT>(c, h, r0, nr, wsm, a.err);
+        }
     }
-    if (SCHEME < 0 && threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(&a.queue[1], 1u) == gridDim.x - 1) {
-            a.queue[0] = 0;
-            a.queue[1] = 0;
+    if constexpr (SCHEME < 0) {
+        if (threadIdx.x == 0) {
             __threadfence();
+            if (atomicAdd(&a.queue[1], 1u) == gridDim.x - 1) {
+                a.queue[0] = 0;
+                a.queue[1] = 0;
+                __threadfence();
+            }
         }
     }
 }
@@ -235,21 +245,9 @@ std::unordered_map<void*, bool> g_attr_set;
 
 namespace zf {
 
-uint32_t smem_bytes(int scheme, int dtype, uint32_t tile_rows) {
-    uint32_t sz = dtype == ZF_I64 ? 8 : dtype == ZF_I32 ? 4 : 1;
-    switch (scheme) {
-    case ZF_RAW: return 16;
-    case ZF_FOR_BP: case ZF_DICT_BP: return tile_rows * sz + 48;    // widest packing: b = 8*sz bits
-    case ZF_DELTA_BP: return kDeltaBlock * sz + 48;
-    case ZF_RLE: {
-        uint32_t cap = tile_rows + 1;
-        return ((cap + 3) & ~3u) * 4 + cap * sz + 16;
-    }
-    }
-    return 16;
+uint32_t warp_smem_bytes(int scheme, int dtype, uint32_t bmax) {
+    return zfd::warp_smem(scheme, dtype == ZF_I64 ? 8 : dtype == ZF_I32 ? 4 : 1, bmax);
 }
-
-uint32_t rle_cap(uint32_t tile_rows) { return tile_rows + 1; }
 
 cudaError_t launch_tiles(const TileLaunch& L, cudaStream_t s) {
     KernelFn fn = nullptr;
@@ -287,7 +285,7 @@ cudaError_t launch_tiles(const TileLaunch& L, cudaStream_t s) {
     uint64_t grid = (uint64_t)per_sm * (uint64_t)L.num_sms;
     if (grid > L.ntiles) grid = L.ntiles;
     if (grid == 0) return cudaSuccess;
-    LaunchArgs a{L.chunks, L.nchunks, L.ntiles, L.tile_rows, rle_cap(L.tile_rows), L.err,
+    LaunchArgs a{L.chunks, L.nchunks, L.ntiles, L.tile_rows, L.smem / (L.threads / 32), L.err,
                  L.scheme < 0 ? L.queue : nullptr};
     fn<<<(unsigned)grid, L.threads, L.smem, s>>>(a);
     return cudaGetLastError();

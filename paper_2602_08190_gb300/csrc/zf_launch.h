@@ -14,13 +14,13 @@ struct TileLaunch {
     uint32_t tile_rows;
     uint32_t threads;
     uint32_t ctas_per_sm;       // 0 = occupancy limit
-    uint32_t smem;
+    uint32_t smem;              // dynamic shared memory: threads/32 slices of equal size
     int num_sms;
     uint32_t* err;
     uint32_t* queue;
 };
 
-uint32_t smem_bytes(int scheme, int dtype, uint32_t tile_rows);
+uint32_t warp_smem_bytes(int scheme, int dtype, uint32_t bmax);
 cudaError_t launch_tiles(const TileLaunch& L, cudaStream_t s);
 cudaError_t launch_lz(const ZfDevChunk* chunks, uint32_t n, uint32_t* err, int num_sms, cudaStream_t s);
 

@@ -52,7 +52,7 @@ struct zf_ctx {
     ZfDevChunk* h_desc = nullptr;  // pinned
     size_t desc_cap = 0;
     std::vector<ZfDevChunk> resident_cache;   // descriptors last uploaded for resident decode
-    zf_kcfg kcfg{4096, 256, 0, 8u << 20, 0};
+    zf_kcfg kcfg{0, 256, 0, 8u << 20, 0};
     bool busy = false;
     zf_status host_err = ZF_OK;
     std::string last_error;
@@ -72,10 +72,13 @@ zf_status cuda_fail(zf_ctx* ctx, cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
     } while (0)
 
+// Zero fields take the built-in geometry; a CTA tile holds at least one
+// 1024-row warp tile per warp.
 zf_kcfg effective_kcfg(const zf_ctx* ctx) {
     zf_kcfg k = ctx->kcfg;
-    if (!k.tile_rows) k.tile_rows = 4096;
     if (!k.threads) k.threads = 256;
+    const uint32_t min_rows = 1024 * (k.threads / 32);
+    if (k.tile_rows < min_rows) k.tile_rows = min_rows;
     if (!k.stage_bytes) k.stage_bytes = 8u << 20;
     return k;
 }
@@ -175,6 +178,7 @@ zf_status ensure_slots(zf_ctx* ctx, uint64_t bytes) {
 struct Group {
     int scheme, dtype;   // (-1, -1): batched work-queue kernel; (LZ77, BYTES): LZ kernel
     uint32_t first, count, ntiles;
+    uint32_t warp_smem;  // widest per-warp shared memory of the group's chunks
 };
 
 // Append descriptors of works[b, e) to `desc`, grouped for launching.
@@ -193,7 +197,7 @@ void build_groups(const std::vector<Work>& w, size_t b, size_t e, const zf_kcfg&
         if (std::find(keys.begin(), keys.end(), std::make_pair(s, d)) == keys.end()) keys.push_back({s, d});
     }
     for (auto& key : keys) {
-        Group g{key.first, key.second, (uint32_t)desc.size(), 0, 0};
+        Group g{key.first, key.second, (uint32_t)desc.size(), 0, 0, 16};
         for (size_t i = b; i < e; i++) {
             int s = w[i].ch->scheme, d = w[i].ch->dtype;
             bool lz = s == ZF_LZ77;
@@ -211,6 +215,7 @@ void build_groups(const std::vector<Work>& w, size_t b, size_t e, const zf_kcfg&
             dc.scheme = (uint8_t)s;
             dc.dtype = (uint8_t)d;
             g.ntiles += dc.ntiles;
+            g.warp_smem = std::max(g.warp_smem, zf::warp_smem_bytes(s, d, w[i].ch->bmax));
             desc.push_back(dc);
             g.count++;
         }
@@ -226,13 +231,7 @@ zf_status launch_groups(zf_ctx* ctx, const std::vector<Group>& groups, const std
         if (g.scheme == ZF_LZ77) {
             e = zf::launch_lz(dchunks, g.count, ctx->d_err, ctx->num_sms, ctx->compute);
         } else {
-            uint32_t smem = 16;
-            if (g.scheme < 0) {
-                for (uint32_t i = g.first; i < g.first + g.count; i++)
-                    smem = std::max(smem, zf::smem_bytes(desc[i].scheme, desc[i].dtype, k.tile_rows));
-            } else {
-                smem = zf::smem_bytes(g.scheme, g.dtype, k.tile_rows);
-            }
+            uint32_t smem = ((g.warp_smem + 15) & ~15u) * (k.threads / 32);
             zf::TileLaunch L{dchunks, g.count, g.ntiles, g.scheme, g.dtype, k.tile_rows, k.threads,
                              k.ctas_per_sm, smem, ctx->num_sms, ctx->d_err, ctx->d_err + 2};
             e = zf::launch_tiles(L, ctx->compute);
@@ -331,8 +330,8 @@ const char* zf_last_error(const zf_ctx* ctx) { return ctx ? ctx->last_error.c_st
 zf_status zf_ctx_set_kcfg(zf_ctx* ctx, const zf_kcfg* k) {
     if (!ctx || !k) return ZF_EINVAL;
     zf_kcfg n = *k;
-    if (!n.tile_rows) n.tile_rows = 4096;
     if (!n.threads) n.threads = 256;
+    if (!n.tile_rows) n.tile_rows = 1024 * (n.threads / 32);
     if (!n.stage_bytes) n.stage_bytes = 8u << 20;
     if (!kcfg_valid(n)) {
         ctx->last_error = "invalid kernel geometry";
@@ -621,7 +620,7 @@ extern "C" zf_status zf_plan(zf_ctx* ctx, const zf_column* col, const zf_plan_op
         if (ctx) ctx->last_error = "chunk_rows must be a multiple of 1024 and at most 2^30";
         return ZF_EINVAL;
     }
-    p.kcfg = ctx ? ctx->kcfg : zf_kcfg{4096, 256, 0, 8u << 20, 0};
+    p.kcfg = ctx ? ctx->kcfg : zf_kcfg{0, 256, 0, 8u << 20, 0};
     if (o.scheme >= 0) {
         if (o.scheme >= ZF_NSCHEMES) return ZF_EINVAL;
         p.scheme = o.scheme;
