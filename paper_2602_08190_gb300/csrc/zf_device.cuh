@@ -84,9 +84,11 @@ __device__ __forceinline__ void warp_stage(uint32_t* wsm, const uint8_t* src, ui
 }
 
 // Store N consecutive values of type T with the widest aligned vector stores
-// (the values are packed into 32-bit words in registers first).
+// (the values are packed into 32-bit words in registers first).  32-byte rows
+// use one 256-bit store when `al32` says the address is 32-byte aligned, so
+// a lane writes a whole L2 sector at once.
 template <class T, int N>
-__device__ __forceinline__ void store_vec(T* dst, const T (&v)[N]) {
+__device__ __forceinline__ void store_vec(T* dst, const T (&v)[N], bool al32 = false) {
     static_assert(sizeof(T) == 4 || sizeof(T) == 8, "int32 or int64 values");
     constexpr int W = N * (int)sizeof(T) / 4;
     uint32_t w[W];
@@ -97,6 +99,17 @@ __device__ __forceinline__ void store_vec(T* dst, const T (&v)[N]) {
             w[2 * k + 1] = (uint32_t)((uint64_t)v[k] >> 32);
         } else {
             w[k] = (uint32_t)v[k];
+        }
+    }
+    if constexpr (W == 8) {
+        if (al32) {
+            ulonglong4_32a q;
+            q.x = ((unsigned long long)w[1] << 32) | w[0];
+            q.y = ((unsigned long long)w[3] << 32) | w[2];
+            q.z = ((unsigned long long)w[5] << 32) | w[4];
+            q.w = ((unsigned long long)w[7] << 32) | w[6];
+            *reinterpret_cast<ulonglong4_32a*>(dst) = q;
+            return;
         }
     }
     if constexpr (W % 4 == 0) {
@@ -223,7 +236,7 @@ __device__ __forceinline__ void extract4(const uint32_t* wsm, uint32_t bitpos, u
 
 template <class T, class S, bool NARROW>
 __device__ __forceinline__ void delta_rows(T* dst, const uint32_t* wsm, uint32_t mk, uint32_t b, uint64_t base,
-                                           uint64_t min_d, uint32_t lane) {
+                                           uint64_t min_d, uint32_t lane, bool al32) {
     using U = typename std::conditional<sizeof(T) == 8, unsigned long long, unsigned int>::type;
     U acc = 0;
     const U md = (U)min_d;
@@ -248,11 +261,63 @@ __device__ __forceinline__ void delta_rows(T* dst, const uint32_t* wsm, uint32_t
         out[1] = (T)(x0 + md + (U)(s1 - u[0]));
         out[2] = (T)(x0 + 2 * md + (U)(s2 - u[0]));
         out[3] = (T)(x0 + 3 * md + (U)(s3 - u[0]));
-        if (j0 + 4 <= mk) store_vec<T, 4>(dst + j0, out);
+        if (j0 + 4 <= mk) store_vec<T, 4>(dst + j0, out, al32);
         else
             for (uint32_t k = 0; j0 + k < mk; k++) dst[j0 + k] = out[k];
         acc += (U)tot;
         t += row_step;
+    }
+}
+
+// b <= 8: two rows of 128 values per step.  A lane's four differences sum to
+// at most 4 * 255 and a row to at most 32,640 < 2^16, so both rows' lane sums
+// share one 32-bit word (row a low, row b high) and one shuffle scan.
+template <class T>
+__device__ __forceinline__ void delta_rows_pair(T* dst, const uint32_t* wsm, uint32_t mk, uint32_t b, uint64_t base,
+                                                uint64_t min_d, uint32_t lane, bool al32) {
+    using U = typename std::conditional<sizeof(T) == 8, unsigned long long, unsigned int>::type;
+    U acc = 0;
+    const U md = (U)min_d;
+    U t = (U)base + (U)(lane * 4) * md;
+    const U row_step = (U)128 * md;
+    for (uint32_t row = 0; row * 128 < mk; row += 2) {
+        const uint32_t ja = row * 128 + lane * 4, jb = ja + 128;
+        uint32_t ua[4], ub[4];
+        extract4<true, uint32_t>(wsm, ja * b, b, ua);
+        extract4<true, uint32_t>(wsm, jb * b, b, ub);
+        if (ja == 0) ua[0] = 0;
+        if (jb + 4 > mk) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (ja + k >= mk) ua[k] = 0;
+                if (jb + k >= mk) ub[k] = 0;
+            }
+        }
+        const uint32_t a1 = ua[0] + ua[1], a2 = a1 + ua[2], a3 = a2 + ua[3];
+        const uint32_t b1 = ub[0] + ub[1], b2 = b1 + ub[2], b3 = b2 + ub[3];
+        const uint32_t packed = a3 | (b3 << 16);
+        const uint32_t incl = warp_incl_sum<uint32_t>(packed, lane);
+        const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        const uint32_t excl = incl - packed;
+        const U xa = t + acc + (U)(excl & 0xFFFFu) + (U)ua[0];
+        const U xb = t + row_step + acc + (U)(tot & 0xFFFFu) + (U)(excl >> 16) + (U)ub[0];
+        T oa[4], ob[4];
+        oa[0] = (T)xa;
+        oa[1] = (T)(xa + md + (U)(a1 - ua[0]));
+        oa[2] = (T)(xa + 2 * md + (U)(a2 - ua[0]));
+        oa[3] = (T)(xa + 3 * md + (U)(a3 - ua[0]));
+        ob[0] = (T)xb;
+        ob[1] = (T)(xb + md + (U)(b1 - ub[0]));
+        ob[2] = (T)(xb + 2 * md + (U)(b2 - ub[0]));
+        ob[3] = (T)(xb + 3 * md + (U)(b3 - ub[0]));
+        if (ja + 4 <= mk) store_vec<T, 4>(dst + ja, oa, al32);
+        else
+            for (uint32_t k = 0; ja + k < mk; k++) dst[ja + k] = oa[k];
+        if (jb + 4 <= mk) store_vec<T, 4>(dst + jb, ob, al32);
+        else
+            for (uint32_t k = 0; jb + k < mk; k++) dst[jb + k] = ob[k];
+        acc += (U)(tot & 0xFFFFu) + (U)(tot >> 16);
+        t += 2 * row_step;
     }
 }
 
@@ -277,10 +342,11 @@ __device__ void delta_warp(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint3
     }
     warp_stage(wsm, c.blob + h.off[1] + poff, nbytes, lane);
     T* dst = reinterpret_cast<T*>(c.dst) + r0;
+    const bool al32 = (reinterpret_cast<uintptr_t>(dst) & 31) == 0;
     // 128 values of at most 24 bits sum below 2^31: scan in 32 bits
-    if (b <= 8) delta_rows<T, uint32_t, true>(dst, wsm, nr, b, base, min_d, lane);
-    else if (b <= 24) delta_rows<T, uint32_t, false>(dst, wsm, nr, b, base, min_d, lane);
-    else delta_rows<T, U, false>(dst, wsm, nr, b, base, min_d, lane);
+    if (b <= 8) delta_rows_pair<T>(dst, wsm, nr, b, base, min_d, lane, al32);
+    else if (b <= 24) delta_rows<T, uint32_t, false>(dst, wsm, nr, b, base, min_d, lane, al32);
+    else delta_rows<T, U, false>(dst, wsm, nr, b, base, min_d, lane, al32);
     __syncwarp();
 }
 
@@ -325,22 +391,34 @@ __device__ void rle_warp(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_
     // last run of a tile can be longer than the tile, so 32-bit sums hold.
     uint32_t end = 0;                 // rows covered so far, counted from the first run's start
     uint32_t first_len = 0, last_start = 0;
-    for (uint32_t g = 0; g < m; g += 32) {
-        const uint32_t i = g + lane;
-        uint32_t L = 0;
-        if (i < m) {
-            L = __ldg(lens + rf + i);
-            rv[i] = __ldg(vals + rf + i);
+    for (uint32_t g0 = 0; g0 < m; g0 += 128) {
+        // four groups of 32 runs: independent loads first, then the scans
+        uint32_t Ls[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const uint32_t i = g0 + 32 * q + lane;
+            Ls[q] = 0;
+            if (i < m) {
+                Ls[q] = __ldg(lens + rf + i);
+                rv[i] = __ldg(vals + rf + i);
+            }
         }
-        bad |= i < m && (L == 0 || L > h.rows);
-        const uint32_t incl = warp_incl_sum<uint32_t>(L, lane);
-        const uint32_t start = end + incl - L;   // relative to the first run's start
-        if (i < m && i > 0 && start >= skip && start - skip < nr) mark[start - skip] = (uint16_t)i;
-        if (g == 0) first_len = __shfl_sync(0xFFFFFFFFu, L, 0);
-        const uint32_t ls = __shfl_sync(0xFFFFFFFFu, start, (m - 1 - g) & 31);
-        if (m - 1 - g < 32) last_start = ls;
-        end += __shfl_sync(0xFFFFFFFFu, incl, 31);
-        if (end > 2u * (1u << 30) + 2048u) bad = true;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const uint32_t g = g0 + 32 * q;
+            if (g >= m) break;
+            const uint32_t i = g + lane;
+            const uint32_t L = Ls[q];
+            bad |= i < m && (L == 0 || L > h.rows);
+            const uint32_t incl = warp_incl_sum<uint32_t>(L, lane);
+            const uint32_t start = end + incl - L;   // relative to the first run's start
+            if (i < m && i > 0 && start >= skip && start - skip < nr) mark[start - skip] = (uint16_t)i;
+            if (g == 0) first_len = __shfl_sync(0xFFFFFFFFu, L, 0);
+            const uint32_t ls = __shfl_sync(0xFFFFFFFFu, start, (m - 1 - g) & 31);
+            if (m - 1 - g < 32) last_start = ls;
+            end += __shfl_sync(0xFFFFFFFFu, incl, 31);
+            if (end > 2u * (1u << 30) + 2048u) bad = true;
+        }
     }
     // The runs cover exactly [0, nr): the first starts at or before row 0, the
     // last ends at nr or continues into the next tile by the directory's amount.
@@ -351,6 +429,7 @@ __device__ void rle_warp(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_
     if (lane == 0 && (!ok || any_bad)) report(err, ZF_ECORRUPT, c.chunk_id);
     __syncwarp();
     T* dst = reinterpret_cast<T*>(c.dst) + r0;
+    const bool al32 = (reinterpret_cast<uintptr_t>(dst) & 31) == 0;
     uint32_t carry = 0;
     for (uint32_t j0 = lane * V; j0 - lane * V < nr; j0 += 32 * V) {
         const uint2 mk = reinterpret_cast<const uint2*>(mark)[j0 / 4];
@@ -365,7 +444,7 @@ __device__ void rle_warp(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_
         T v[V];
 #pragma unroll
         for (int k = 0; k < V; k++) v[k] = rv[min(max(before, r[k]), m - 1)];
-        if (j0 + V <= nr) store_vec<T, V>(dst + j0, v);
+        if (j0 + V <= nr) store_vec<T, V>(dst + j0, v, al32);
         else
             for (uint32_t k = 0; j0 + k < nr; k++) dst[j0 + k] = v[k];
         carry = max(carry, __shfl_sync(0xFFFFFFFFu, incl, 31));
