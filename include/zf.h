@@ -205,6 +205,34 @@ zf_status zf_resident_free(zf_resident* r);
 zf_status zf_decompress_resident(zf_ctx* ctx, const zf_resident* const* cols, uint32_t ncols,
                                  void* const* d_out, const uint64_t* d_out_bytes);
 
+/* ---- decode without allocation ------------------------------------------ */
+
+/* Decode one compressed I32/I64 column (scheme RAW, FOR_BP, DICT_BP,
+ * DELTA_BP or RLE) whose serialized bytes (the format above, for example
+ * zf_compressed_bytes copied to the GPU) already sit in device memory at
+ * `d_column`, into the device buffer `d_out`, on `stream` (a cudaStream_t,
+ * or NULL for the default stream).  The paper has no counterpart: this entry
+ * point exists for callers that may not allocate device memory once they are
+ * running -- engines that reserve all device memory at start-up, code whose
+ * memory budget belongs to another runtime, or code that must not grow the
+ * device heap inside a call.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine and needs no zf_ctx.
+ *
+ * Its scratch (chunk descriptors, work-queue counters, error word) is one
+ * fixed device array of 262,400 bytes in the library, held by every GPU
+ * that loads the library until the process exits.  It fits columns of at
+ * most 4096 chunks; larger columns return ZF_EINVAL before any GPU work.
+ * The first call on a device looks up the array's device address, so make
+ * that first call before any stream capture.  The call is synchronous: it
+ * returns after the decode has finished and reports ZF_ECORRUPT if the
+ * device checks of the stream failed.  Every call on a device shares the
+ * array (each call rewrites what it uses); calls that overlap on the GPU,
+ * from several host threads or streams at once, race -- serialize them.
+ * Both pointers must be 16-byte aligned; `out_bytes` must hold all rows.
+ * Returns ZF_EUNSUPPORTED for BYTES columns. */
+zf_status zf_decompress_device_noalloc(const void* d_column, uint64_t column_bytes, void* d_out,
+                                       uint64_t out_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

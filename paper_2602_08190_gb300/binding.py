@@ -21,7 +21,7 @@ __all__ = [
     "zf_plan_t", "zf_stats", "Column", "zf_ctx_create", "zf_ctx_destroy", "zf_last_error", "zf_ctx_set_kcfg",
     "zf_ctx_set_ring", "zf_plan", "zf_compress_host", "zf_compressed_info", "zf_compressed_free",
     "zf_compressed_bytes", "zf_compressed_from_bytes", "zf_transfer_decompress", "zf_sync", "zf_upload",
-    "zf_resident_free", "zf_decompress_resident", "EXPORTED", "LIB_PATH",
+    "zf_resident_free", "zf_decompress_resident", "zf_decompress_device_noalloc", "EXPORTED", "LIB_PATH",
 ]
 
 (ZF_OK, ZF_EINVAL, ZF_ENOMEM, ZF_ECUDA, ZF_ECORRUPT, ZF_ETIMEOUT, ZF_EUNSUPPORTED, ZF_EBUSY) = range(8)
@@ -82,6 +82,7 @@ _SIGS = {
     "zf_upload": [_vp, _vp, ctypes.POINTER(_vp)],
     "zf_resident_free": [_vp],
     "zf_decompress_resident": [_vp, ctypes.POINTER(_vp), _u32, ctypes.POINTER(_vp), ctypes.POINTER(_u64)],
+    "zf_decompress_device_noalloc": [_vp, _u64, _vp, _u64, _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_L, _name)
@@ -207,3 +208,10 @@ def zf_resident_free(r: int) -> None:
 def zf_decompress_resident(ctx: int, cols: list[int], outs: list[int], caps: list[int]) -> None:
     c, o, k = _arrays(cols, outs, caps)
     _check(_L.zf_decompress_resident(ctx, c, len(cols), o, k), "zf_decompress_resident", ctx)
+
+
+def zf_decompress_device_noalloc(d_column: int, column_bytes: int, d_out: int, out_bytes: int,
+                                 stream: int | None = None) -> int:
+    """Decode a serialized integer column already in device memory without
+    allocating; returns the zf_status (0 = ok) instead of raising."""
+    return int(_L.zf_decompress_device_noalloc(d_column, column_bytes, d_out, out_bytes, stream or None))
