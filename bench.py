@@ -169,6 +169,98 @@ def run_reference(args, rank: int):
     print(json.dumps(line), flush=True)
 
 
+# Schemes of the fact table's column kinds (the task's mix: FOR for small
+# integers and scaled decimals, delta for sorted keys, RLE for dates,
+# dictionary for the 25-value codes).
+FACT_SCHEMES = {"uniform_1_50": "for_bp", "lognormal_cents": "for_bp", "sorted_keys": "delta_bp",
+                "dates": "rle", "codes_25": "dict_bp"}
+FACT_ROWS = 400_000_000
+BATCHED_WORKLOAD = ("batched: 16-column fact table x 400M rows (2 int32 uniform 1-50, 7 int64 log-normal cents, "
+                    "2 int64 sorted keys, 3 int32 RLE dates, 2 int32 25-value Zipf codes; 100 B/row, 40 GB), "
+                    "streamed in uneven 4-64 MB pieces, one work-queue launch per stage, CUDA graph")
+
+
+def build_fact_table(zf, rows: int = FACT_ROWS, seed: int = 1, keep: bool = True):
+    """Generate the fact table column by column, cut each column into its
+    uneven pieces and compress every piece (one single-chunk compressed
+    column per piece).  Returns (columns or None, [(handle, col, row0, rows)])."""
+    import zf_workloads as W
+    scheme_of = {"raw": zf.ZF_RAW, "for_bp": zf.ZF_FOR_BP, "dict_bp": zf.ZF_DICT_BP, "delta_bp": zf.ZF_DELTA_BP,
+                 "rle": zf.ZF_RLE}
+    cols, pieces = [], []
+    for ci, (name, dt, kind) in enumerate(W.FACT_COLUMNS):
+        x = W.fact_column(seed, ci, rows)
+        scheme = scheme_of[FACT_SCHEMES[kind]]
+        r0 = 0
+        for n in W.fact_pieces(seed, ci, rows):
+            part = zf.Column(x[r0:r0 + n])
+            h = zf.zf_compress_host(zf.zf_plan(None, part, scheme=scheme, chunk_rows=(n + 1023) // 1024 * 1024),
+                                    part)
+            pieces.append((h, ci, r0, n))
+            r0 += n
+        cols.append(x if keep else None)
+    return cols, pieces
+
+
+def run_batched(args, zf, torch):
+    """The batched workload: every piece of the 16 columns in one call."""
+    import zf_workloads as W
+    rows = args.rows if args.rows != N_ROWS else FACT_ROWS
+    cols, pieces = build_fact_table(zf, rows)
+    copy_s, comp_s = torch.cuda.Stream(), torch.cuda.Stream()
+    ctx = zf.zf_ctx_create(0, copy_s.cuda_stream, comp_s.cuda_stream)
+    stage = int((args.stage_mb or 64) * (1 << 20))
+    zf.zf_ctx_set_kcfg(ctx, args.tile_rows, args.threads, args.ctas_per_sm, stage,
+                       zf.ZF_KCFG_BATCHED | zf.ZF_KCFG_GRAPH)
+    zf.zf_ctx_set_ring(ctx, args.slots or 3)
+    dev = [torch.empty(rows * np.dtype(dt).itemsize, dtype=torch.uint8, device="cuda")
+           for _, dt, _ in W.FACT_COLUMNS]
+    handles = [h for h, _, _, _ in pieces]
+    outs, caps = [], []
+    for h, ci, r0, n in pieces:
+        isz = np.dtype(W.FACT_COLUMNS[ci][1]).itemsize
+        outs.append(dev[ci].data_ptr() + r0 * isz)
+        caps.append(n * isz)
+    raw = sum(caps)
+    comp = sum(zf.zf_compressed_info(h)[1] for h in handles)
+    # correctness of this run's outputs before timing
+    zf.zf_transfer_decompress(ctx, handles, outs, caps)
+    zf.zf_sync(ctx)
+    for ci, x in enumerate(cols):
+        assert np.array_equal(dev[ci].cpu().numpy().view(x.dtype), x), W.FACT_COLUMNS[ci][0]
+    res = [zf.zf_upload(ctx, h) for h in handles]
+    e2e_ms, dev_ms, launches = [], [], 0
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        zf.zf_transfer_decompress(ctx, handles, outs, caps)
+        st, stats = zf.zf_sync(ctx)
+        if i >= args.warmup:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+            launches += stats.n_launches
+    for i in range(args.warmup + args.steps):
+        zf.zf_decompress_resident(ctx, res, outs, caps)
+        st, stats = zf.zf_sync(ctx)
+        if i >= args.warmup:
+            dev_ms.append(stats.total_ms)
+            launches += stats.n_launches
+    t_e2e, t_dev = float(np.mean(e2e_ms)), float(np.mean(dev_ms))
+    line = {"metric": METRIC, "value": round(raw / (t_dev * 1e-3) / 1e9, 2), "unit": "GB/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_dev, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64/int32", "data": "synthetic",
+            "config": {"workload": BATCHED_WORKLOAD, "raw_bytes_per_step": raw, "comp_bytes_per_step": comp,
+                       "compression_ratio": round(raw / comp, 3), "pieces": len(pieces), "stage_bytes": stage,
+                       "l2": "inputs and outputs far larger than L2"},
+            "e2e": {"value": round(raw / (t_e2e * 1e-3) / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": comp,
+                    "d2h_bytes_per_step": 8, "ms_per_step": round(t_e2e, 3)},
+            "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+    for r in res:
+        zf.zf_resident_free(r)
+    for h in handles:
+        zf.zf_compressed_free(h)
+    zf.zf_ctx_destroy(ctx)
+
+
 def run_profile(args, zf, torch):
     """Resident decode of one workload column, nothing else (ncu target)."""
     keys, dates = make_workload(1, args.rows)
@@ -220,7 +312,9 @@ def main():
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--profile", choices=["keys", "dates", "both"], default=None,
                     help="only decode the resident column(s) --steps times (for ncu captures)")
-    ap.add_argument("--rows", type=int, default=N_ROWS, help="rows per column (profile runs)")
+    ap.add_argument("--rows", type=int, default=N_ROWS, help="rows per column (profile / batched runs)")
+    ap.add_argument("--workload", choices=["group_parallel", "batched"], default="group_parallel",
+                    help="group_parallel: the benchmark line; batched: the 40 GB fact table")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.profile, "at least 3 warm-up steps"
 
@@ -243,6 +337,9 @@ def main():
     if args.profile:
         assert world == 1
         return run_profile(args, zf, torch)
+    if args.workload == "batched":
+        assert world == 1
+        return run_batched(args, zf, torch)
     keys, dates = make_workload(1 + rank)
     ck, cd = zf.Column(keys), zf.Column(dates)
     copy_s, comp_s = torch.cuda.Stream(), torch.cuda.Stream()

@@ -100,14 +100,15 @@ typedef struct {
 } zf_column;
 
 /* Kernel geometry, the <L,S,C> vector of Section 4: S = threads per CTA,
- * C = values a thread handles per 16-byte store, L = tile_rows / (S*C)
- * loop iterations per tile.  Zero fields take the tuned or built-in value. */
+ * C = values a lane stores per 16-byte store (16 / value size), L = the
+ * warp job's 1024-row tiles: each warp decodes tile_rows / 1024 consecutive
+ * tiles of one chunk, staging the next tile while it decodes the current
+ * one.  Zero fields take the built-in values. */
 typedef struct {
-    uint32_t tile_rows;       /* rows per CTA tile: a multiple of 1024, <= 65536; raised to
-                                 1024 x threads/32 (one 1024-row warp tile per warp) */
-    uint32_t threads;         /* 128, 256 or 512 */
-    uint32_t ctas_per_sm;     /* persistent grid = ctas_per_sm x SM count (0 = occupancy limit) */
-    uint32_t stage_bytes;     /* pipeline stage: compressed bytes per H2D copy + decode step */
+    uint32_t tile_rows;       /* rows per warp job: a multiple of 1024, <= 16384 (default 4096) */
+    uint32_t threads;         /* 128, 256 or 512 (default 256) */
+    uint32_t ctas_per_sm;     /* batched launch: persistent grid = ctas_per_sm x SM count (0 = occupancy limit) */
+    uint32_t stage_bytes;     /* pipeline stage: compressed bytes per H2D copy + decode step (default 8 MiB) */
     uint32_t flags;           /* ZF_KCFG_BATCHED: one work-queue launch per stage for all schemes
                                  (else one launch per (scheme, dtype) group);
                                  ZF_KCFG_GRAPH: capture repeated transfers in a CUDA graph */
@@ -204,6 +205,78 @@ zf_status zf_resident_free(zf_resident* r);
  * (asynchronous; finish with zf_sync).  Outputs as in zf_transfer_decompress. */
 zf_status zf_decompress_resident(zf_ctx* ctx, const zf_resident* const* cols, uint32_t ncols,
                                  void* const* d_out, const uint64_t* d_out_bytes);
+
+/* ---- autotuning (Section 4, device geometry; Section 5.5) ------------------ */
+
+/* One measured point of the search: the geometry and its median time. */
+typedef struct {
+    zf_kcfg kcfg;
+    float ms;                 /* median of `reps` runs: zf_stats.total_ms */
+} zf_tune_point;
+
+/* Exhaustive search of the kernel geometry for these columns, the
+ * brute-force search of Section 5.5 on this GPU: every tile_rows in
+ * {1024, 2048, 4096, 8192, 16384} (L = 1..16 tiles per warp job) x threads in
+ * {128, 256, 512} (S) is run once to warm up and `reps` times (0 = 3); with
+ * `transfer` != 0 the full transfer is timed and stage_bytes in
+ * {4, 8, 16, 32, 64} MiB is searched too (75 points), otherwise the decode of
+ * the columns uploaded to HBM (15 points).  C is fixed by the store width.
+ * Writes up to max_points points (every point is visited once, in that
+ * order), sets *n_points to the number visited, stores the fastest geometry
+ * in *best (nullable) and makes it the context's geometry.  Outputs as in
+ * zf_transfer_decompress; the columns are decoded into them many times. */
+zf_status zf_tune(zf_ctx* ctx, const zf_compressed* const* cols, uint32_t ncols, void* const* d_out,
+                  const uint64_t* d_out_bytes, int32_t transfer, uint32_t reps, zf_tune_point* points,
+                  uint32_t max_points, uint32_t* n_points, zf_kcfg* best);
+
+/* ---- learned selector ------------------------------------------------------ */
+
+/* The 32 statistics of a host column the selector reads (value range,
+ * distinct values, runs, differences, entropies, byte repetition ...),
+ * each scaled to about [0, 1], computed on a fixed sample of the column:
+ * the whole column up to 262,144 rows (bytes for string columns), else 64
+ * windows of 4,096 consecutive rows.  out: 32 floats (host). */
+zf_status zf_column_features(const zf_column* col, float* out);
+
+/* A perceptron 32 -> 64 -> 64 -> 12 (ReLU, FP32) on a device, trained and run
+ * by the library's CUDA kernels.  Classes: label = scheme * 2 + size, size 0
+ * = 4 MiB and 1 = 32 MiB of uncompressed bytes per chunk.  Parameters are
+ * 7,052 floats: W1[64][32], b1[64], W2[64][64], b2[64], W3[12][64], b3[12]. */
+typedef struct zf_mlp zf_mlp;
+#define ZF_MLP_PARAMS 7052
+#define ZF_MLP_CLASSES 12
+/* He-normal weights from `seed`, zero biases, Adam state cleared. */
+zf_status zf_mlp_create(int device, uint64_t seed, zf_mlp** out);
+zf_status zf_mlp_destroy(zf_mlp* net);
+/* Copy the parameters out (host, 7,052 floats) or in (also clears Adam state). */
+zf_status zf_mlp_get_params(const zf_mlp* net, float* host);
+zf_status zf_mlp_set_params(zf_mlp* net, const float* host);
+/* Device buffers: d_x batch x 32, d_logits batch x 12, d_y batch labels,
+ * d_mask batch x 12 bytes (1 = class allowed), d_grad 7,052 floats, d_loss
+ * one float (nullable).  `stream` is a cudaStream_t or NULL. */
+zf_status zf_mlp_forward(zf_mlp* net, const float* d_x, uint32_t batch, float* d_logits, void* stream);
+/* Gradient of the mean masked softmax cross-entropy of the batch. */
+zf_status zf_mlp_grad(zf_mlp* net, const float* d_x, const int32_t* d_y, const uint8_t* d_mask, uint32_t batch,
+                      float* d_grad, float* d_loss, void* stream);
+/* One Adam step (b1 0.9, b2 0.999, eps 1e-8) with learning rate lr. */
+zf_status zf_mlp_adam(zf_mlp* net, const float* d_grad, float lr, void* stream);
+/* Train on host arrays (count samples): `epochs` passes in seeded random
+ * order, mini-batches of `batch`, Adam at lr.  h_losses (nullable) gets the
+ * mean loss of each epoch. */
+zf_status zf_mlp_train(zf_mlp* net, const float* h_x, const int32_t* h_y, const uint8_t* h_mask, uint32_t count,
+                       uint32_t epochs, uint32_t batch, float lr, uint64_t seed, float* h_losses);
+/* Class of each host row (argmax of the logits over its allowed classes, -1
+ * if none allowed), computed on the GPU. */
+zf_status zf_mlp_predict(zf_mlp* net, const float* h_x, const uint8_t* h_mask, uint32_t count, int32_t* h_class);
+/* Time every selector class on a column: compress with the class's scheme
+ * and chunk size, then transfer + decode (reps runs after one warm-up, median
+ * of zf_sync's total_ms).  ms: 12 floats, -1 for classes that do not apply.
+ * This is the exhaustive search zf_plan's selector 2 uses and the label
+ * source for training the selector. */
+zf_status zf_measure_classes(zf_ctx* ctx, const zf_column* col, uint32_t reps, float* ms);
+/* Use `net` (kept, not owned) for zf_plan's selector 1; features are
+ * standardized as (f - mean) / std with the given 32-float host vectors. */
+zf_status zf_ctx_set_selector(zf_ctx* ctx, zf_mlp* net, const float* mean, const float* std);
 
 /* ---- decode without allocation ------------------------------------------ */
 

@@ -21,8 +21,12 @@ __all__ = [
     "zf_plan_t", "zf_stats", "Column", "zf_ctx_create", "zf_ctx_destroy", "zf_last_error", "zf_ctx_set_kcfg",
     "zf_ctx_set_ring", "zf_plan", "zf_compress_host", "zf_compressed_info", "zf_compressed_free",
     "zf_compressed_bytes", "zf_compressed_from_bytes", "zf_transfer_decompress", "zf_sync", "zf_upload",
-    "zf_resident_free", "zf_decompress_resident", "zf_decompress_device_noalloc", "EXPORTED", "LIB_PATH",
+    "zf_resident_free", "zf_decompress_resident", "zf_decompress_device_noalloc", "zf_tune", "zf_tune_point",
+    "zf_column_features", "zf_measure_classes", "zf_ctx_set_selector", "zf_mlp_create", "zf_mlp_destroy",
+    "zf_mlp_get_params", "zf_mlp_set_params", "zf_mlp_forward", "zf_mlp_grad", "zf_mlp_adam", "zf_mlp_train",
+    "zf_mlp_predict", "ZF_MLP_PARAMS", "ZF_MLP_CLASSES", "EXPORTED", "LIB_PATH",
 ]
+ZF_MLP_PARAMS, ZF_MLP_CLASSES = 7052, 12
 
 (ZF_OK, ZF_EINVAL, ZF_ENOMEM, ZF_ECUDA, ZF_ECORRUPT, ZF_ETIMEOUT, ZF_EUNSUPPORTED, ZF_EBUSY) = range(8)
 ZF_I32, ZF_I64, ZF_BYTES = range(3)
@@ -59,6 +63,10 @@ class zf_plan_t(ctypes.Structure):
                 ("kcfg", zf_kcfg), ("predicted_ms", ctypes.c_float), ("label", ctypes.c_int32)]
 
 
+class zf_tune_point(ctypes.Structure):
+    _fields_ = [("kcfg", zf_kcfg), ("ms", ctypes.c_float)]
+
+
 class zf_stats(ctypes.Structure):
     _fields_ = [("raw_bytes", ctypes.c_uint64), ("comp_bytes", ctypes.c_uint64), ("n_chunks", ctypes.c_uint32),
                 ("n_stages", ctypes.c_uint32), ("n_launches", ctypes.c_uint32), ("device_error", ctypes.c_uint32),
@@ -83,6 +91,20 @@ _SIGS = {
     "zf_resident_free": [_vp],
     "zf_decompress_resident": [_vp, ctypes.POINTER(_vp), _u32, ctypes.POINTER(_vp), ctypes.POINTER(_u64)],
     "zf_decompress_device_noalloc": [_vp, _u64, _vp, _u64, _vp],
+    "zf_column_features": [ctypes.POINTER(zf_column), _vp],
+    "zf_measure_classes": [_vp, ctypes.POINTER(zf_column), _u32, _vp],
+    "zf_ctx_set_selector": [_vp, _vp, _vp, _vp],
+    "zf_mlp_create": [ctypes.c_int, _u64, ctypes.POINTER(_vp)],
+    "zf_mlp_destroy": [_vp],
+    "zf_mlp_get_params": [_vp, _vp],
+    "zf_mlp_set_params": [_vp, _vp],
+    "zf_mlp_forward": [_vp, _vp, _u32, _vp, _vp],
+    "zf_mlp_grad": [_vp, _vp, _vp, _vp, _u32, _vp, _vp, _vp],
+    "zf_mlp_adam": [_vp, _vp, ctypes.c_float, _vp],
+    "zf_mlp_train": [_vp, _vp, _vp, _vp, _u32, _u32, _u32, ctypes.c_float, _u64, _vp],
+    "zf_mlp_predict": [_vp, _vp, _vp, _u32, _vp],
+    "zf_tune": [_vp, ctypes.POINTER(_vp), _u32, ctypes.POINTER(_vp), ctypes.POINTER(_u64), ctypes.c_int32, _u32,
+                ctypes.POINTER(zf_tune_point), _u32, ctypes.POINTER(_u32), ctypes.POINTER(zf_kcfg)],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_L, _name)
@@ -215,3 +237,90 @@ def zf_decompress_device_noalloc(d_column: int, column_bytes: int, d_out: int, o
     """Decode a serialized integer column already in device memory without
     allocating; returns the zf_status (0 = ok) instead of raising."""
     return int(_L.zf_decompress_device_noalloc(d_column, column_bytes, d_out, out_bytes, stream or None))
+
+
+def zf_tune(ctx: int, cols: list[int], outs: list[int], caps: list[int], transfer: bool = False,
+            reps: int = 3) -> tuple[list[zf_tune_point], zf_kcfg]:
+    c, o, k = _arrays(cols, outs, caps)
+    pts = (zf_tune_point * 128)()
+    n = _u32()
+    best = zf_kcfg()
+    _check(_L.zf_tune(ctx, c, len(cols), o, k, 1 if transfer else 0, reps, pts, 128, ctypes.byref(n),
+                      ctypes.byref(best)), "zf_tune", ctx)
+    return [pts[i] for i in range(min(n.value, 128))], best
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def zf_column_features(col: Column) -> np.ndarray:
+    out = np.zeros(32, np.float32)
+    _check(_L.zf_column_features(ctypes.byref(col.c), out.ctypes.data), "zf_column_features")
+    return out
+
+
+def zf_measure_classes(ctx: int, col: Column, reps: int = 3) -> np.ndarray:
+    out = np.zeros(ZF_MLP_CLASSES, np.float32)
+    _check(_L.zf_measure_classes(ctx, ctypes.byref(col.c), reps, out.ctypes.data), "zf_measure_classes", ctx)
+    return out
+
+
+def zf_ctx_set_selector(ctx: int, net: int | None, mean=None, std=None) -> None:
+    m = _f32(mean) if mean is not None else None
+    sd = _f32(std) if std is not None else None
+    _check(_L.zf_ctx_set_selector(ctx, net, m.ctypes.data if m is not None else None,
+                                  sd.ctypes.data if sd is not None else None), "zf_ctx_set_selector", ctx)
+
+
+def zf_mlp_create(device: int = 0, seed: int = 0) -> int:
+    out = _vp()
+    _check(_L.zf_mlp_create(device, seed, ctypes.byref(out)), "zf_mlp_create")
+    return out.value
+
+
+def zf_mlp_destroy(net: int) -> None:
+    _check(_L.zf_mlp_destroy(net), "zf_mlp_destroy")
+
+
+def zf_mlp_get_params(net: int) -> np.ndarray:
+    out = np.zeros(ZF_MLP_PARAMS, np.float32)
+    _check(_L.zf_mlp_get_params(net, out.ctypes.data), "zf_mlp_get_params")
+    return out
+
+
+def zf_mlp_set_params(net: int, params) -> None:
+    p = _f32(params)
+    assert p.size == ZF_MLP_PARAMS
+    _check(_L.zf_mlp_set_params(net, p.ctypes.data), "zf_mlp_set_params")
+
+
+def zf_mlp_forward(net: int, d_x: int, batch: int, d_logits: int, stream: int | None = None) -> None:
+    _check(_L.zf_mlp_forward(net, d_x, batch, d_logits, stream or None), "zf_mlp_forward")
+
+
+def zf_mlp_grad(net: int, d_x: int, d_y: int, d_mask: int, batch: int, d_grad: int, d_loss: int | None = None,
+                stream: int | None = None) -> None:
+    _check(_L.zf_mlp_grad(net, d_x, d_y, d_mask, batch, d_grad, d_loss or None, stream or None), "zf_mlp_grad")
+
+
+def zf_mlp_adam(net: int, d_grad: int, lr: float, stream: int | None = None) -> None:
+    _check(_L.zf_mlp_adam(net, d_grad, lr, stream or None), "zf_mlp_adam")
+
+
+def zf_mlp_train(net: int, x, y, mask, epochs: int, batch: int, lr: float, seed: int = 0) -> np.ndarray:
+    x = _f32(x)
+    y = np.ascontiguousarray(y, dtype=np.int32)
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    losses = np.zeros(epochs, np.float32)
+    _check(_L.zf_mlp_train(net, x.ctypes.data, y.ctypes.data, m.ctypes.data, len(y), epochs, batch, lr, seed,
+                           losses.ctypes.data), "zf_mlp_train")
+    return losses
+
+
+def zf_mlp_predict(net: int, x, mask) -> np.ndarray:
+    x = _f32(x)
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    out = np.zeros(len(x), np.int32)
+    _check(_L.zf_mlp_predict(net, x.ctypes.data, m.ctypes.data, len(x), out.ctypes.data), "zf_mlp_predict")
+    return out

@@ -1,11 +1,13 @@
-// zf_device.cuh -- device-side decode of one warp tile (1024 output rows) of
-// one chunk, per scheme.
+// zf_device.cuh -- device-side decode of one warp job: up to K consecutive
+// 1024-row warp tiles of one chunk, per scheme.
 //
-// A launch decodes a list of chunks (ZfDevChunk).  A CTA takes a CTA tile of
-// `tile_rows` rows of one chunk; each of its warps decodes 1024-row warp
-// tiles of it on its own, with its own slice of shared memory and no
-// CTA-wide barrier, so an SM keeps dozens of independent warp tiles in
-// flight.  The decoders follow the parallel patterns of Section 3.1:
+// A launch decodes a list of chunks (ZfDevChunk) cut into warp jobs.  Each
+// warp decodes its job alone, in its own slice of shared memory, with no
+// CTA-wide barrier.  Inside a job the warp fetches all block / directory
+// metadata of its tiles at once and copies the next tile's compressed bytes
+// into shared memory (cp.async, double-buffered) while it decodes the
+// current tile, so DRAM latency overlaps the decode.  The decoders follow
+// the parallel patterns of Section 3.1:
 //   fp_warp     Fully-Parallel: FOR / dictionary / raw.  The warp stages the
 //               tile's packed words in shared memory with coalesced 16-byte
 //               loads, then every lane extracts C = 16/sizeof(T) consecutive
@@ -23,6 +25,7 @@
 // A failed check of the stream sets a bit in the launch's error word; the
 // tile then writes in-bounds placeholder values.  Nothing traps.
 #pragma once
+#include <cuda_pipeline.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -83,6 +86,18 @@ __device__ __forceinline__ void warp_stage(uint32_t* wsm, const uint8_t* src, ui
     __syncwarp();
 }
 
+// One 256-bit store of four 64-bit words to a 32-byte aligned global address:
+// a lane writes a whole L2 sector at once.  st.global takes a global-space
+// address, so the generic pointer is converted first.  Decoders take a WS
+// template flag: only the single-scheme kernels use this store (in the
+// batched kernel's out-of-line dispatch it wrote only its first word on
+// sm_103a, so that kernel keeps 16-byte stores).
+__device__ __forceinline__ void store32(void* dst, unsigned long long a, unsigned long long b, unsigned long long c,
+                                        unsigned long long d) {
+    const size_t g = __cvta_generic_to_global(dst);
+    asm volatile("st.global.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(g), "l"(a), "l"(b), "l"(c), "l"(d) : "memory");
+}
+
 // Store N consecutive values of type T with the widest aligned vector stores
 // (the values are packed into 32-bit words in registers first).  32-byte rows
 // use one 256-bit store when `al32` says the address is 32-byte aligned, so
@@ -103,12 +118,8 @@ __device__ __forceinline__ void store_vec(T* dst, const T (&v)[N], bool al32 = f
     }
     if constexpr (W == 8) {
         if (al32) {
-            ulonglong4_32a q;
-            q.x = ((unsigned long long)w[1] << 32) | w[0];
-            q.y = ((unsigned long long)w[3] << 32) | w[2];
-            q.z = ((unsigned long long)w[5] << 32) | w[4];
-            q.w = ((unsigned long long)w[7] << 32) | w[6];
-            *reinterpret_cast<ulonglong4_32a*>(dst) = q;
+            store32(dst, ((unsigned long long)w[1] << 32) | w[0], ((unsigned long long)w[3] << 32) | w[2],
+                    ((unsigned long long)w[5] << 32) | w[4], ((unsigned long long)w[7] << 32) | w[6]);
             return;
         }
     }
@@ -144,10 +155,35 @@ __device__ __forceinline__ uint32_t warp_incl_max(uint32_t x, uint32_t lane) {
     return x;
 }
 
-// ---------------------------------------------------------------- Fully-Parallel
-template <bool NARROW, class S>
-__device__ __forceinline__ void extract4(const uint32_t* wsm, uint32_t bitpos, uint32_t b, S (&u)[4]);
+// ---------------------------------------------------------------- async staging
+// Copy `nbytes` (rounded up to 16) from a 16-byte aligned global address into
+// a warp's shared-memory buffer with cp.async, 16 bytes per lane per step.
+// The caller commits the group.
+__device__ __forceinline__ void stage_async(uint32_t* buf, const uint8_t* src, uint32_t nbytes, uint32_t lane) {
+    const uint32_t nvec = (nbytes + 15) >> 4;
+    for (uint32_t i = lane; i < nvec; i += 32) __pipeline_memcpy_async(buf + 4 * i, src + 16ull * i, 16);
+}
 
+// Four consecutive b-bit values starting at bit `bitpos`.  NARROW needs
+// b <= 8 (4b + 31 <= 63: one 64-bit window of two words).
+template <bool NARROW, class S>
+__device__ __forceinline__ void extract4(const uint32_t* wsm, uint32_t bitpos, uint32_t b, S (&u)[4]) {
+    if constexpr (NARROW) {
+        const uint32_t w = bitpos >> 5, sh = bitpos & 31;
+        const uint64_t x = ((((uint64_t)wsm[w + 1]) << 32) | wsm[w]) >> sh;
+        const uint32_t m = (1u << b) - 1u;
+#pragma unroll
+        for (int k = 0; k < 4; k++) u[k] = (S)((uint32_t)(x >> (k * b)) & m);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++) u[k] = (S)extract(wsm, bitpos + k * b, b);
+    }
+}
+
+// Bytes of one staging buffer of a warp for packed payloads of width bmax.
+__host__ __device__ inline uint32_t stage_bytes_for(uint32_t bmax) { return ((kWarpRows * bmax / 8 + 15) & ~15u) + 32; }
+
+// ---------------------------------------------------------------- Fully-Parallel
 // Extract and store the rows of a staged FOR/dictionary warp tile; returns
 // true if a dictionary code was out of range.
 template <class T, int SCHEME, bool NARROW>
@@ -175,8 +211,9 @@ __device__ __forceinline__ bool fp_rows(const ZfDevChunk& c, const Hdr& h, T* ds
             if constexpr (SCHEME == ZF_FOR_BP) {
                 v[k] = (T)(ref + (T)u[k]);
             } else {
-                bad |= u[k] >= h.n_aux;
-                v[k] = u[k] < h.n_aux ? __ldg(dict + u[k]) : (T)0;
+                const bool in = i0 + k < nr;
+                bad |= in && u[k] >= h.n_aux;
+                v[k] = (in && u[k] < h.n_aux) ? __ldg(dict + u[k]) : (T)0;
             }
         }
         if (i0 + V <= nr) store_vec<T, V>(dst + i0, v);
@@ -186,19 +223,21 @@ __device__ __forceinline__ bool fp_rows(const ZfDevChunk& c, const Hdr& h, T* ds
     return bad;
 }
 
-// SCHEME: ZF_FOR_BP, ZF_DICT_BP or ZF_RAW.  Rows [r0, r0+nr) of the chunk, nr <= 1024.
+// SCHEME: ZF_FOR_BP, ZF_DICT_BP or ZF_RAW.  Rows [r0, r0 + nrows) of the chunk
+// (r0 a multiple of 1024).  The packed stream of consecutive tiles is
+// contiguous, so tile i+1 is staged while tile i decodes.
 template <class T, int SCHEME>
-__device__ void fp_warp(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t nr, uint32_t* wsm,
-                        uint32_t* err) {
+__device__ void fp_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t nrows, uint32_t* wsm,
+                       uint32_t* err) {
     constexpr int V = 16 / sizeof(T);
     const uint32_t lane = threadIdx.x & 31;
     T* dst = reinterpret_cast<T*>(c.dst) + r0;
     if constexpr (SCHEME == ZF_RAW) {
         const T* src = reinterpret_cast<const T*>(c.blob + h.off[0]) + r0;
-        for (uint32_t i0 = lane * V; i0 < nr; i0 += 32 * V) {
-            if (i0 + V <= nr) reinterpret_cast<uint4*>(dst + i0)[0] = ldg16(src + i0);
+        for (uint32_t i0 = lane * V; i0 < nrows; i0 += 32 * V) {
+            if (i0 + V <= nrows) reinterpret_cast<uint4*>(dst + i0)[0] = ldg16(src + i0);
             else
-                for (uint32_t i = i0; i < nr; i++) dst[i] = src[i];
+                for (uint32_t i = i0; i < nrows; i++) dst[i] = src[i];
         }
     } else {
         const uint32_t b = h.b;
@@ -207,33 +246,35 @@ __device__ void fp_warp(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t
             return;
         }
         const uint8_t* sec = c.blob + h.off[SCHEME == ZF_DICT_BP ? 1 : 0];
-        warp_stage(wsm, sec + ((uint64_t)r0 * b >> 3), (nr * b + 7) >> 3, lane);
-        bool bad;
-        if (V == 4 && b <= 8) bad = fp_rows<T, SCHEME, true>(c, h, dst, wsm, nr, b, lane);
-        else bad = fp_rows<T, SCHEME, false>(c, h, dst, wsm, nr, b, lane);
+        const uint32_t sb = stage_bytes_for(b) / 4;          // words per staging buffer
+        const uint32_t ntiles = (nrows + kWarpRows - 1) / kWarpRows;
+        auto issue = [&](uint32_t i) {
+            const uint32_t rr = r0 + i * kWarpRows, nr = min(kWarpRows, r0 + nrows - rr);
+            stage_async(wsm + (i & 1) * sb, sec + ((uint64_t)rr * b >> 3), (nr * b + 7) >> 3, lane);
+            __pipeline_commit();
+        };
+        issue(0);
+        bool bad = false;
+        for (uint32_t i = 0; i < ntiles; i++) {
+            if (i + 1 < ntiles) {
+                issue(i + 1);
+                __pipeline_wait_prior(1);
+            } else {
+                __pipeline_wait_prior(0);
+            }
+            __syncwarp();
+            const uint32_t nr = min(kWarpRows, nrows - i * kWarpRows);
+            const uint32_t* buf = wsm + (i & 1) * sb;
+            if (V == 4 && b <= 8) bad |= fp_rows<T, SCHEME, true>(c, h, dst + i * kWarpRows, buf, nr, b, lane);
+            else bad |= fp_rows<T, SCHEME, false>(c, h, dst + i * kWarpRows, buf, nr, b, lane);
+            __syncwarp();
+        }
         if (bad) report(err, ZF_ECORRUPT, c.chunk_id);
-        __syncwarp();
     }
 }
 
 // ---------------------------------------------------------------- delta (Group-Parallel)
 // One 1024-row block: x_j = base + j*min_d + sum_{k=1..j} u_k (mod 2^width).
-// Four consecutive b-bit values starting at bit `bitpos`.  WIDE = false needs
-// b <= 8 (4b + 31 <= 63: one 64-bit window of two words).
-template <bool NARROW, class S>
-__device__ __forceinline__ void extract4(const uint32_t* wsm, uint32_t bitpos, uint32_t b, S (&u)[4]) {
-    if constexpr (NARROW) {
-        const uint32_t w = bitpos >> 5, sh = bitpos & 31;
-        const uint64_t x = ((((uint64_t)wsm[w + 1]) << 32) | wsm[w]) >> sh;
-        const uint32_t m = (1u << b) - 1u;
-#pragma unroll
-        for (int k = 0; k < 4; k++) u[k] = (S)((uint32_t)(x >> (k * b)) & m);
-    } else {
-#pragma unroll
-        for (int k = 0; k < 4; k++) u[k] = (S)extract(wsm, bitpos + k * b, b);
-    }
-}
-
 template <class T, class S, bool NARROW>
 __device__ __forceinline__ void delta_rows(T* dst, const uint32_t* wsm, uint32_t mk, uint32_t b, uint64_t base,
                                            uint64_t min_d, uint32_t lane, bool al32) {
@@ -321,104 +362,181 @@ __device__ __forceinline__ void delta_rows_pair(T* dst, const uint32_t* wsm, uin
     }
 }
 
-template <class T>
-__device__ void delta_warp(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t nr, uint32_t* wsm,
-                           uint32_t* err) {
+// One 1024-row block with each lane owning 32 consecutive values
+// [32*lane, 32*lane + 32): a single warp scan per block.  The lane's bits
+// start on a word boundary (32*lane*b bits = lane*b words), so every lane
+// walks the same bit positions and the refill of the two-word bit reader is
+// uniform across the warp.  The 32 differences are read once into registers
+// and summed in place; values leave in 32-byte stores (four int64 or eight
+// int32), each a whole L2 sector.  WIDE (b > 21): 64-bit sums and
+// funnel-shift extraction; otherwise 32-bit sums (32 * 1024 * (2^21 - 1) < 2^32).
+template <class T, bool WIDE, bool WS>
+__device__ __forceinline__ void delta_block_lanes(T* dst, const uint32_t* wsm, uint32_t mk, uint32_t b, uint64_t base,
+                                                  uint64_t min_d, uint32_t lane) {
+    using U = typename std::conditional<sizeof(T) == 8, unsigned long long, unsigned int>::type;
+    using S = typename std::conditional<WIDE, unsigned long long, unsigned int>::type;
+    constexpr int PER = 32 / sizeof(T);           // values per 32-byte store
+    const uint32_t j0 = lane * 32;
+    const uint32_t nv = mk > j0 ? min(32u, mk - j0) : 0u;   // valid values of this lane
+    // inclusive prefix of the lane's differences (u_0 of the block counts as 0)
+    S pre[32];
+    if constexpr (!WIDE) {
+        const uint32_t mask = (1u << b) - 1u;
+        uint32_t wi = lane * b;
+        uint32_t lo = wsm[wi], hi = wsm[wi + 1];
+        wi += 2;
+        uint32_t pos = 0;
+        uint32_t run = 0;
+#pragma unroll
+        for (int k = 0; k < 32; k++) {
+            const uint32_t u = __funnelshift_r(lo, hi, pos) & mask;
+            run += ((uint32_t)k < nv && (j0 + k) > 0) ? u : 0u;
+            pre[k] = run;
+            pos += b;
+            if (pos >= 32) {
+                lo = hi;
+                hi = wsm[wi++];
+                pos -= 32;
+            }
+        }
+    } else {
+        // wide differences: the total first, the values re-read below
+        S run = 0;
+        for (uint32_t k = 0; k < nv; k++)
+            if (j0 + k > 0) run += (S)extract(wsm, (j0 + k) * b, b);
+        pre[31] = run;
+    }
+    const S total = pre[31];
+    const S excl = warp_incl_sum<S>(total, lane) - total;
+    const U md = (U)min_d;
+    U t = (U)base + (U)j0 * md + (U)excl;        // x_j = t + (j - j0) * min_d + pre[j - j0]
+    const bool al32 = WS && (reinterpret_cast<uintptr_t>(dst + j0) & 31) == 0;
+    S wrun = 0;
+#pragma unroll
+    for (int q = 0; q < 32 / PER; q++) {
+        T v[PER];
+#pragma unroll
+        for (int e = 0; e < PER; e++) {
+            const int k = q * PER + e;
+            if constexpr (WIDE) {
+                if ((uint32_t)k < nv && (j0 + k) > 0) wrun += (S)extract(wsm, (j0 + k) * b, b);
+                v[e] = (T)(t + (U)wrun);
+            } else {
+                v[e] = (T)(t + (U)pre[k]);
+            }
+            t += md;
+        }
+        if ((uint32_t)(q * PER + PER) <= nv) {
+            if (WS && al32) {
+                if constexpr (sizeof(T) == 8) {
+                    store32(dst + j0 + q * PER, (uint64_t)v[0], (uint64_t)v[1], (uint64_t)v[2], (uint64_t)v[3]);
+                } else {
+                    store32(dst + j0 + q * PER, ((uint64_t)(uint32_t)v[1] << 32) | (uint32_t)v[0],
+                            ((uint64_t)(uint32_t)v[3] << 32) | (uint32_t)v[2],
+                            ((uint64_t)(uint32_t)v[5] << 32) | (uint32_t)v[4],
+                            ((uint64_t)(uint32_t)v[7] << 32) | (uint32_t)v[6]);
+                }
+            } else {
+                store_vec<T, PER>(dst + j0 + q * PER, v);
+            }
+        } else {
+            for (uint32_t e = 0; q * PER + e < nv; e++) dst[j0 + q * PER + e] = v[e];
+        }
+    }
+}
+
+// Blocks of rows [r0, r0 + nrows) (r0 a multiple of 1024, at most 32 blocks).
+// Lane j holds block j's 24-byte entry; block i+1's payload is staged while
+// block i decodes.
+template <class T, bool WS>
+__device__ void delta_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t nrows, uint32_t* wsm,
+                          uint32_t* err, uint32_t bmax) {
     using U = typename std::conditional<sizeof(T) == 8, unsigned long long, unsigned int>::type;
     const uint32_t lane = threadIdx.x & 31;
-    const uint32_t blk = r0 / zf::kDeltaBlock;
-    const uint8_t* e = c.blob + h.off[0] + (uint64_t)blk * zf::kDeltaEntry;
-    // 24-byte entry: base, min_d, payload offset, b (8-byte aligned)
-    uint2 e0 = __ldg(reinterpret_cast<const uint2*>(e));
-    uint2 e1 = __ldg(reinterpret_cast<const uint2*>(e + 8));
-    uint2 e2 = __ldg(reinterpret_cast<const uint2*>(e + 16));
-    uint64_t base = ((uint64_t)e0.y << 32) | e0.x;
-    uint64_t min_d = ((uint64_t)e1.y << 32) | e1.x;
-    uint32_t poff = e2.x, b = e2.y & 0xFF;
-    uint32_t nbytes = (nr * b + 7) >> 3;
-    if (b > 8 * sizeof(T) || (poff & 15) || (uint64_t)poff + nbytes > h.len[1] || nr > zf::kDeltaBlock) {
-        if (lane == 0) report(err, ZF_ECORRUPT, c.chunk_id);
-        return;
+    const uint32_t blk0 = r0 / zf::kDeltaBlock;
+    const uint32_t nblk = (nrows + zf::kDeltaBlock - 1) / zf::kDeltaBlock;
+    uint64_t e_base = 0, e_md = 0;
+    uint32_t e_poff = 0, e_b = 0;
+    if (lane < nblk) {
+        const uint8_t* e = c.blob + h.off[0] + (uint64_t)(blk0 + lane) * zf::kDeltaEntry;
+        const uint2 e0 = __ldg(reinterpret_cast<const uint2*>(e));
+        const uint2 e1 = __ldg(reinterpret_cast<const uint2*>(e + 8));
+        const uint2 e2 = __ldg(reinterpret_cast<const uint2*>(e + 16));
+        e_base = ((uint64_t)e0.y << 32) | e0.x;
+        e_md = ((uint64_t)e1.y << 32) | e1.x;
+        e_poff = e2.x;
+        e_b = e2.y & 0xFF;
     }
-    warp_stage(wsm, c.blob + h.off[1] + poff, nbytes, lane);
-    T* dst = reinterpret_cast<T*>(c.dst) + r0;
-    const bool al32 = (reinterpret_cast<uintptr_t>(dst) & 31) == 0;
-    // 128 values of at most 24 bits sum below 2^31: scan in 32 bits
-    if (b <= 8) delta_rows_pair<T>(dst, wsm, nr, b, base, min_d, lane, al32);
-    else if (b <= 24) delta_rows<T, uint32_t, false>(dst, wsm, nr, b, base, min_d, lane, al32);
-    else delta_rows<T, U, false>(dst, wsm, nr, b, base, min_d, lane, al32);
-    __syncwarp();
+    // a block whose entry is inconsistent is reported and skipped
+    const uint32_t mk_lane = min(zf::kDeltaBlock, nrows - min(nrows, lane * zf::kDeltaBlock));
+    const bool lane_ok = lane >= nblk || (e_b <= 8 * sizeof(T) && e_b <= bmax && !(e_poff & 15) &&
+                                          (uint64_t)e_poff + ((mk_lane * e_b + 7) >> 3) <= h.len[1]);
+    const uint32_t ok_mask = __ballot_sync(0xFFFFFFFFu, lane_ok);
+    if (ok_mask != 0xFFFFFFFFu && lane == 0) report(err, ZF_ECORRUPT, c.chunk_id);
+    const uint32_t sb = stage_bytes_for(bmax) / 4;
+    const uint8_t* payload = c.blob + h.off[1];
+    auto issue = [&](uint32_t i) {
+        const uint32_t poff = __shfl_sync(0xFFFFFFFFu, e_poff, i);
+        const uint32_t b = __shfl_sync(0xFFFFFFFFu, e_b, i);
+        const uint32_t mk = min(zf::kDeltaBlock, nrows - i * zf::kDeltaBlock);
+        if ((ok_mask >> i) & 1) stage_async(wsm + (i & 1) * sb, payload + poff, (mk * b + 7) >> 3, lane);
+        __pipeline_commit();
+    };
+    issue(0);
+    for (uint32_t i = 0; i < nblk; i++) {
+        if (i + 1 < nblk) {
+            issue(i + 1);
+            __pipeline_wait_prior(1);
+        } else {
+            __pipeline_wait_prior(0);
+        }
+        __syncwarp();
+        const uint64_t base = __shfl_sync(0xFFFFFFFFu, e_base, i);
+        const uint64_t md = __shfl_sync(0xFFFFFFFFu, e_md, i);
+        const uint32_t b = __shfl_sync(0xFFFFFFFFu, e_b, i);
+        const uint32_t mk = min(zf::kDeltaBlock, nrows - i * zf::kDeltaBlock);
+        if ((ok_mask >> i) & 1) {
+            T* dst = reinterpret_cast<T*>(c.dst) + r0 + i * zf::kDeltaBlock;
+            const bool al32 = (reinterpret_cast<uintptr_t>(dst) & 31) == 0;
+            const uint32_t* buf = wsm + (i & 1) * sb;
+            if (b <= 21) delta_block_lanes<T, false, WS>(dst, buf, mk, b, base, md, lane);
+            else delta_block_lanes<T, true, WS>(dst, buf, mk, b, base, md, lane);
+            (void)al32;
+        }
+        __syncwarp();
+    }
 }
 
 // ---------------------------------------------------------------- RLE (Group-Parallel)
-// The warp's slice holds one u16 per row -- the index (relative to the tile's
-// first run) of a run that starts at that row, 0 elsewhere -- followed by the
-// values of the tile's runs.
-template <class T>
-__device__ void rle_warp(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t nr, uint32_t* wsm,
-                         uint32_t* err) {
-    constexpr int V = 4;
-    const uint32_t lane = threadIdx.x & 31;
-    const T* vals = reinterpret_cast<const T*>(c.blob + h.off[0]);
-    const uint32_t* lens = reinterpret_cast<const uint32_t*>(c.blob + h.off[1]);
-    const uint2* dir = reinterpret_cast<const uint2*>(c.blob + h.off[2]);
-    const uint32_t R = h.n_aux;
-    const uint32_t t = r0 / zf::kRleDirRows;
-    const uint2 e0 = __ldg(dir + t);
-    const uint32_t rf = e0.x, skip = e0.y;
-    const bool last_tile = r0 + nr >= h.rows;
-    uint32_t rl = R - 1, next_skip = 0;
-    bool bad = false;
-    if (!last_tile) {
-        const uint2 e1 = __ldg(dir + t + 1);
-        next_skip = e1.y;
-        bad |= e1.y == 0 && e1.x == 0;
-        rl = e1.y > 0 ? e1.x : e1.x - 1;
-    }
-    bad |= r0 == 0 && (rf != 0 || skip != 0);
-    if (bad || R == 0 || rf > rl || rl >= R || rl - rf + 1 > nr + 1 || nr > zf::kRleDirRows || skip >= h.rows) {
-        if (lane == 0) report(err, ZF_ECORRUPT, c.chunk_id);
-        return;
-    }
-    const uint32_t m = rl - rf + 1;
-    uint16_t* mark = reinterpret_cast<uint16_t*>(wsm);
-    T* rv = reinterpret_cast<T*>(wsm + zf::kRleDirRows / 2);
+// Expansion of one 1024-row tile whose runs [rf, rf+m) have their lengths at
+// `lens` and values at `vals` (staged in shared memory, or in global memory
+// when the tile has more runs than a staging buffer holds).  `mark` is the
+// warp's 1024 u16 row marks.
+template <class T, bool WS>
+__device__ __forceinline__ void rle_rows(const ZfDevChunk& c, const Hdr& h, T* dst, const uint32_t* lens,
+                                         const T* vals, uint16_t* mark, uint32_t m, uint32_t skip, uint32_t nr,
+                                         bool last_tile, uint32_t next_skip, uint32_t lane, uint32_t* err) {
 #pragma unroll
     for (int q = 0; q < 4; q++) reinterpret_cast<uint4*>(mark)[lane + 32 * q] = make_uint4(0, 0, 0, 0);
     __syncwarp();
     // presum: start row of each run relative to the tile, 32 runs per step.
     // Lengths are at most the chunk's rows (< 2^30), and only the first and
     // last run of a tile can be longer than the tile, so 32-bit sums hold.
+    bool bad = false;
     uint32_t end = 0;                 // rows covered so far, counted from the first run's start
     uint32_t first_len = 0, last_start = 0;
-    for (uint32_t g0 = 0; g0 < m; g0 += 128) {
-        // four groups of 32 runs: independent loads first, then the scans
-        uint32_t Ls[4];
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const uint32_t i = g0 + 32 * q + lane;
-            Ls[q] = 0;
-            if (i < m) {
-                Ls[q] = __ldg(lens + rf + i);
-                rv[i] = __ldg(vals + rf + i);
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const uint32_t g = g0 + 32 * q;
-            if (g >= m) break;
-            const uint32_t i = g + lane;
-            const uint32_t L = Ls[q];
-            bad |= i < m && (L == 0 || L > h.rows);
-            const uint32_t incl = warp_incl_sum<uint32_t>(L, lane);
-            const uint32_t start = end + incl - L;   // relative to the first run's start
-            if (i < m && i > 0 && start >= skip && start - skip < nr) mark[start - skip] = (uint16_t)i;
-            if (g == 0) first_len = __shfl_sync(0xFFFFFFFFu, L, 0);
-            const uint32_t ls = __shfl_sync(0xFFFFFFFFu, start, (m - 1 - g) & 31);
-            if (m - 1 - g < 32) last_start = ls;
-            end += __shfl_sync(0xFFFFFFFFu, incl, 31);
-            if (end > 2u * (1u << 30) + 2048u) bad = true;
-        }
+    for (uint32_t g = 0; g < m; g += 32) {
+        const uint32_t i = g + lane;
+        const uint32_t L = i < m ? lens[i] : 0u;
+        bad |= i < m && (L == 0 || L > h.rows);
+        const uint32_t incl = warp_incl_sum<uint32_t>(L, lane);
+        const uint32_t start = end + incl - L;   // relative to the first run's start
+        if (i < m && i > 0 && start >= skip && start - skip < nr) mark[start - skip] = (uint16_t)i;
+        if (g == 0) first_len = __shfl_sync(0xFFFFFFFFu, L, 0);
+        const uint32_t ls = __shfl_sync(0xFFFFFFFFu, start, (m - 1 - g) & 31);
+        if (m - 1 - g < 32) last_start = ls;
+        end += __shfl_sync(0xFFFFFFFFu, incl, 31);
+        if (end > 2u * (1u << 30) + 2048u) bad = true;
     }
     // The runs cover exactly [0, nr): the first starts at or before row 0, the
     // last ends at nr or continues into the next tile by the directory's amount.
@@ -428,36 +546,167 @@ __device__ void rle_warp(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_
     const bool any_bad = __any_sync(0xFFFFFFFFu, bad);
     if (lane == 0 && (!ok || any_bad)) report(err, ZF_ECORRUPT, c.chunk_id);
     __syncwarp();
-    T* dst = reinterpret_cast<T*>(c.dst) + r0;
-    const bool al32 = (reinterpret_cast<uintptr_t>(dst) & 31) == 0;
+    // Expansion, two rows of 128 per step: lane l takes rows 4l..4l+3 of each.
+    // A row's run index is the largest mark at or before it: a running max
+    // over the lane's four marks, then one shuffle max-scan over lanes for
+    // both rows at once (16-bit halves, __vmaxu2; run indices are <= 1025).
+    constexpr int V = 4;
+    const bool al32 = WS && (reinterpret_cast<uintptr_t>(dst) & 31) == 0;
     uint32_t carry = 0;
-    for (uint32_t j0 = lane * V; j0 - lane * V < nr; j0 += 32 * V) {
-        const uint2 mk = reinterpret_cast<const uint2*>(mark)[j0 / 4];
-        uint32_t r[V];
-        r[0] = mk.x & 0xFFFF;
-        r[1] = max(r[0], mk.x >> 16);
-        r[2] = max(r[1], mk.y & 0xFFFF);
-        r[3] = max(r[2], mk.y >> 16);
-        const uint32_t incl = warp_incl_max(r[3], lane);
-        uint32_t before = __shfl_up_sync(0xFFFFFFFFu, incl, 1);
-        before = lane ? max(before, carry) : carry;
-        T v[V];
+    for (uint32_t row = 0; row * 128 < nr; row += 2) {
+        const uint32_t ja = row * 128 + lane * V, jb = ja + 128;
+        const uint2 ma = reinterpret_cast<const uint2*>(mark)[ja / 4];
+        const uint2 mb = reinterpret_cast<const uint2*>(mark)[jb / 4];
+        uint32_t ra[V], rb[V];
+        ra[0] = ma.x & 0xFFFF;
+        ra[1] = max(ra[0], ma.x >> 16);
+        ra[2] = max(ra[1], ma.y & 0xFFFF);
+        ra[3] = max(ra[2], ma.y >> 16);
+        rb[0] = mb.x & 0xFFFF;
+        rb[1] = max(rb[0], mb.x >> 16);
+        rb[2] = max(rb[1], mb.y & 0xFFFF);
+        rb[3] = max(rb[2], mb.y >> 16);
+        uint32_t x = ra[3] | (rb[3] << 16);
 #pragma unroll
-        for (int k = 0; k < V; k++) v[k] = rv[min(max(before, r[k]), m - 1)];
-        if (j0 + V <= nr) store_vec<T, V>(dst + j0, v, al32);
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+            if (lane >= (uint32_t)d) x = __vmaxu2(x, y);
+        }
+        const uint32_t tot = __shfl_sync(0xFFFFFFFFu, x, 31);
+        uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, x, 1);
+        if (lane == 0) prev = 0;
+        const uint32_t before_a = max(prev & 0xFFFFu, carry);
+        const uint32_t before_b = max(max(prev >> 16, carry), tot & 0xFFFFu);
+        T va[V], vb[V];
+#pragma unroll
+        for (int k = 0; k < V; k++) {
+            va[k] = vals[min(max(before_a, ra[k]), m - 1)];
+            vb[k] = vals[min(max(before_b, rb[k]), m - 1)];
+        }
+        if (ja + V <= nr) store_vec<T, V>(dst + ja, va, al32);
         else
-            for (uint32_t k = 0; j0 + k < nr; k++) dst[j0 + k] = v[k];
-        carry = max(carry, __shfl_sync(0xFFFFFFFFu, incl, 31));
+            for (uint32_t k = 0; ja + k < nr; k++) dst[ja + k] = va[k];
+        if (jb + V <= nr) store_vec<T, V>(dst + jb, vb, al32);
+        else
+            for (uint32_t k = 0; jb + k < nr; k++) dst[jb + k] = vb[k];
+        carry = max(carry, max(tot & 0xFFFFu, tot >> 16));
     }
     __syncwarp();
 }
 
+constexpr uint32_t kRleStageRuns = 256;   // runs per staging buffer
+
+// Shared memory of one RLE staging buffer: lengths then values.
+__host__ __device__ inline uint32_t rle_buf_bytes(uint32_t value_bytes) {
+    return kRleStageRuns * 4 + ((kRleStageRuns * value_bytes + 15) & ~15u);
+}
+
+// Tiles of rows [r0, r0 + nrows) (r0 a multiple of 1024, at most 31 tiles).
+// Lane j holds the directory entry of tile j (and of the tile after the
+// last); the next tile's lengths and values are staged while a tile expands.
+template <class T, bool WS>
+__device__ void rle_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t nrows, uint32_t* wsm,
+                        uint32_t* err) {
+    const uint32_t lane = threadIdx.x & 31;
+    const T* vals = reinterpret_cast<const T*>(c.blob + h.off[0]);
+    const uint32_t* lens = reinterpret_cast<const uint32_t*>(c.blob + h.off[1]);
+    const uint2* dir = reinterpret_cast<const uint2*>(c.blob + h.off[2]);
+    const uint32_t R = h.n_aux;
+    const uint32_t t0 = r0 / zf::kRleDirRows;
+    const uint32_t nt = (nrows + zf::kRleDirRows - 1) / zf::kRleDirRows;
+    const uint32_t tiles_in_chunk = (h.rows + zf::kRleDirRows - 1) / zf::kRleDirRows;
+    uint2 d = make_uint2(0, 0);
+    if (lane <= nt && t0 + lane < tiles_in_chunk) d = __ldg(dir + t0 + lane);
+    uint16_t* mark = reinterpret_cast<uint16_t*>(wsm);
+    uint8_t* bufs = reinterpret_cast<uint8_t*>(wsm) + zf::kRleDirRows * 2;
+    const uint32_t bb = rle_buf_bytes(sizeof(T));
+    // run range [rf, rf + m) of tile i, or m = 0 if its directory entries are inconsistent
+    auto runs = [&](uint32_t i, uint32_t& rf, uint32_t& skip, uint32_t& m, uint32_t& next_skip, bool& last) {
+        rf = __shfl_sync(0xFFFFFFFFu, d.x, i);
+        skip = __shfl_sync(0xFFFFFFFFu, d.y, i);
+        const uint32_t nx = __shfl_sync(0xFFFFFFFFu, d.x, i + 1);
+        next_skip = __shfl_sync(0xFFFFFFFFu, d.y, i + 1);
+        const uint32_t rr = r0 + i * zf::kRleDirRows, nr = min(zf::kRleDirRows, r0 + nrows - rr);
+        last = rr + nr >= h.rows;
+        uint32_t rl = R - 1;
+        bool bad = (rr == 0 && (rf != 0 || skip != 0)) || R == 0 || skip >= h.rows;
+        if (!last) {
+            bad |= next_skip == 0 && nx == 0;
+            rl = next_skip > 0 ? nx : nx - 1;
+        } else {
+            next_skip = 0;
+        }
+        bad |= rf > rl || rl >= R || rl - rf + 1 > nr + 1;
+        m = bad ? 0 : rl - rf + 1;
+    };
+    auto issue = [&](uint32_t i) {
+        uint32_t rf, skip, m, ns;
+        bool last;
+        runs(i, rf, skip, m, ns, last);
+        if (m && m <= kRleStageRuns) {
+            uint8_t* b = bufs + (i & 1) * bb;
+            uint32_t* ls = reinterpret_cast<uint32_t*>(b);
+            T* vs = reinterpret_cast<T*>(b + kRleStageRuns * 4);
+            for (uint32_t k = lane; k < m; k += 32) {
+                __pipeline_memcpy_async(ls + k, lens + rf + k, 4);
+                __pipeline_memcpy_async(vs + k, vals + rf + k, sizeof(T));
+            }
+        }
+        __pipeline_commit();
+    };
+    issue(0);
+    for (uint32_t i = 0; i < nt; i++) {
+        if (i + 1 < nt) {
+            issue(i + 1);
+            __pipeline_wait_prior(1);
+        } else {
+            __pipeline_wait_prior(0);
+        }
+        __syncwarp();
+        uint32_t rf, skip, m, ns;
+        bool last;
+        runs(i, rf, skip, m, ns, last);
+        const uint32_t rr = r0 + i * zf::kRleDirRows, nr = min(zf::kRleDirRows, r0 + nrows - rr);
+        if (!m) {
+            if (lane == 0) report(err, ZF_ECORRUPT, c.chunk_id);
+        } else {
+            T* dst = reinterpret_cast<T*>(c.dst) + rr;
+            if (m <= kRleStageRuns) {
+                const uint8_t* b = bufs + (i & 1) * bb;
+                rle_rows<T, WS>(c, h, dst, reinterpret_cast<const uint32_t*>(b),
+                            reinterpret_cast<const T*>(b + kRleStageRuns * 4), mark, m, skip, nr, last, ns, lane, err);
+            } else {
+                rle_rows<T, WS>(c, h, dst, lens + rf, vals + rf, mark, m, skip, nr, last, ns, lane, err);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------- single-tile entry points
+// (used by the allocation-free kernel; 16-byte stores only)
+template <class T, int SCHEME>
+__device__ __forceinline__ void fp_warp(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t nr, uint32_t* wsm,
+                                        uint32_t* err) {
+    fp_job<T, SCHEME>(c, h, r0, nr, wsm, err);
+}
+template <class T>
+__device__ __forceinline__ void delta_warp(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t nr,
+                                           uint32_t* wsm, uint32_t* err) {
+    delta_job<T, false>(c, h, r0, nr, wsm, err, 8 * sizeof(T));
+}
+template <class T>
+__device__ __forceinline__ void rle_warp(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t nr, uint32_t* wsm,
+                                         uint32_t* err) {
+    rle_job<T, false>(c, h, r0, nr, wsm, err);
+}
+
 // Shared memory (bytes) one warp needs for a scheme, given the value size and
-// the widest bit width of the chunks it decodes.
+// the widest bit width of the chunks it decodes (two staging buffers).
 __host__ __device__ inline uint32_t warp_smem(int scheme, uint32_t value_bytes, uint32_t bmax) {
     switch (scheme) {
-    case ZF_FOR_BP: case ZF_DICT_BP: case ZF_DELTA_BP: return ((kWarpRows * bmax / 8 + 15) & ~15u) + 32;
-    case ZF_RLE: return kWarpRows * 2 + (((kWarpRows + 1) * value_bytes + 15) & ~15u);  // marks + run values
+    case ZF_FOR_BP: case ZF_DICT_BP: case ZF_DELTA_BP: return 2 * stage_bytes_for(bmax);
+    case ZF_RLE: return kWarpRows * 2 + 2 * rle_buf_bytes(value_bytes);
     }
     return 0;
 }

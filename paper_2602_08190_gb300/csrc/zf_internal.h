@@ -21,7 +21,7 @@ constexpr uint32_t kLzBlock = 65536;           // bytes per LZ77 block
 constexpr uint32_t kLzMinMatch = 4;
 constexpr uint32_t kLzMaxOffset = 65535;
 constexpr uint32_t kMaxDict = 65536;
-constexpr uint32_t kMaxTileRows = 65536;
+constexpr uint32_t kMaxTileRows = 16384;   // rows per warp job (16 warp tiles)
 
 inline uint64_t align16(uint64_t x) { return (x + 15) & ~uint64_t(15); }
 inline uint32_t bits_of(uint64_t x) { return x ? 64u - (uint32_t)__builtin_clzll(x) : 0u; }
@@ -64,11 +64,13 @@ struct ZfDevChunk {
     uint8_t* dst;            // device address of the chunk's row 0 in the output
     uint64_t dst_cap;        // writable bytes at dst
     uint32_t rows;
-    uint32_t tile0;          // first tile of this chunk within the launch
-    uint32_t ntiles;
+    uint32_t tile0;          // first warp job of this chunk within the launch
+    uint32_t ntiles;         // warp jobs of this chunk
     uint32_t blob_bytes;
     uint32_t chunk_id;       // index reported with a decode error
-    uint8_t scheme, dtype, pad0, pad1;
+    uint8_t scheme, dtype;
+    uint8_t bmax;            // widest bit width of the chunk (sizes the staging buffers)
+    uint8_t pad1;
     uint32_t pad2[4];
 };
 static_assert(sizeof(ZfDevChunk) == 64, "descriptor layout");

@@ -21,52 +21,53 @@ namespace {
 struct LaunchArgs {
     const ZfDevChunk* chunks;
     uint32_t nchunks;
-    uint32_t ntiles;
-    uint32_t tile_rows;    // rows of one CTA tile (a multiple of 1024)
+    uint32_t njobs;        // warp jobs in the launch
+    uint32_t job_rows;     // rows of one warp job (a multiple of 1024)
     uint32_t warp_smem;    // bytes of shared memory per warp
     uint32_t* err;
-    uint32_t* queue;       // [0] next tile, [1] CTAs done; null for static striding
+    uint32_t* queue;       // [0] next job, [1] CTAs done; batched launches only
 };
 
-__device__ __forceinline__ uint32_t find_chunk(const ZfDevChunk* ch, uint32_t n, uint32_t tile) {
+__device__ __forceinline__ uint32_t find_chunk(const ZfDevChunk* ch, uint32_t n, uint32_t job) {
     uint32_t a = 0, z = n;
     while (z - a > 1) {
         uint32_t mid = (a + z) >> 1;
-        if (__ldg(&ch[mid].tile0) <= tile) a = mid;
+        if (__ldg(&ch[mid].tile0) <= job) a = mid;
         else z = mid;
     }
     return a;
 }
 
-template <int SCHEME, int DT>
-__device__ __forceinline__ void decode_one(const ZfDevChunk& c, const zfd::Hdr& h, uint32_t r0, uint32_t nr,
+// WS: 256-bit stores (single-scheme kernels only).
+template <int SCHEME, int DT, bool WS>
+__device__ __forceinline__ void decode_one(const ZfDevChunk& c, const zfd::Hdr& h, uint32_t r0, uint32_t nrows,
                                            uint32_t* wsm, uint32_t* err) {
     if constexpr (DT == ZF_I32 || DT == ZF_I64) {
         using T = typename std::conditional<DT == ZF_I64, int64_t, int32_t>::type;
         if constexpr (SCHEME == ZF_FOR_BP || SCHEME == ZF_DICT_BP || SCHEME == ZF_RAW)
-            zfd::fp_warp<T, SCHEME>(c, h, r0, nr, wsm, err);
+            zfd::fp_job<T, SCHEME>(c, h, r0, nrows, wsm, err);
         else if constexpr (SCHEME == ZF_DELTA_BP)
-            zfd::delta_warp<T>(c, h, r0, nr, wsm, err);
+            zfd::delta_job<T, WS>(c, h, r0, nrows, wsm, err, c.bmax);
         else if constexpr (SCHEME == ZF_RLE)
-            zfd::rle_warp<T>(c, h, r0, nr, wsm, err);
+            zfd::rle_job<T, WS>(c, h, r0, nrows, wsm, err);
     } else if constexpr (DT == ZF_BYTES && SCHEME == ZF_RAW) {
         // raw bytes: 16-byte copies
         const uint32_t lane = threadIdx.x & 31;
         const uint8_t* src = c.blob + h.off[0] + r0;
         uint8_t* dst = c.dst + r0;
-        for (uint32_t i0 = lane * 16; i0 < nr; i0 += 512) {
-            if (i0 + 16 <= nr) reinterpret_cast<uint4*>(dst + i0)[0] = zfd::ldg16(src + i0);
+        for (uint32_t i0 = lane * 16; i0 < nrows; i0 += 512) {
+            if (i0 + 16 <= nrows) reinterpret_cast<uint4*>(dst + i0)[0] = zfd::ldg16(src + i0);
             else
-                for (uint32_t i = i0; i < nr; i++) dst[i] = src[i];
+                for (uint32_t i = i0; i < nrows; i++) dst[i] = src[i];
         }
     }
 }
 
-__device__ __noinline__ void decode_mixed(const ZfDevChunk& c, const zfd::Hdr& h, uint32_t r0, uint32_t nr,
+__device__ __noinline__ void decode_mixed(const ZfDevChunk& c, const zfd::Hdr& h, uint32_t r0, uint32_t nrows,
                                           uint32_t* wsm, uint32_t* err) {
     switch (c.scheme * 4 + c.dtype) {
 #define ZF_CASE(S, D) \
-    case S * 4 + D: decode_one<S, D>(c, h, r0, nr, wsm, err); break;
+    case S * 4 + D: decode_one<S, D, false>(c, h, r0, nrows, wsm, err); break;
         ZF_CASE(ZF_RAW, ZF_I32) ZF_CASE(ZF_RAW, ZF_I64) ZF_CASE(ZF_RAW, ZF_BYTES)
         ZF_CASE(ZF_FOR_BP, ZF_I32) ZF_CASE(ZF_FOR_BP, ZF_I64)
         ZF_CASE(ZF_DICT_BP, ZF_I32) ZF_CASE(ZF_DICT_BP, ZF_I64)
@@ -78,49 +79,49 @@ __device__ __noinline__ void decode_mixed(const ZfDevChunk& c, const zfd::Hdr& h
     }
 }
 
-// A CTA decodes CTA tiles (tile_rows rows of one chunk); its warps take the
-// tile's 1024-row warp tiles in turn.  Specialized launches stride over the
-// tiles statically; the batched launch pops them from a work queue.
+// One warp job of a chunk: job_rows consecutive rows (the last job of a
+// chunk may be shorter).
+template <int SCHEME, int DT>
+__device__ __forceinline__ void run_job(const LaunchArgs& a, uint32_t job, uint32_t* wsm) {
+    const uint32_t k = find_chunk(a.chunks, a.nchunks, job);
+    const ZfDevChunk c = a.chunks[k];
+    zfd::Hdr h;
+    zfd::load_hdr(c.blob, h);
+    const uint32_t r0 = (job - c.tile0) * a.job_rows;
+    const uint32_t sz = c.dtype == ZF_I64 ? 8 : c.dtype == ZF_I32 ? 4 : 1;
+    if (h.rows != c.rows || r0 >= c.rows || (uint64_t)c.rows * sz > c.dst_cap) {
+        if ((threadIdx.x & 31) == 0) zfd::report(a.err, ZF_ECORRUPT, c.chunk_id);
+        return;
+    }
+    const uint32_t nrows = min(a.job_rows, c.rows - r0);
+    if constexpr (SCHEME < 0) decode_mixed(c, h, r0, nrows, wsm, a.err);
+    else decode_one<SCHEME, DT, true>(c, h, r0, nrows, wsm, a.err);
+}
+
+// Specialized launches (one scheme and dtype): one warp job per warp, as
+// many CTAs as jobs need.  The batched launch (SCHEME < 0) is persistent: its
+// CTAs pop one job per warp from a work queue that the last CTA resets, so
+// the launch can be replayed from a CUDA graph.
 // At least 32 resident warps per SM: registers are capped at 64 per thread.
 template <int SCHEME, int DT, int THREADS>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS) tiles_kernel(LaunchArgs a) {
     extern __shared__ uint4 smem4[];
-    __shared__ uint32_t s_tile;
     constexpr uint32_t NW = THREADS / 32;
     const uint32_t warp = threadIdx.x >> 5;
     uint32_t* wsm = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(smem4) + warp * a.warp_smem);
-    uint32_t it = 0;
-    for (;;) {
-        uint32_t tile;
-        if constexpr (SCHEME < 0) {
+    if constexpr (SCHEME >= 0) {
+        const uint32_t job = blockIdx.x * NW + warp;
+        if (job < a.njobs) run_job<SCHEME, DT>(a, job, wsm);
+    } else {
+        __shared__ uint32_t s_job;
+        for (;;) {
             __syncthreads();
-            if (threadIdx.x == 0) s_tile = atomicAdd(&a.queue[0], 1u);
+            if (threadIdx.x == 0) s_job = atomicAdd(&a.queue[0], NW);
             __syncthreads();
-            tile = s_tile;
-        } else {
-            tile = blockIdx.x + it * gridDim.x;
-            it++;
+            const uint32_t base = s_job;
+            if (base >= a.njobs) break;
+            if (base + warp < a.njobs) run_job<SCHEME, DT>(a, base + warp, wsm);
         }
-        if (tile >= a.ntiles) break;
-        const uint32_t k = find_chunk(a.chunks, a.nchunks, tile);
-        const ZfDevChunk c = a.chunks[k];
-        zfd::Hdr h;
-        zfd::load_hdr(c.blob, h);
-        const uint32_t rc = (tile - c.tile0) * a.tile_rows;
-        const uint32_t sz = c.dtype == ZF_I64 ? 8 : c.dtype == ZF_I32 ? 4 : 1;
-        if (h.rows != c.rows || rc >= c.rows || (uint64_t)c.rows * sz > c.dst_cap) {
-            if (threadIdx.x == 0) zfd::report(a.err, ZF_ECORRUPT, c.chunk_id);
-            continue;
-        }
-        for (uint32_t sub = warp; sub * zfd::kWarpRows < a.tile_rows; sub += NW) {
-            const uint32_t r0 = rc + sub * zfd::kWarpRows;
-            if (r0 >= c.rows) break;
-            const uint32_t nr = min(zfd::kWarpRows, c.rows - r0);
-            if constexpr (SCHEME < 0) decode_mixed(c, h, r0, nr, wsm, a.err);
-            else decode_one<SCHEME, DT>(c, h, r0, nr, wsm, a.err);
-        }
-    }
-    if constexpr (SCHEME < 0) {
         if (threadIdx.x == 0) {
             __threadfence();
             if (atomicAdd(&a.queue[1], 1u) == gridDim.x - 1) {
@@ -282,11 +283,14 @@ cudaError_t launch_tiles(const TileLaunch& L, cudaStream_t s) {
         if (per_sm <= 0 || per_sm > it->second) per_sm = it->second;
     }
     if (per_sm <= 0) return cudaErrorInvalidConfiguration;
-    uint64_t grid = (uint64_t)per_sm * (uint64_t)L.num_sms;
-    if (grid > L.ntiles) grid = L.ntiles;
+    const uint32_t nw = L.threads / 32;
+    uint64_t grid = ((uint64_t)L.ntiles + nw - 1) / nw;               // one job per warp
+    if (L.scheme < 0) {                                                // persistent work-queue launch
+        uint64_t resident = (uint64_t)per_sm * (uint64_t)L.num_sms;
+        if (grid > resident) grid = resident;
+    }
     if (grid == 0) return cudaSuccess;
-    LaunchArgs a{L.chunks, L.nchunks, L.ntiles, L.tile_rows, L.smem / (L.threads / 32), L.err,
-                 L.scheme < 0 ? L.queue : nullptr};
+    LaunchArgs a{L.chunks, L.nchunks, L.ntiles, L.tile_rows, L.smem / nw, L.err, L.scheme < 0 ? L.queue : nullptr};
     fn<<<(unsigned)grid, L.threads, L.smem, s>>>(a);
     return cudaGetLastError();
 }

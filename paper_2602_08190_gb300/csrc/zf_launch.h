@@ -9,9 +9,9 @@ namespace zf {
 struct TileLaunch {
     const ZfDevChunk* chunks;   // device descriptors of this launch
     uint32_t nchunks;
-    uint32_t ntiles;
+    uint32_t ntiles;            // warp jobs
     int scheme, dtype;          // -1, -1 for the batched work-queue kernel
-    uint32_t tile_rows;
+    uint32_t tile_rows;         // rows per warp job
     uint32_t threads;
     uint32_t ctas_per_sm;       // 0 = occupancy limit
     uint32_t smem;              // dynamic shared memory: threads/32 slices of equal size

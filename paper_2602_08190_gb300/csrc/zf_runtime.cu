@@ -53,6 +53,18 @@ struct zf_ctx {
     size_t desc_cap = 0;
     std::vector<ZfDevChunk> resident_cache;   // descriptors last uploaded for resident decode
     zf_kcfg kcfg{0, 256, 0, 8u << 20, 0};
+    uint64_t slots_gen = 0;        // bumped whenever the staging slots are reallocated
+    // CUDA graph of the last transfer (ZF_KCFG_GRAPH) and what it was built for
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<uint64_t> graph_key;
+    ZfDevChunk* g_d_desc = nullptr;
+    ZfDevChunk* g_h_desc = nullptr;   // pinned, read by the graph's descriptor copy
+    size_t g_desc_cap = 0;
+    zf_stats graph_stats{};
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    zf_mlp* selector = nullptr;       // learned selector (not owned) and its feature scaling
+    float sel_mean[32] = {0}, sel_std[32] = {0};
     bool busy = false;
     zf_status host_err = ZF_OK;
     std::string last_error;
@@ -72,13 +84,12 @@ zf_status cuda_fail(zf_ctx* ctx, cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
     } while (0)
 
-// Zero fields take the built-in geometry; a CTA tile holds at least one
-// 1024-row warp tile per warp.
+// Zero fields take the built-in geometry: 256 threads, warp jobs of four
+// 1024-row tiles.
 zf_kcfg effective_kcfg(const zf_ctx* ctx) {
     zf_kcfg k = ctx->kcfg;
     if (!k.threads) k.threads = 256;
-    const uint32_t min_rows = 1024 * (k.threads / 32);
-    if (k.tile_rows < min_rows) k.tile_rows = min_rows;
+    if (!k.tile_rows) k.tile_rows = 4096;
     if (!k.stage_bytes) k.stage_bytes = 8u << 20;
     return k;
 }
@@ -171,6 +182,7 @@ zf_status ensure_slots(zf_ctx* ctx, uint64_t bytes) {
             return ZF_ENOMEM;
         }
     ctx->slot_cap = bytes;
+    ctx->slots_gen++;
     return ZF_OK;
 }
 
@@ -214,6 +226,7 @@ void build_groups(const std::vector<Work>& w, size_t b, size_t e, const zf_kcfg&
             dc.chunk_id = w[i].id;
             dc.scheme = (uint8_t)s;
             dc.dtype = (uint8_t)d;
+            dc.bmax = w[i].ch->bmax;
             g.ntiles += dc.ntiles;
             g.warp_smem = std::max(g.warp_smem, zf::warp_smem_bytes(s, d, w[i].ch->bmax));
             desc.push_back(dc);
@@ -223,10 +236,9 @@ void build_groups(const std::vector<Work>& w, size_t b, size_t e, const zf_kcfg&
     }
 }
 
-zf_status launch_groups(zf_ctx* ctx, const std::vector<Group>& groups, const std::vector<ZfDevChunk>& desc,
-                        const zf_kcfg& k) {
+zf_status launch_groups(zf_ctx* ctx, const std::vector<Group>& groups, const ZfDevChunk* d_desc, const zf_kcfg& k) {
     for (const Group& g : groups) {
-        const ZfDevChunk* dchunks = ctx->d_desc + g.first;
+        const ZfDevChunk* dchunks = d_desc + g.first;
         cudaError_t e;
         if (g.scheme == ZF_LZ77) {
             e = zf::launch_lz(dchunks, g.count, ctx->d_err, ctx->num_sms, ctx->compute);
@@ -291,7 +303,9 @@ zf_status zf_ctx_create(int device, void* copy_stream, void* compute_stream, zf_
         if (cudaEventCreateWithFlags(&ctx->ev_copied[s], cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&ctx->ev_free[s], cudaEventDisableTiming) != cudaSuccess)
             return fail(ZF_ECUDA);
-    if (cudaEventCreate(&ctx->ev_t0) != cudaSuccess || cudaEventCreate(&ctx->ev_t1) != cudaSuccess)
+    if (cudaEventCreate(&ctx->ev_t0) != cudaSuccess || cudaEventCreate(&ctx->ev_t1) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess)
         return fail(ZF_ECUDA);
     if (cudaMalloc(&ctx->d_err, 64) != cudaSuccess || cudaMemset(ctx->d_err, 0, 64) != cudaSuccess)
         return fail(ZF_ENOMEM);
@@ -315,6 +329,12 @@ zf_status zf_ctx_destroy(zf_ctx* ctx) {
     }
     if (ctx->ev_t0) cudaEventDestroy(ctx->ev_t0);
     if (ctx->ev_t1) cudaEventDestroy(ctx->ev_t1);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    if (ctx->g_d_desc) cudaFree(ctx->g_d_desc);
+    if (ctx->g_h_desc) cudaFreeHost(ctx->g_h_desc);
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->h_err) cudaFreeHost(ctx->h_err);
     if (ctx->d_desc) cudaFree(ctx->d_desc);
@@ -331,7 +351,7 @@ zf_status zf_ctx_set_kcfg(zf_ctx* ctx, const zf_kcfg* k) {
     if (!ctx || !k) return ZF_EINVAL;
     zf_kcfg n = *k;
     if (!n.threads) n.threads = 256;
-    if (!n.tile_rows) n.tile_rows = 1024 * (n.threads / 32);
+    if (!n.tile_rows) n.tile_rows = 4096;
     if (!n.stage_bytes) n.stage_bytes = 8u << 20;
     if (!kcfg_valid(n)) {
         ctx->last_error = "invalid kernel geometry";
@@ -424,6 +444,33 @@ zf_status zf_transfer_decompress(zf_ctx* ctx, const zf_compressed* const* cols, 
     zf_status st = begin_call(ctx);
     if (st) return st;
     const zf_kcfg k = effective_kcfg(ctx);
+    const bool use_graph = (k.flags & ZF_KCFG_GRAPH) != 0;
+    std::vector<uint64_t> key;
+    uint32_t nout = 0;
+    if (use_graph) {
+        // everything the captured work depends on
+        for (uint32_t c = 0; c < ncols; c++) {
+            if (!cols[c]) return ZF_EINVAL;
+            key.push_back((uint64_t)(uintptr_t)cols[c]);
+            key.push_back((uint64_t)(uintptr_t)cols[c]->host);
+            key.push_back(cols[c]->len);
+            nout += (uint32_t)cols[c]->nparts;
+        }
+        for (uint32_t o = 0; o < nout; o++) {
+            key.push_back((uint64_t)(uintptr_t)d_out[o]);
+            key.push_back(d_out_bytes[o]);
+        }
+        key.insert(key.end(), {k.tile_rows, k.threads, k.ctas_per_sm, k.stage_bytes, k.flags, ctx->nslots,
+                               ctx->slot_req, ctx->slots_gen});
+        if (ctx->graph_exec && key == ctx->graph_key) {
+            ZF_CU(ctx, cudaEventRecord(ctx->ev_t0, ctx->copy));
+            ZF_CU(ctx, cudaGraphLaunch(ctx->graph_exec, ctx->copy));
+            ZF_CU(ctx, cudaEventRecord(ctx->ev_t1, ctx->copy));
+            ctx->st = ctx->graph_stats;
+            ctx->busy = true;
+            return ZF_OK;
+        }
+    }
     std::vector<Work> work;
     uint64_t raw = 0, comp = 0;
     st = map_outputs<zf_compressed>(ctx, cols, ncols, d_out, d_out_bytes, work, &raw, &comp, host_of, nodev_of);
@@ -441,6 +488,7 @@ zf_status zf_transfer_decompress(zf_ctx* ctx, const zf_compressed* const* cols, 
     }
     st = ensure_slots(ctx, std::max<uint64_t>(std::max(max_stage, ctx->slot_req), 16));
     if (st) return st;
+    if (use_graph) key.back() = ctx->slots_gen;
     // Copy plan: runs of chunks contiguous in one host buffer become one copy;
     // each chunk's blob lands at its offset inside the stage's slot.
     struct Piece { const uint8_t* src; uint64_t bytes; uint64_t slot_off; };
@@ -462,40 +510,119 @@ zf_status zf_transfer_decompress(zf_ctx* ctx, const zf_compressed* const* cols, 
     std::vector<ZfDevChunk> desc;
     std::vector<std::vector<Group>> groups(stages.size());
     for (size_t s = 0; s < stages.size(); s++) build_groups(work, stages[s].first, stages[s].second, k, desc, groups[s]);
-    st = ensure_desc(ctx, std::max<size_t>(desc.size(), 1));
-    if (st) return st;
-    ctx->resident_cache.clear();
-    if (!desc.empty()) memcpy(ctx->h_desc, desc.data(), desc.size() * sizeof(ZfDevChunk));
-    ZF_CU(ctx, cudaEventRecord(ctx->ev_t0, ctx->copy));
-    ZF_CU(ctx, cudaMemsetAsync(ctx->d_err, 0, 4, ctx->copy));
-    ZF_CU(ctx, cudaMemsetAsync(ctx->d_err + 1, 0xFF, 4, ctx->copy));
+    const size_t nd = std::max<size_t>(desc.size(), 1);
+    ZfDevChunk* d_desc;
+    ZfDevChunk* h_desc;
+    if (use_graph) {
+        // the graph keeps its own descriptor buffers: other calls reuse the context's
+        if (nd > ctx->g_desc_cap) {
+            if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+            if (ctx->graph) cudaGraphDestroy(ctx->graph);
+            ctx->graph_exec = nullptr;
+            ctx->graph = nullptr;
+            ctx->graph_key.clear();
+            if (ctx->g_d_desc) cudaFree(ctx->g_d_desc);
+            if (ctx->g_h_desc) cudaFreeHost(ctx->g_h_desc);
+            ctx->g_d_desc = nullptr;
+            ctx->g_h_desc = nullptr;
+            ctx->g_desc_cap = 0;
+            if (cudaMalloc(&ctx->g_d_desc, nd * sizeof(ZfDevChunk)) != cudaSuccess ||
+                cudaHostAlloc(&ctx->g_h_desc, nd * sizeof(ZfDevChunk), cudaHostAllocDefault) != cudaSuccess) {
+                cudaGetLastError();
+                ctx->last_error = "graph descriptor buffers";
+                return ZF_ENOMEM;
+            }
+            ctx->g_desc_cap = nd;
+        }
+        d_desc = ctx->g_d_desc;
+        h_desc = ctx->g_h_desc;
+    } else {
+        st = ensure_desc(ctx, nd);
+        if (st) return st;
+        ctx->resident_cache.clear();
+        d_desc = ctx->d_desc;
+        h_desc = ctx->h_desc;
+    }
+    if (!desc.empty()) memcpy(h_desc, desc.data(), desc.size() * sizeof(ZfDevChunk));
+    if (use_graph) {
+        // capture the whole call (both streams) into a graph, then launch it
+        if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+        if (ctx->graph) cudaGraphDestroy(ctx->graph);
+        ctx->graph_exec = nullptr;
+        ctx->graph = nullptr;
+        ctx->graph_key.clear();
+        ZF_CU(ctx, cudaStreamBeginCapture(ctx->copy, cudaStreamCaptureModeRelaxed));
+        ZF_CU(ctx, cudaEventRecord(ctx->ev_fork, ctx->copy));
+        ZF_CU(ctx, cudaStreamWaitEvent(ctx->compute, ctx->ev_fork, 0));
+    } else {
+        ZF_CU(ctx, cudaEventRecord(ctx->ev_t0, ctx->copy));
+    }
+    auto abort_capture = [&](zf_status s2) {
+        if (use_graph) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(ctx->copy, &g);
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+        }
+        cudaStreamSynchronize(ctx->copy);
+        cudaStreamSynchronize(ctx->compute);
+        return s2;
+    };
+#define ZF_CAP(call)                                                          \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) return abort_capture(cuda_fail(ctx, e_, #call)); \
+    } while (0)
+    ZF_CAP(cudaMemsetAsync(ctx->d_err, 0, 4, ctx->copy));
+    ZF_CAP(cudaMemsetAsync(ctx->d_err + 1, 0xFF, 4, ctx->copy));
     if (!desc.empty())
-        ZF_CU(ctx, cudaMemcpyAsync(ctx->d_desc, ctx->h_desc, desc.size() * sizeof(ZfDevChunk),
-                                   cudaMemcpyHostToDevice, ctx->copy));
-    if (stages.empty()) ZF_CU(ctx, cudaEventRecord(ctx->ev_copied[0], ctx->copy));
-    if (stages.empty()) ZF_CU(ctx, cudaStreamWaitEvent(ctx->compute, ctx->ev_copied[0], 0));
+        ZF_CAP(cudaMemcpyAsync(d_desc, h_desc, desc.size() * sizeof(ZfDevChunk), cudaMemcpyHostToDevice, ctx->copy));
+    if (stages.empty()) ZF_CAP(cudaEventRecord(ctx->ev_copied[0], ctx->copy));
+    if (stages.empty()) ZF_CAP(cudaStreamWaitEvent(ctx->compute, ctx->ev_copied[0], 0));
     for (size_t s = 0; s < stages.size(); s++) {
         uint32_t slot = (uint32_t)(s % ctx->nslots);
-        if (s >= ctx->nslots) ZF_CU(ctx, cudaStreamWaitEvent(ctx->copy, ctx->ev_free[slot], 0));
+        if (s >= ctx->nslots) ZF_CAP(cudaStreamWaitEvent(ctx->copy, ctx->ev_free[slot], 0));
         for (const Piece& p : pieces[s])
-            ZF_CU(ctx, cudaMemcpyAsync(ctx->slots[slot] + p.slot_off, p.src, p.bytes, cudaMemcpyHostToDevice,
-                                       ctx->copy));
-        ZF_CU(ctx, cudaEventRecord(ctx->ev_copied[slot], ctx->copy));
-        ZF_CU(ctx, cudaStreamWaitEvent(ctx->compute, ctx->ev_copied[slot], 0));
-        st = launch_groups(ctx, groups[s], desc, k);
-        if (st) {
-            // nothing may still read the descriptor or staging buffers after an error return
-            cudaStreamSynchronize(ctx->copy);
-            cudaStreamSynchronize(ctx->compute);
-            return st;
-        }
-        ZF_CU(ctx, cudaEventRecord(ctx->ev_free[slot], ctx->compute));
+            ZF_CAP(cudaMemcpyAsync(ctx->slots[slot] + p.slot_off, p.src, p.bytes, cudaMemcpyHostToDevice, ctx->copy));
+        ZF_CAP(cudaEventRecord(ctx->ev_copied[slot], ctx->copy));
+        ZF_CAP(cudaStreamWaitEvent(ctx->compute, ctx->ev_copied[slot], 0));
+        st = launch_groups(ctx, groups[s], d_desc, k);
+        if (st) return abort_capture(st);
+        ZF_CAP(cudaEventRecord(ctx->ev_free[slot], ctx->compute));
     }
+    ZF_CAP(cudaMemcpyAsync(ctx->h_err, ctx->d_err, 8, cudaMemcpyDeviceToHost, ctx->compute));
+#undef ZF_CAP
     ctx->st.raw_bytes = raw;
     ctx->st.comp_bytes = comp;
     ctx->st.n_chunks = (uint32_t)work.size();
     ctx->st.n_stages = (uint32_t)stages.size();
-    return finish_enqueue(ctx);
+    if (!use_graph) {
+        ZF_CU(ctx, cudaEventRecord(ctx->ev_t1, ctx->compute));
+        ctx->busy = true;
+        return ZF_OK;
+    }
+    cudaError_t e = cudaEventRecord(ctx->ev_join, ctx->compute);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy, ctx->ev_join, 0);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(ctx->copy, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(ctx, e != cudaSuccess ? e : e2, "graph capture");
+    }
+    e = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        ctx->graph_exec = nullptr;
+        return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    }
+    ctx->graph = g;
+    ctx->graph_key = key;
+    ctx->graph_stats = ctx->st;
+    ZF_CU(ctx, cudaEventRecord(ctx->ev_t0, ctx->copy));
+    ZF_CU(ctx, cudaGraphLaunch(ctx->graph_exec, ctx->copy));
+    ZF_CU(ctx, cudaEventRecord(ctx->ev_t1, ctx->copy));
+    ctx->busy = true;
+    return ZF_OK;
 }
 
 zf_status zf_sync(zf_ctx* ctx, zf_stats* stats) {
@@ -589,7 +716,7 @@ zf_status zf_decompress_resident(zf_ctx* ctx, const zf_resident* const* cols, ui
         }
         ctx->resident_cache = desc;
     }
-    st = launch_groups(ctx, groups, desc, k);
+    st = launch_groups(ctx, groups, ctx->d_desc, k);
     if (st) {
         cudaStreamSynchronize(ctx->compute);
         return st;
@@ -605,6 +732,97 @@ zf_status zf_decompress_resident(zf_ctx* ctx, const zf_resident* const* cols, ui
 
 namespace zf {
 int heuristic_scheme(const zf_column& col, uint32_t chunk_rows);
+}
+
+namespace {
+// Selector classes: label = scheme * 2 + size; size 0 = 4 MiB, 1 = 32 MiB of
+// uncompressed bytes per chunk (string columns keep 64 KiB LZ77 blocks).
+uint32_t class_chunk_rows(const zf_column& col, int label) {
+    if (col.dtype == ZF_BYTES) return zf::kLzBlock;
+    const uint64_t bytes = (label & 1) ? (32ull << 20) : (4ull << 20);
+    const uint64_t rows = bytes / zf::dtype_size(col.dtype) / 1024 * 1024;
+    return (uint32_t)std::max<uint64_t>(rows, 1024);
+}
+
+void class_mask(const zf_column& col, uint8_t* mask) {
+    for (int k = 0; k < ZF_MLP_CLASSES; k++) {
+        const int scheme = k / 2;
+        mask[k] = col.dtype == ZF_BYTES ? (scheme == ZF_RAW || scheme == ZF_LZ77) : (scheme != ZF_LZ77);
+    }
+}
+}  // namespace
+
+// Median end-to-end time (transfer + decode, zf_sync's total_ms) of every
+// selector class on this column; classes that do not apply get -1.
+extern "C" zf_status zf_measure_classes(zf_ctx* ctx, const zf_column* col, uint32_t reps, float* ms) {
+    if (!ctx || !col || !ms) return ZF_EINVAL;
+    if (ctx->busy) return ZF_EBUSY;
+    if (!reps) reps = 3;
+    uint8_t mask[ZF_MLP_CLASSES];
+    class_mask(*col, mask);
+    uint64_t outs[2] = {0, 0};
+    void* dbuf[2] = {nullptr, nullptr};
+    if (col->dtype == ZF_BYTES) {
+        outs[0] = std::max<uint64_t>((uint64_t)(uint32_t)col->offsets[col->n], 16);
+        outs[1] = 4 * (col->n + 1);
+    } else {
+        outs[0] = std::max<uint64_t>(col->n * zf::dtype_size(col->dtype), 16);
+    }
+    cudaSetDevice(ctx->device);
+    for (int o = 0; o < 2; o++)
+        if (outs[o] && cudaMalloc(&dbuf[o], outs[o]) != cudaSuccess) {
+            cudaGetLastError();
+            for (void* q : dbuf)
+                if (q) cudaFree(q);
+            return ZF_ENOMEM;
+        }
+    zf_status result = ZF_OK;
+    for (int k = 0; k < ZF_MLP_CLASSES && !result; k++) {
+        ms[k] = -1.0f;
+        if (!mask[k]) continue;
+        zf_plan_t p{};
+        p.scheme = k / 2;
+        p.chunk_rows = class_chunk_rows(*col, k);
+        p.offsets_scheme = ZF_DELTA_BP;
+        p.label = k;
+        zf_compressed* c = nullptr;
+        std::string why;
+        zf_status st = zf::encode_column(p, *col, &c, &why);
+        if (st == ZF_EINVAL) continue;          // the scheme does not fit (dictionary too large)
+        if (st) {
+            result = st;
+            break;
+        }
+        std::vector<float> t;
+        for (uint32_t r = 0; r < reps + 1 && !result; r++) {
+            const zf_compressed* cc = c;
+            st = zf_transfer_decompress(ctx, &cc, 1, dbuf, outs);
+            if (!st) {
+                zf_stats sts;
+                st = zf_sync(ctx, &sts);
+                if (r) t.push_back(sts.total_ms);
+            }
+            if (st) result = st;
+        }
+        zf::free_compressed(c);
+        if (!result) {
+            std::sort(t.begin(), t.end());
+            ms[k] = t[t.size() / 2];
+        }
+    }
+    for (void* q : dbuf)
+        if (q) cudaFree(q);
+    return result;
+}
+
+extern "C" zf_status zf_ctx_set_selector(zf_ctx* ctx, zf_mlp* net, const float* mean, const float* std_) {
+    if (!ctx || (net && (!mean || !std_))) return ZF_EINVAL;
+    ctx->selector = net;
+    if (net) {
+        memcpy(ctx->sel_mean, mean, sizeof(ctx->sel_mean));
+        memcpy(ctx->sel_std, std_, sizeof(ctx->sel_std));
+    }
+    return ZF_OK;
 }
 
 extern "C" zf_status zf_plan(zf_ctx* ctx, const zf_column* col, const zf_plan_opts* opts, zf_plan_t* out) {
@@ -626,10 +844,107 @@ extern "C" zf_status zf_plan(zf_ctx* ctx, const zf_column* col, const zf_plan_op
         p.scheme = o.scheme;
     } else if (o.selector == 0) {
         p.scheme = zf::heuristic_scheme(*col, p.chunk_rows);
+    } else if (o.selector == 1) {
+        if (!ctx || !ctx->selector) {
+            if (ctx) ctx->last_error = "no learned selector attached (zf_ctx_set_selector)";
+            return ZF_EUNSUPPORTED;
+        }
+        float f[32];
+        zf_status st = zf_column_features(col, f);
+        if (st) return st;
+        for (int i = 0; i < 32; i++) f[i] = (f[i] - ctx->sel_mean[i]) / (ctx->sel_std[i] > 0 ? ctx->sel_std[i] : 1.0f);
+        uint8_t mask[ZF_MLP_CLASSES];
+        class_mask(*col, mask);
+        int32_t label = -1;
+        st = zf_mlp_predict(ctx->selector, f, mask, 1, &label);
+        if (st) return st;
+        if (label < 0) return ZF_EINVAL;
+        p.label = label;
+        p.scheme = label / 2;
+        p.chunk_rows = class_chunk_rows(*col, label);
+    } else if (o.selector == 2) {
+        if (!ctx) return ZF_EINVAL;
+        float ms[ZF_MLP_CLASSES];
+        zf_status st = zf_measure_classes(ctx, col, 3, ms);
+        if (st) return st;
+        int best = -1;
+        for (int k = 0; k < ZF_MLP_CLASSES; k++)
+            if (ms[k] >= 0 && (best < 0 || ms[k] < ms[best])) best = k;
+        if (best < 0) return ZF_EINVAL;
+        p.label = best;
+        p.scheme = best / 2;
+        p.chunk_rows = class_chunk_rows(*col, best);
+        p.predicted_ms = ms[best];
     } else {
-        if (ctx) ctx->last_error = "selector not available";
-        return ZF_EUNSUPPORTED;
+        return ZF_EINVAL;
     }
     *out = p;
     return ZF_OK;
+}
+
+// ---------------------------------------------------------------- exhaustive autotuner
+namespace {
+const uint32_t kTuneTileRows[] = {1024, 2048, 4096, 8192, 16384};
+const uint32_t kTuneThreads[] = {128, 256, 512};
+const uint32_t kTuneStageMiB[] = {4, 8, 16, 32, 64};
+}  // namespace
+
+extern "C" zf_status zf_tune(zf_ctx* ctx, const zf_compressed* const* cols, uint32_t ncols, void* const* d_out,
+                             const uint64_t* d_out_bytes, int32_t transfer, uint32_t reps, zf_tune_point* points,
+                             uint32_t max_points, uint32_t* n_points, zf_kcfg* best) {
+    if (!ctx || !cols || !ncols || !d_out || !d_out_bytes || !n_points) return ZF_EINVAL;
+    if (ctx->busy) return ZF_EBUSY;
+    if (reps == 0) reps = 3;
+    const zf_kcfg saved = ctx->kcfg;
+    std::vector<zf_resident*> res;
+    auto cleanup = [&](zf_status s) {
+        for (zf_resident* r : res) zf_resident_free(r);
+        if (s != ZF_OK) ctx->kcfg = saved;
+        return s;
+    };
+    if (!transfer) {
+        for (uint32_t c = 0; c < ncols; c++) {
+            zf_resident* r = nullptr;
+            zf_status s = zf_upload(ctx, cols[c], &r);
+            if (s) return cleanup(s);
+            res.push_back(r);
+        }
+    }
+    const uint32_t nstage = transfer ? (uint32_t)(sizeof(kTuneStageMiB) / sizeof(kTuneStageMiB[0])) : 1;
+    uint32_t n = 0;
+    float best_ms = 3.0e38f;
+    zf_kcfg best_k = saved;
+    for (uint32_t si = 0; si < nstage; si++)
+        for (uint32_t tr : kTuneTileRows)
+            for (uint32_t th : kTuneThreads) {
+                zf_kcfg k = saved;
+                k.tile_rows = tr;
+                k.threads = th;
+                k.flags = saved.flags & ~ZF_KCFG_GRAPH;
+                k.stage_bytes = transfer ? (kTuneStageMiB[si] << 20) : (saved.stage_bytes ? saved.stage_bytes : 8u << 20);
+                ctx->kcfg = k;
+                std::vector<float> ms;
+                for (uint32_t rep = 0; rep < reps + 1; rep++) {   // first run warms up
+                    zf_status s = transfer ? zf_transfer_decompress(ctx, cols, ncols, d_out, d_out_bytes)
+                                           : zf_decompress_resident(ctx, res.data(), ncols, d_out, d_out_bytes);
+                    if (s) return cleanup(s);
+                    zf_stats stt;
+                    s = zf_sync(ctx, &stt);
+                    if (s) return cleanup(s);
+                    if (rep) ms.push_back(stt.total_ms);
+                }
+                std::sort(ms.begin(), ms.end());
+                const float med = ms[ms.size() / 2];
+                if (points && n < max_points) points[n] = zf_tune_point{k, med};
+                n++;
+                if (med < best_ms) {
+                    best_ms = med;
+                    best_k = k;
+                }
+            }
+    best_k.flags = saved.flags;
+    ctx->kcfg = best_k;
+    *n_points = n;
+    if (best) *best = best_k;
+    return cleanup(ZF_OK);
 }

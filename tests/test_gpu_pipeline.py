@@ -1,0 +1,76 @@
+"""The pipeline's replay and tuning paths: a transfer captured once as a
+CUDA graph and replayed, and the exhaustive geometry search (Section 4,
+Table 3's brute-force search) visiting every point once and keeping the
+fastest."""
+import numpy as np
+import pytest
+
+import zf_workloads as W
+from gpu_helpers import Gpu, compress, out_specs
+
+zf = pytest.importorskip("paper_2602_08190_gb300")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def columns():
+    cols = [(W.sorted_keys(21, 3 << 20), zf.ZF_DELTA_BP, 1 << 18),
+            (W.dates_rle(21, 3 << 20), zf.ZF_RLE, 1 << 18),
+            (W.uniform_int(21, 0, 0, 2_000_000, 0, 4096).astype(np.int32), zf.ZF_FOR_BP, 65536),
+            (W.dict_codes(21, 5, 0, 1_000_000), zf.ZF_DICT_BP, 65536)]
+    hs = [compress(x, s, cr) for x, s, cr in cols]
+    yield cols, hs
+    for h in hs:
+        zf.zf_compressed_free(h)
+
+
+@pytest.mark.parametrize("flags", [zf.ZF_KCFG_GRAPH, zf.ZF_KCFG_GRAPH | zf.ZF_KCFG_BATCHED])
+def test_graph_replay(columns, flags):
+    cols, hs = columns
+    specs = [sp for x, s, cr in cols for sp in out_specs(x)]
+    g = Gpu(stage_bytes=4 << 20, flags=flags)
+    try:
+        bufs = g.alloc(specs)
+        outs, caps = [b.data_ptr() for b in bufs], [b.numel() for b in bufs]
+        for rep in range(3):                      # capture once, then replay
+            for b in bufs:
+                b.fill_(0x5A)
+            zf.zf_transfer_decompress(g.ctx, hs, outs, caps)
+            st, stats = zf.zf_sync(g.ctx)
+            assert stats.n_stages > 2
+            for (x, s, cr), b in zip(cols, bufs):
+                assert np.array_equal(b[: x.nbytes].cpu().numpy().view(x.dtype), x), (rep, s)
+        bufs2 = g.alloc(specs)                    # new outputs: a new capture
+        zf.zf_transfer_decompress(g.ctx, hs, [b.data_ptr() for b in bufs2], [b.numel() for b in bufs2])
+        zf.zf_sync(g.ctx)
+        for (x, s, cr), b in zip(cols, bufs2):
+            assert np.array_equal(b[: x.nbytes].cpu().numpy().view(x.dtype), x)
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("transfer,npts", [(False, 15), (True, 75)])
+def test_tune_visits_every_point_and_keeps_the_fastest(columns, transfer, npts):
+    cols, hs = columns
+    specs = [sp for x, s, cr in cols for sp in out_specs(x)]
+    g = Gpu()
+    try:
+        bufs = g.alloc(specs)
+        outs, caps = [b.data_ptr() for b in bufs], [b.numel() for b in bufs]
+        pts, best = zf.zf_tune(g.ctx, hs, outs, caps, transfer=transfer, reps=2)
+        assert len(pts) == npts
+        seen = {(p.kcfg.tile_rows, p.kcfg.threads, p.kcfg.stage_bytes) for p in pts}
+        assert len(seen) == npts
+        fastest = min(pts, key=lambda p: p.ms)
+        assert (best.tile_rows, best.threads) == (fastest.kcfg.tile_rows, fastest.kcfg.threads)
+        if transfer:
+            assert best.stage_bytes == fastest.kcfg.stage_bytes
+        # the context now decodes with the chosen geometry, bit-exact
+        for b in bufs:
+            b.fill_(0)
+        zf.zf_transfer_decompress(g.ctx, hs, outs, caps)
+        zf.zf_sync(g.ctx)
+        for (x, s, cr), b in zip(cols, bufs):
+            assert np.array_equal(b[: x.nbytes].cpu().numpy().view(x.dtype), x)
+    finally:
+        g.close()

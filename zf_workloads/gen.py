@@ -7,7 +7,8 @@ __all__ = [
     "splitmix64", "hash_u64", "uniform_int", "uniform_unit",
     "geometric_gaps", "sorted_keys", "run_lengths_geometric", "dates_rle",
     "zipf_cdf", "zipf_ranks", "vocabulary", "text_column", "lognormal_cents",
-    "dict_codes", "rle_distribution", "DATE_LO", "DATE_HI",
+    "dict_codes", "rle_distribution", "DATE_LO", "DATE_HI", "parallel_rows", "FACT_COLUMNS", "fact_column",
+    "fact_pieces",
 ]
 
 _M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
@@ -56,8 +57,26 @@ def uniform_unit(seed: int, stream: int, start: int, n: int) -> np.ndarray:
     return ((h >> np.uint64(11)).astype(np.float64) + 0.5) * (1.0 / 9007199254740992.0)
 
 
+_GROUP_LSB = {2: np.uint64(0x5555555555555555), 3: np.uint64(0x1249249249249249)}
+
+
 def _first_success(h: np.ndarray, bits: int) -> np.ndarray:
-    """1-based index of the first all-zero ``bits``-wide group of ``h`` (0 if none)."""
+    """1-based index of the first all-zero ``bits``-wide group of ``h`` (0 if none).
+
+    For 2- and 3-bit groups the zero groups are found with word-wide bit
+    operations and the lowest one located through its isolated bit."""
+    if bits in _GROUP_LSB:
+        x = h
+        for k in range(1, bits):
+            x = x | (h >> np.uint64(k))
+        z = ~x & _GROUP_LSB[bits]
+        if bits == 3:
+            z &= np.uint64((1 << 63) - 1)   # 21 whole groups; bit 63 is not a group start
+        low = z & (~z + np.uint64(1))       # isolate the lowest set bit
+        pos = np.zeros(h.shape, np.int64)
+        nz = low != 0
+        pos[nz] = np.log2(low[nz].astype(np.float64)).astype(np.int64) // bits + 1
+        return pos
     groups = 64 // bits
     out = np.zeros(h.shape, np.int64)
     mask = np.uint64((1 << bits) - 1)
@@ -259,3 +278,64 @@ def rle_distribution(seed: int, kind: str, n: int, a: int = 1, b: int = 1) -> np
     vals[same] ^= 1
     out = np.repeat(vals.astype(np.int32), lens)
     return np.ascontiguousarray(out[:n])
+
+
+def parallel_rows(fn, n: int, piece: int = 1 << 24, workers: int = 0) -> np.ndarray:
+    """``fn(start, count)`` over [0, n) in pieces on a thread pool (numpy
+    releases the GIL), concatenated.  ``fn`` must be a pure function of the
+    row range (the counter-based generators are)."""
+    import concurrent.futures as cf
+    import os
+    if n <= piece:
+        return fn(0, n)
+    starts = list(range(0, n, piece))
+    workers = workers or min(16, os.cpu_count() or 1)
+    with cf.ThreadPoolExecutor(workers) as ex:
+        parts = list(ex.map(lambda s: fn(s, min(piece, n - s)), starts))
+    return np.concatenate(parts)
+
+
+# The 16 columns of the synthetic fact table, 100 bytes per row:
+# (name, numpy dtype, kind)
+FACT_COLUMNS = (
+    [("qty_%d" % i, np.int32, "uniform_1_50") for i in range(2)]
+    + [("price_%d" % i, np.int64, "lognormal_cents") for i in range(7)]
+    + [("key_%d" % i, np.int64, "sorted_keys") for i in range(2)]
+    + [("date_%d" % i, np.int32, "dates") for i in range(3)]
+    + [("code_%d" % i, np.int32, "codes_25") for i in range(2)]
+)
+
+
+def fact_column(seed: int, idx: int, n: int) -> np.ndarray:
+    """Column ``idx`` of the fact table (n rows), each column its own stream."""
+    name, dt, kind = FACT_COLUMNS[idx]
+    s = seed * 1000 + idx
+    if kind == "uniform_1_50":
+        return parallel_rows(lambda a, c: uniform_int(s, 11, a, c, 1, 51).astype(np.int32), n)
+    if kind == "lognormal_cents":
+        return parallel_rows(lambda a, c: lognormal_cents(s, 21, a, c), n)
+    if kind == "sorted_keys":
+        gaps = parallel_rows(lambda a, c: geometric_gaps(s, 101, a, c, 2), n)
+        return np.cumsum(gaps, dtype=np.int64)
+    if kind == "dates":
+        return dates_rle(s, n)
+    if kind == "codes_25":
+        return parallel_rows(lambda a, c: dict_codes(s, 31, a, c), n)
+    raise ValueError(kind)
+
+
+def fact_pieces(seed: int, idx: int, n: int, lo_bytes: int = 4 << 20, hi_bytes: int = 64 << 20) -> list[int]:
+    """Row counts of the uneven pieces a fact column is streamed in: sizes
+    log-uniform over [lo_bytes, hi_bytes] of uncompressed bytes, rounded to a
+    multiple of 1,024 rows (the last piece takes the remainder)."""
+    itemsize = np.dtype(FACT_COLUMNS[idx][1]).itemsize
+    out, total, k = [], 0, 0
+    lo, hi = np.log(lo_bytes), np.log(hi_bytes)
+    while total < n:
+        u = float(uniform_unit(seed * 1000 + idx, 77, k, 1)[0])
+        rows = int(np.exp(lo + (hi - lo) * u) / itemsize) // 1024 * 1024
+        rows = max(1024, min(rows, n - total))
+        out.append(rows)
+        total += rows
+        k += 1
+    return out
