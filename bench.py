@@ -43,6 +43,39 @@ WORKLOAD = ("group_parallel: 64M int64 sorted keys (gaps geometric mean 4; delta
             "blocks) + 64M int32 dates (2,557 days, runs geometric mean 8; RLE), 1M-row chunks")
 
 
+KERNEL_SOURCES = ("paper_2602_08190_gb300/csrc/zf_device.cuh", "paper_2602_08190_gb300/csrc/zf_kernels.cu")
+TRAFFIC_PROFILE = "profiles/delta_i64_decode_32M_rows.md"
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic():
+    """DRAM bytes per 64M-row delta launch from the committed ncu summary,
+    or None if the kernel sources changed since those counters were taken."""
+    path = os.path.join(ROOT, TRAFFIC_PROFILE)
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and line.startswith("- "):
+                k, v = line[2:].split(":", 1)
+                fields[k.strip()] = v.strip().strip("`")
+    if fields.get("kernel source hash") != kernel_source_hash():
+        return None
+    try:
+        return int(fields["dram bytes per 64M-row launch (scaled)"])
+    except (KeyError, ValueError):
+        return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -261,6 +294,182 @@ def run_batched(args, zf, torch):
     zf.zf_ctx_destroy(ctx)
 
 
+TEXT_WORKLOAD = ("non_parallel: 268,435,456-byte string column, Zipf(1.1) words from a 5,000-word vocabulary "
+                 "(3-12 letters), 1-8 words per row; LZ77 in 64 KiB blocks (one warp per block), int32 offsets "
+                 "delta-packed in 65,536-row chunks")
+
+
+def run_text(args, zf, torch):
+    """The Non-Parallel workload: decode of a 256 MB LZ77 string column."""
+    import zf_workloads as W
+    t, o = W.text_column(1, 1 << 28)
+    col = zf.Column(t, o)
+    h = zf.zf_compress_host(zf.zf_plan(None, col, scheme=zf.ZF_LZ77), col)
+    raw, comp, nch = zf.zf_compressed_info(h)
+    copy_s, comp_s = torch.cuda.Stream(), torch.cuda.Stream()
+    ctx = zf.zf_ctx_create(0, copy_s.cuda_stream, comp_s.cuda_stream)
+    zf.zf_ctx_set_kcfg(ctx, args.tile_rows, args.threads, args.ctas_per_sm, int((args.stage_mb or 16) * (1 << 20)), 0)
+    zf.zf_ctx_set_ring(ctx, args.slots or 3)
+    ob = torch.empty(t.nbytes, dtype=torch.uint8, device="cuda")
+    oo = torch.empty(o.nbytes, dtype=torch.uint8, device="cuda")
+    outs, caps = [ob.data_ptr(), oo.data_ptr()], [t.nbytes, o.nbytes]
+    zf.zf_transfer_decompress(ctx, [h], outs, caps)
+    zf.zf_sync(ctx)
+    assert np.array_equal(ob.cpu().numpy(), t) and np.array_equal(oo.cpu().numpy().view(np.int32), o)
+    r = zf.zf_upload(ctx, h)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    dev_ms, e2e_ms, launches = [], [], 0
+    for i in range(args.warmup + args.steps):
+        with torch.cuda.stream(comp_s):
+            flush.fill_(1)
+        zf.zf_decompress_resident(ctx, [r], outs, caps)
+        st, stats = zf.zf_sync(ctx)
+        if i >= args.warmup:
+            dev_ms.append(stats.total_ms)
+            launches += stats.n_launches
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        zf.zf_transfer_decompress(ctx, [h], outs, caps)
+        st, stats = zf.zf_sync(ctx)
+        if i >= args.warmup:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+            launches += stats.n_launches
+    td, te = float(np.mean(dev_ms)), float(np.mean(e2e_ms))
+    line = {"metric": METRIC, "value": round(raw / (td * 1e-3) / 1e9, 2), "unit": "GB/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(td, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8/int32", "data": "synthetic",
+            "config": {"workload": TEXT_WORKLOAD, "raw_bytes_per_step": raw, "comp_bytes_per_step": comp,
+                       "compression_ratio": round(raw / comp, 3), "blocks": nch,
+                       "l2": "flushed (256 MiB write) before every resident step"},
+            "e2e": {"value": round(raw / (te * 1e-3) / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": comp,
+                    "d2h_bytes_per_step": 8, "ms_per_step": round(te, 4)},
+            "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+    zf.zf_resident_free(r)
+    zf.zf_compressed_free(h)
+    zf.zf_ctx_destroy(ctx)
+
+
+SELECTOR_METRIC = "learned selector: mean regret vs exhaustive class search on held-out columns"
+
+
+def selector_dataset(zf, ctx, seeds, cap_rows: int, reps: int = 2):
+    """Features and measured per-class transfer+decode times of the columns
+    with the given seeds."""
+    import zf_workloads as W
+    F, T, fam, dts = [], [], [], []
+    for s in seeds:
+        x, o, meta = W.selector_column(s, cap_rows)
+        col = zf.Column(x, o)
+        F.append(zf.zf_column_features(col))
+        T.append(zf.zf_measure_classes(ctx, col, reps))
+        fam.append(meta["family"])
+        dts.append(meta.get("dtype", "bytes"))
+    return np.array(F, np.float32), np.array(T, np.float32), fam, dts
+
+
+def selector_eval(zf, ctx, F, T, n_train, epochs=400, batch=256, lr=1e-3, seed=1):
+    """Train the MLP on the first n_train columns (on the GPU), evaluate the
+    rest; returns a dict of regrets and the trained network."""
+    mask = T >= 0
+    y = np.where(mask, T, np.inf).argmin(1).astype(np.int32)
+    Ftr, Fte = F[:n_train], F[n_train:]
+    mean = Ftr.mean(0)
+    std = Ftr.std(0)
+    std[std == 0] = 1.0
+    net = zf.zf_mlp_create(0, seed)
+    t0 = time.perf_counter()
+    losses = zf.zf_mlp_train(net, (Ftr - mean) / std, y[:n_train], mask[:n_train], epochs, batch, lr, seed=seed)
+    train_s = time.perf_counter() - t0
+    pred = zf.zf_mlp_predict(net, (Fte - mean) / std, mask[n_train:])
+    Tte, yte = T[n_train:], y[n_train:]
+    best = Tte[np.arange(len(yte)), yte]
+
+    def regret(choice):
+        return float(np.mean((Tte[np.arange(len(yte)), choice] - best) / best))
+
+    # the method without the network: one static class (per value type),
+    # the best one on the training columns
+    def static_choice(Ttr, Tev):
+        mtr = Ttr >= 0
+        btr = np.where(mtr, Ttr, np.inf).min(1)
+        best_k, best_r = -1, np.inf
+        for k in range(Ttr.shape[1]):
+            if not mtr[:, k].all():
+                continue
+            r = np.mean((Ttr[:, k] - btr) / btr)
+            if r < best_r:
+                best_k, best_r = k, r
+        return best_k
+    is_bytes = F[:, 2] > 0.5
+    static = np.zeros(len(yte), np.int32)
+    for grp in (False, True):
+        tr = is_bytes[:n_train] == grp
+        te = is_bytes[n_train:] == grp
+        if te.any():
+            static[te] = static_choice(T[:n_train][tr], Tte[te])
+    return {"regret": regret(pred), "accuracy": float((pred == yte).mean()), "static_regret": regret(static),
+            "static_classes": sorted(set(static.tolist())), "loss_first": float(losses[0]),
+            "loss_last": float(losses[-1]), "train_s": round(train_s, 3), "mean": mean, "std": std,
+            "pred": pred, "labels": yte}, net
+
+
+def run_selector(args, zf, torch):
+    import zf_workloads as W
+    n_train, n_test = args.sel_train, args.sel_test
+    ctx = zf.zf_ctx_create(0)
+    zf.zf_ctx_set_kcfg(ctx, 0, 0, 0, 16 << 20, 0)
+    zf.zf_ctx_set_ring(ctx, 3)
+    t0 = time.perf_counter()
+    F, T, fam, dts = selector_dataset(zf, ctx, range(1, n_train + n_test + 1), args.sel_cap)
+    collect_s = time.perf_counter() - t0
+    res, net = selector_eval(zf, ctx, F, T, n_train)
+    # the rule-based heuristic (zf_plan selector 0) on the held-out columns
+    heur = []
+    for i, s in enumerate(range(n_train + 1, n_train + n_test + 1)):
+        x, o, meta = W.selector_column(s, args.sel_cap)
+        col = zf.Column(x, o)
+        p = zf.zf_plan(None, col, selector=0)
+        k = p.scheme * 2 if o is None else (zf.ZF_LZ77 * 2)
+        tt = T[n_train + i]
+        b = tt[tt >= 0].min()
+        heur.append((tt[k] - b) / b if tt[k] >= 0 else np.nan)
+    # the trained network inside zf_plan, and its inference time
+    zf.zf_ctx_set_selector(ctx, net, res["mean"], res["std"])
+    x, o, meta = W.selector_column(n_train + 1, args.sel_cap)
+    col = zf.Column(x, o)
+    zf.zf_plan(ctx, col, selector=1)
+    t1 = time.perf_counter()
+    for _ in range(20):
+        zf.zf_plan(ctx, col, selector=1)
+    plan_us = (time.perf_counter() - t1) / 20 * 1e6
+    Fn = ((F[n_train:] - res["mean"]) / res["std"]).astype(np.float32)
+    m = (T[n_train:] >= 0).astype(np.uint8)
+    zf.zf_mlp_predict(net, Fn, m)
+    t1 = time.perf_counter()
+    for _ in range(20):
+        zf.zf_mlp_predict(net, Fn, m)
+    infer_us = (time.perf_counter() - t1) / 20 * 1e6
+    line = {"metric": SELECTOR_METRIC, "value": round(res["regret"], 4), "unit": "fraction", "n_gpus": 1,
+            "steps": 1, "warmup": 1, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"selector: {n_train} train + {n_test} held-out seeded columns "
+                                   f"(uniform/zipf/sorted/runs/text; int32/int64/bytes), rows log-uniform 1M-64M "
+                                   f"capped at {args.sel_cap} for label collection, 12 classes = 6 schemes x "
+                                   f"{{4, 32}} MiB chunks, labels = fastest measured transfer+decode",
+                       "collect_s": round(collect_s, 1)},
+            "selector": {"regret": round(res["regret"], 4), "accuracy": round(res["accuracy"], 4),
+                         "static_class_regret": round(res["static_regret"], 4),
+                         "static_classes": res["static_classes"],
+                         "heuristic_regret": round(float(np.nanmean(heur)), 4),
+                         "loss_first_epoch": round(res["loss_first"], 4), "loss_last_epoch": round(res["loss_last"], 4),
+                         "gpu_train_s": res["train_s"], "plan_us_with_features": round(plan_us, 1),
+                         "predict_us_batch": round(infer_us, 1), "predict_batch": n_test,
+                         "label_counts": np.bincount(np.where(T >= 0, T, np.inf).argmin(1), minlength=12).tolist()}}
+    print(json.dumps(line), flush=True)
+    zf.zf_mlp_destroy(net)
+    zf.zf_ctx_destroy(ctx)
+
+
 def run_profile(args, zf, torch):
     """Resident decode of one workload column, nothing else (ncu target)."""
     keys, dates = make_workload(1, args.rows)
@@ -310,11 +519,16 @@ def main():
     ap.add_argument("--stage-mb", type=float, default=0)
     ap.add_argument("--slots", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--no-graph", action="store_true", help="enqueue transfers call by call (no CUDA graph)")
     ap.add_argument("--profile", choices=["keys", "dates", "both"], default=None,
                     help="only decode the resident column(s) --steps times (for ncu captures)")
     ap.add_argument("--rows", type=int, default=N_ROWS, help="rows per column (profile / batched runs)")
-    ap.add_argument("--workload", choices=["group_parallel", "batched"], default="group_parallel",
-                    help="group_parallel: the benchmark line; batched: the 40 GB fact table")
+    ap.add_argument("--workload", choices=["group_parallel", "batched", "selector", "text"], default="group_parallel",
+                    help="group_parallel: the benchmark line; batched: the 40 GB fact table; "
+                         "selector: train and evaluate the learned selector")
+    ap.add_argument("--sel-train", type=int, default=2000)
+    ap.add_argument("--sel-test", type=int, default=200)
+    ap.add_argument("--sel-cap", type=int, default=2_000_000, help="row cap for label collection")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.profile, "at least 3 warm-up steps"
 
@@ -340,12 +554,19 @@ def main():
     if args.workload == "batched":
         assert world == 1
         return run_batched(args, zf, torch)
+    if args.workload == "selector":
+        assert world == 1
+        return run_selector(args, zf, torch)
+    if args.workload == "text":
+        assert world == 1
+        return run_text(args, zf, torch)
     keys, dates = make_workload(1 + rank)
     ck, cd = zf.Column(keys), zf.Column(dates)
     copy_s, comp_s = torch.cuda.Stream(), torch.cuda.Stream()
     ctx = zf.zf_ctx_create(local, copy_s.cuda_stream, comp_s.cuda_stream)
-    if any((args.tile_rows, args.threads, args.stage_mb, args.ctas_per_sm)):
-        zf.zf_ctx_set_kcfg(ctx, args.tile_rows, args.threads, args.ctas_per_sm, int(args.stage_mb * (1 << 20)), 0)
+    # transfers replay a captured CUDA graph (the same host buffers every step)
+    zf.zf_ctx_set_kcfg(ctx, args.tile_rows, args.threads, args.ctas_per_sm, int(args.stage_mb * (1 << 20)),
+                       0 if args.no_graph else zf.ZF_KCFG_GRAPH)
     if args.slots:
         zf.zf_ctx_set_ring(ctx, args.slots)
     hk = zf.zf_compress_host(zf.zf_plan(ctx, ck, scheme=zf.ZF_DELTA_BP, chunk_rows=CHUNK_ROWS), ck)
@@ -446,11 +667,7 @@ def main():
         import oracle
         oracle.build()
         cpu_b, cpu_s, cpu_desc = oracle_sample([hk, hd], [np.int64, np.int32], args.cpu_budget_s)
-        traffic = None
-        prof = os.path.join(ROOT, "profiles", "traffic.json")
-        if os.path.exists(prof):
-            with open(prof) as f:
-                traffic = json.load(f).get("delta_i64_decode_bytes_per_launch")
+        traffic = measured_traffic()
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(t_dev, 4), "higher_is_better": True, "scaling": "weak",

@@ -53,7 +53,8 @@
  *     LZ77     rows = raw bytes of one block; flags bit0 = stored raw (s0);
  *              otherwise s0 = tokens, s1 = literals; a token is a LEB128
  *              literal length and, unless it is the last of the block, a u16
- *              offset (1..65535) and a LEB128 (match length - 4)
+ *              offset (1..65535) and a LEB128 (match length - 4); a LEB128
+ *              field takes at most 3 bytes
  *   Bit-packing: value i occupies stream bits [i*b, i*b+b), least
  *   significant bit first; stream bit k is bit k%8 of byte k/8.
  */
@@ -108,7 +109,7 @@ typedef struct {
     uint32_t tile_rows;       /* rows per warp job: a multiple of 1024, <= 16384 (default 4096) */
     uint32_t threads;         /* 128, 256 or 512 (default 256) */
     uint32_t ctas_per_sm;     /* batched launch: persistent grid = ctas_per_sm x SM count (0 = occupancy limit) */
-    uint32_t stage_bytes;     /* pipeline stage: compressed bytes per H2D copy + decode step (default 8 MiB) */
+    uint32_t stage_bytes;     /* pipeline stage: compressed bytes per H2D copy + decode step (default 16 MiB) */
     uint32_t flags;           /* ZF_KCFG_BATCHED: one work-queue launch per stage for all schemes
                                  (else one launch per (scheme, dtype) group);
                                  ZF_KCFG_GRAPH: capture repeated transfers in a CUDA graph */
@@ -157,7 +158,7 @@ zf_status zf_ctx_destroy(zf_ctx* ctx);
 const char* zf_last_error(const zf_ctx* ctx);
 /* Override the kernel geometry used when a plan does not carry one. */
 zf_status zf_ctx_set_kcfg(zf_ctx* ctx, const zf_kcfg* kcfg);
-/* Number of staging slots (2..8, default 2) and bytes per slot (0 = sized per call). */
+/* Number of staging slots (2..8, default 3) and bytes per slot (0 = sized per call). */
 zf_status zf_ctx_set_ring(zf_ctx* ctx, uint32_t slots, uint64_t slot_bytes);
 
 /* ---- planning and host compression (Section 3, offline path) ------------ */

@@ -134,22 +134,13 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) tiles_kernel(LaunchAr
 }
 
 // ---------------------------------------------------------------- LZ77 (Non-Parallel)
-__device__ __forceinline__ bool leb(const uint8_t* s, uint32_t len, uint32_t& p, uint32_t& v) {
-    v = 0;
-    for (uint32_t sh = 0; sh <= 28; sh += 7) {
-        if (p >= len) return false;
-        uint32_t byte = __ldg(s + p++);
-        v |= (byte & 0x7Fu) << sh;
-        if (!(byte & 0x80u)) return true;
-    }
-    return false;
-}
-
-// One warp decodes one block: every lane parses the same token (broadcast
-// loads), then the lanes copy the literals and the match 32 bytes at a time.
-// A match of offset `off` reads out[p - off + (k mod off)], which lies
-// before p, so all lanes copy in parallel even when the match overlaps
-// itself.
+// One warp decodes one block.  Every lane parses the same token: the eight
+// bytes at the token's start arrive as three aligned words (broadcast loads)
+// and the LEB128 literal length, u16 offset and LEB128 match length are taken
+// from them with shifts, so a token costs one round of loads.  The lanes then
+// copy the literals and the match 32 bytes at a time.  A match of offset
+// `off` reads out[p - off + (k mod off)], which lies before p, so all lanes
+// copy in parallel even when the match overlaps itself.
 __device__ void lz_block(const ZfDevChunk& c, uint32_t* err) {
     const uint32_t lane = threadIdx.x & 31;
     zfd::Hdr h;
@@ -169,22 +160,50 @@ __device__ void lz_block(const ZfDevChunk& c, uint32_t* err) {
     }
     const uint8_t* lit = c.blob + h.off[1];
     const uint32_t tl = h.len[0], ll_total = h.len[1], rows = h.rows;
+    // words readable from the token section to the end of the blob (16-byte granules)
+    const uint32_t s0_words = (c.blob_bytes - h.off[0]) >> 2;
+    const uint32_t* s0w = reinterpret_cast<const uint32_t*>(s0);
     uint32_t tp = 0, lp = 0, op = 0;
     bool ok = true;
     for (uint32_t t = 0; t < h.n_aux; t++) {
-        uint32_t ll;
-        if (!leb(s0, tl, tp, ll) || lp + ll > ll_total || op + ll > rows) { ok = false; break; }
+        const uint32_t w = tp >> 2, sh = (tp & 3) * 8;
+        const uint32_t a = w < s0_words ? __ldg(s0w + w) : 0u;
+        const uint32_t b = w + 1 < s0_words ? __ldg(s0w + w + 1) : 0u;
+        const uint32_t cc = w + 2 < s0_words ? __ldg(s0w + w + 2) : 0u;
+        uint64_t x = ((uint64_t)__funnelshift_r(b, cc, sh) << 32) | __funnelshift_r(a, b, sh);
+        // literal length: LEB128, at most 3 bytes in a 64 KiB block
+        uint32_t ll = (uint32_t)x & 0x7F, n = 1;
+        if (x & 0x80) {
+            ll |= ((uint32_t)(x >> 8) & 0x7F) << 7;
+            n = 2;
+            if (x & 0x8000) {
+                ll |= ((uint32_t)(x >> 16) & 0x7F) << 14;
+                n = 3;
+                if (x & 0x800000) { ok = false; break; }
+            }
+        }
+        tp += n;
+        if (tp > tl || lp + ll > ll_total || op + ll > rows) { ok = false; break; }
         for (uint32_t i = lane; i < ll; i += 32) dst[op + i] = __ldg(lit + lp + i);
         op += ll;
         lp += ll;
         if (t + 1 == h.n_aux) break;
-        if (tp + 2 > tl) { ok = false; break; }
-        uint32_t off = (uint32_t)__ldg(s0 + tp) | ((uint32_t)__ldg(s0 + tp + 1) << 8);
-        tp += 2;
-        uint32_t ml;
-        if (!leb(s0, tl, tp, ml)) { ok = false; break; }
+        x >>= 8 * n;
+        const uint32_t off = (uint32_t)x & 0xFFFF;
+        x >>= 16;
+        uint32_t ml = (uint32_t)x & 0x7F, m = 1;
+        if (x & 0x80) {
+            ml |= ((uint32_t)(x >> 8) & 0x7F) << 7;
+            m = 2;
+            if (x & 0x8000) {
+                ml |= ((uint32_t)(x >> 16) & 0x7F) << 14;
+                m = 3;
+                if (x & 0x800000) { ok = false; break; }
+            }
+        }
+        tp += 2 + m;
         ml += zf::kLzMinMatch;
-        if (off == 0 || off > op || op + ml > rows) { ok = false; break; }
+        if (tp > tl || off == 0 || off > op || op + ml > rows) { ok = false; break; }
         __syncwarp();
         if (off >= ml) {
             for (uint32_t k = lane; k < ml; k += 32) dst[op + k] = dst[op - off + k];

@@ -8,7 +8,7 @@ __all__ = [
     "geometric_gaps", "sorted_keys", "run_lengths_geometric", "dates_rle",
     "zipf_cdf", "zipf_ranks", "vocabulary", "text_column", "lognormal_cents",
     "dict_codes", "rle_distribution", "DATE_LO", "DATE_HI", "parallel_rows", "FACT_COLUMNS", "fact_column",
-    "fact_pieces",
+    "fact_pieces", "SELECTOR_FAMILIES", "selector_column",
 ]
 
 _M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
@@ -168,19 +168,25 @@ def zipf_ranks(seed: int, stream: int, start: int, n: int, cdf: np.ndarray) -> n
 
 
 def vocabulary(seed: int, nwords: int = 5000, lmin: int = 3, lmax: int = 12) -> list[bytes]:
-    """``nwords`` distinct lowercase words of length lmin..lmax (duplicates redrawn)."""
+    """``nwords`` distinct lowercase words of length lmin..lmax, in draw order
+    (a repeated draw is skipped)."""
     words: list[bytes] = []
     seen: set[bytes] = set()
-    i = 0
+    start = 0
     while len(words) < nwords:
-        ln = int(uniform_int(seed, 301, i, 1, lmin, lmax + 1)[0])
-        letters = uniform_int(seed, 302 + i % 1000003, 0, ln, 0, 26)
-        w = bytes((letters + ord("a")).astype(np.uint8).tolist())
-        i += 1
-        if w in seen:
-            continue
-        seen.add(w)
-        words.append(w)
+        batch = 2 * (nwords - len(words)) + 64
+        lens = uniform_int(seed, 301, start, batch, lmin, lmax + 1)
+        letters = uniform_int(seed, 302, start * lmax, batch * lmax, 0, 26).reshape(batch, lmax) + ord("a")
+        rows = letters.astype(np.uint8)
+        for i in range(batch):
+            w = rows[i, : lens[i]].tobytes()
+            if w in seen:
+                continue
+            seen.add(w)
+            words.append(w)
+            if len(words) == nwords:
+                break
+        start += batch
     return words
 
 
@@ -339,3 +345,68 @@ def fact_pieces(seed: int, idx: int, n: int, lo_bytes: int = 4 << 20, hi_bytes: 
         total += rows
         k += 1
     return out
+
+
+SELECTOR_FAMILIES = ("uniform", "zipf", "sorted", "runs", "text")
+
+
+def selector_column(seed: int, cap_rows: int | None = None):
+    """One column of the selector's training / held-out sets (seeded).
+
+    Family = seed mod 5: uniform (range 2^1..2^40), zipf (2..100,000
+    distinct values, s in [0.8, 1.5]), sorted (geometric gaps, mean 2..16),
+    runs (geometric run lengths, mean 2..256) or text (Zipf words from a
+    100..20,000-word vocabulary).  Integer families pick int32 or int64 by
+    seed.  Rows are log-uniform over [1M, 64M], cut to ``cap_rows`` when
+    given.  Returns (values or bytes, offsets or None, meta)."""
+    fam = SELECTOR_FAMILIES[seed % 5]
+    u = uniform_unit(seed, 900, 0, 8)
+    rows = int(round(np.exp(np.log(1 << 20) + u[0] * (np.log(64 << 20) - np.log(1 << 20)))))
+    if cap_rows:
+        rows = min(rows, cap_rows)
+    meta = {"family": fam, "rows": rows}
+    if fam == "text":
+        vocab = int(np.exp(np.log(100) + u[1] * (np.log(20000) - np.log(100))))
+        s = 0.8 + 0.7 * u[2]
+        target = min(rows * 12, 8 << 20)          # about 12 bytes per row of 1-2 words, at most 8 MiB
+        data, offs = text_column(seed, target, nwords=vocab, zipf_s=s, wmin=1, wmax=2)
+        meta.update(vocab=vocab, zipf_s=s, bytes=len(data))
+        return data, offs, meta
+    i64 = u[3] < 0.5
+    dt = np.int64 if i64 else np.int32
+    meta["dtype"] = "int64" if i64 else "int32"
+    if fam == "uniform":
+        k = 1 + int(u[1] * (40 if i64 else 30))
+        lo = int(uniform_int(seed, 901, 0, 1, -(1 << 30), 1 << 30)[0]) if not i64 else \
+            int(uniform_int(seed, 901, 0, 1, -(1 << 31), 1 << 31)[0]) << 8
+        span = 1 << k
+        h = hash_u64(seed, 902, np.arange(rows, dtype=np.uint64))
+        x = (lo + (h >> np.uint64(64 - k)).astype(np.int64)) if k < 64 else h.astype(np.int64)
+        meta.update(bits=k)
+        return x.astype(dt), None, meta
+    if fam == "zipf":
+        nd = int(np.exp(np.log(2) + u[1] * (np.log(100000) - np.log(2))))
+        s = 0.8 + 0.7 * u[2]
+        vals = uniform_int(seed, 903, 0, nd, -(1 << 31), 1 << 31)
+        if i64:
+            vals = vals * 4099
+        r = parallel_rows(lambda a, c: zipf_ranks(seed, 904, a, c, zipf_cdf(nd, s)), rows)
+        meta.update(ndistinct=nd, zipf_s=s)
+        return vals[r].astype(dt), None, meta
+    if fam == "sorted":
+        bits = 1 + int(u[1] * 4)
+        g = parallel_rows(lambda a, c: geometric_gaps(seed, 905, a, c, bits), rows)
+        meta.update(gap_bits=bits)
+        return np.cumsum(g).astype(dt), None, meta
+    # runs
+    mean_bits = 1 + int(u[1] * 8)
+    vrange = 1 << (2 + int(u[2] * 28))
+    est = rows // (1 << mean_bits) + 1024
+    while True:
+        lens = geometric_gaps(seed, 906, 0, est, mean_bits)
+        if lens.sum() >= rows:
+            break
+        est *= 2
+    vals = uniform_int(seed, 907, 0, est, 0, min(vrange, 1 << 32)) - (vrange // 2)
+    meta.update(run_bits=mean_bits, value_range=vrange)
+    return np.repeat(vals, lens)[:rows].astype(dt), None, meta
