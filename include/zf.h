@@ -50,11 +50,12 @@
  *     RLE      s0 = run values, s1 = u32 run lengths (n_aux runs),
  *              s2 = one {u32 run, u32 rows of that run before} entry per
  *              1024 rows (the run holding row 1024*t)
- *     LZ77     rows = raw bytes of one block; flags bit0 = stored raw (s0);
- *              otherwise s0 = tokens, s1 = literals; a token is a LEB128
- *              literal length and, unless it is the last of the block, a u16
- *              offset (1..65535) and a LEB128 (match length - 4); a LEB128
- *              field takes at most 3 bytes
+ *     LZ77     rows = raw bytes of one block, n_aux = tokens T; flags bit0 =
+ *              stored raw (s0).  Otherwise s0 = 2T-1 LEB128 lengths (each at
+ *              most 3 bytes): literal length of token t at index 2t, match
+ *              length - 4 of token t at 2t+1; s1 = T-1 u16 offsets (1..65535);
+ *              s2 = literal bytes.  Token t copies its literals, then (all but
+ *              the last token) `length` bytes from `offset` bytes back
  *   Bit-packing: value i occupies stream bits [i*b, i*b+b), least
  *   significant bit first; stream bit k is bit k%8 of byte k/8.
  */

@@ -11,7 +11,7 @@
  *   Dictionary encoding                Section 2.1; Section 3.1, Fig. 6(a)
  *   Delta encoding                     Section 2.1 ("Delta encoding")
  *   Run-length encoding, presum        Section 2.1 ("RLE"); Section 3.2
- *   LZ77 back-references               Section 2.1 ("LZ77-based algorithms")
+ *   LZ77 back-references               Section 2.1 (LZ77-based algorithms)
  *   Independent chunks                 Section 3.1 (Non-Parallel "file chunking")
  *
  * Decoders are the definitions written out: values are read bit by bit,
@@ -151,7 +151,7 @@ static uint64_t chunk_bound(int scheme, int dtype, uint64_t rows) {
     case ORC_DICT_BP: return b + rows * sz + rows * 2 + 16;
     case ORC_DELTA_BP: return b + (rows / DELTA_BLOCK + 1) * (24 + 16) + rows * sz + 16;
     case ORC_RLE: return b + rows * (sz + 4) + (rows / RLE_DIR_ROWS + 1) * 8;
-    case ORC_LZ77: return b + rows + rows / 8 + 64;
+    case ORC_LZ77: return b + rows + rows / 2 + 64;
     }
     return 0;
 }
@@ -304,28 +304,31 @@ static uint32_t lz_hash(const uint8_t* s) {
     return (v * 2654435761u) >> (32 - LZ_HASH_BITS);
 }
 static uint64_t enc_lz(uint8_t* p, const uint8_t* src, uint32_t m) {
-    uint8_t* tok = (uint8_t*)malloc(3ull * m + 16);
+    /* three streams: lengths (LEB128 literal length of every token and, between
+     * them, match length - 4), u16 offsets, literal bytes */
+    uint8_t* len = (uint8_t*)malloc(6ull * m + 16);
+    uint8_t* offs = (uint8_t*)malloc(2ull * m + 16);
     uint8_t* lit = (uint8_t*)malloc((uint64_t)m + 16);
     int32_t* table = (int32_t*)malloc(sizeof(int32_t) << LZ_HASH_BITS);
     for (uint32_t i = 0; i < (1u << LZ_HASH_BITS); i++) table[i] = -1;
-    uint32_t nt = 0, ntok = 0, nlit = 0, lit_start = 0, pos = 0;
+    uint32_t nl = 0, no = 0, ntok = 0, nlit = 0, lit_start = 0, pos = 0;
     while (pos + LZ_MIN_MATCH <= m) {
         uint32_t h = lz_hash(src + pos);
         int32_t cand = table[h];
         table[h] = (int32_t)pos;
         if (cand >= 0 && pos - (uint32_t)cand <= LZ_MAX_OFFSET &&
             memcmp(src + cand, src + pos, LZ_MIN_MATCH) == 0) {
-            uint32_t len = LZ_MIN_MATCH;
-            while (pos + len < m && src[cand + len] == src[pos + len]) len++;
+            uint32_t mlen = LZ_MIN_MATCH;
+            while (pos + mlen < m && src[cand + mlen] == src[pos + mlen]) mlen++;
             uint32_t ll = pos - lit_start;
-            nt += leb128_put(tok + nt, ll);
+            nl += leb128_put(len + nl, ll);
             memcpy(lit + nlit, src + lit_start, ll);
             nlit += ll;
-            put_u16(tok + nt, pos - (uint32_t)cand);
-            nt += 2;
-            nt += leb128_put(tok + nt, len - LZ_MIN_MATCH);
+            nl += leb128_put(len + nl, mlen - LZ_MIN_MATCH);
+            put_u16(offs + no, pos - (uint32_t)cand);
+            no += 2;
             ntok++;
-            pos += len;
+            pos += mlen;
             lit_start = pos;
         } else {
             pos++;
@@ -333,23 +336,25 @@ static uint64_t enc_lz(uint8_t* p, const uint8_t* src, uint32_t m) {
     }
     /* final token: the remaining literals, no match */
     uint32_t ll = m - lit_start;
-    nt += leb128_put(tok + nt, ll);
+    nl += leb128_put(len + nl, ll);
     memcpy(lit + nlit, src + lit_start, ll);
     nlit += ll;
     ntok++;
     chunk_w w = {p, 64};
-    if ((uint64_t)nt + nlit >= m) {          /* does not compress: store the block raw */
+    if ((uint64_t)nl + no + nlit >= m) {     /* does not compress: store the block raw */
         chunk_header(p, ORC_LZ77, ORC_BYTES, 0, 1, m, 0, 0);
         uint64_t off = sec_begin(&w, 0, m);
         memcpy(p + off, src, m);
     } else {
         chunk_header(p, ORC_LZ77, ORC_BYTES, 0, 0, m, ntok, 0);
-        uint64_t toff = sec_begin(&w, 0, nt);
-        memcpy(p + toff, tok, nt);
-        uint64_t loff = sec_begin(&w, 1, nlit);
-        memcpy(p + loff, lit, nlit);
+        uint64_t a = sec_begin(&w, 0, nl);
+        memcpy(p + a, len, nl);
+        uint64_t b = sec_begin(&w, 1, no);
+        if (no) memcpy(p + b, offs, no);
+        uint64_t c = sec_begin(&w, 2, nlit);
+        if (nlit) memcpy(p + c, lit, nlit);
     }
-    free(tok); free(lit); free(table);
+    free(len); free(offs); free(lit); free(table);
     return align16(w.end);
 }
 
@@ -504,38 +509,39 @@ int orc_decode_chunk(const uint8_t* c, uint64_t len, void* out, uint64_t out_cap
             memcpy(o, s0, m);
             return ORC_OK;
         }
-        if (!sec_ok(c, len, 0) || !sec_ok(c, len, 1)) return ORC_ECORRUPT;
-        uint32_t tp = 0, lp = 0, op = 0;
+        /* token t: literal length (varint 2t), the literals, then unless t is the
+         * last token a back-reference: offset t, length varint 2t+1 plus 4 */
+        if (!sec_ok(c, len, 0) || !sec_ok(c, len, 1) || !sec_ok(c, len, 2) || n_aux == 0 ||
+            l1 != 2ull * (n_aux - 1)) return ORC_ECORRUPT;
+        uint32_t vp = 0, lp = 0, op = 0;
         for (uint32_t t = 0; t < n_aux; t++) {
             uint32_t ll = 0, sh = 0;
             for (;;) {
-                if (tp >= l0 || sh > 28) return ORC_ECORRUPT;
-                uint8_t byte = s0[tp++];
+                if (vp >= l0 || sh > 14) return ORC_ECORRUPT; /* at most 3 bytes */
+                uint8_t byte = s0[vp++];
                 ll |= (uint32_t)(byte & 0x7F) << sh;
                 sh += 7;
                 if (!(byte & 0x80)) break;
             }
-            if ((uint64_t)lp + ll > l1 || (uint64_t)op + ll > m) return ORC_ECORRUPT;
-            for (uint32_t k = 0; k < ll; k++) o[op++] = s1[lp++];
+            if ((uint64_t)lp + ll > l2 || (uint64_t)op + ll > m) return ORC_ECORRUPT;
+            for (uint32_t k = 0; k < ll; k++) o[op++] = s2[lp++];
             if (t + 1 == n_aux) break;
-            if (tp + 2 > l0) return ORC_ECORRUPT;
-            uint32_t off = get_u16(s0 + tp);
-            tp += 2;
             uint32_t ml = 0;
             sh = 0;
             for (;;) {
-                if (tp >= l0 || sh > 28) return ORC_ECORRUPT;
-                uint8_t byte = s0[tp++];
+                if (vp >= l0 || sh > 14) return ORC_ECORRUPT; /* at most 3 bytes */
+                uint8_t byte = s0[vp++];
                 ml |= (uint32_t)(byte & 0x7F) << sh;
                 sh += 7;
                 if (!(byte & 0x80)) break;
             }
             ml += LZ_MIN_MATCH;
+            uint32_t off = get_u16(s1 + 2ull * t);
             if (off == 0 || off > op || (uint64_t)op + ml > m) return ORC_ECORRUPT;
             /* back-reference: byte by byte, so a source that overlaps the output repeats */
             for (uint32_t k = 0; k < ml; k++) { o[op] = o[op - off]; op++; }
         }
-        if (op != m || tp != l0 || lp != l1) return ORC_ECORRUPT;
+        if (op != m || vp != l0 || lp != l2) return ORC_ECORRUPT;
         return ORC_OK;
     }
     }

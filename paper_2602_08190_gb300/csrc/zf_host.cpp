@@ -220,12 +220,14 @@ uint32_t leb128(uint8_t* p, uint32_t v) {
 
 // Greedy LZ77 over one block: a hash of 4 bytes indexes the most recent
 // position; every position, including those inside a match, is inserted.
+// Output streams: lengths (LEB128 literal length of each token, and between
+// tokens the match length - 4), u16 offsets, literal bytes.
 void enc_lz(const uint8_t* s, uint32_t m, Out& o) {
     constexpr int HB = 15;
     std::vector<int32_t> table(1u << HB, -1);
-    std::vector<uint8_t> tok;
-    std::vector<uint8_t> lit;
-    tok.reserve(m / 2 + 16);
+    std::vector<uint8_t> lens, offs, lit;
+    lens.reserve(m / 4 + 16);
+    offs.reserve(m / 4 + 16);
     lit.reserve(m + 16);
     auto hash = [&](uint32_t p) {
         uint32_t v;
@@ -247,23 +249,21 @@ void enc_lz(const uint8_t* s, uint32_t m, Out& o) {
             pos++;
             continue;
         }
-        uint32_t ll = pos - lit_start;
-        tok.insert(tok.end(), tmp, tmp + leb128(tmp, ll));
+        lens.insert(lens.end(), tmp, tmp + leb128(tmp, pos - lit_start));
         lit.insert(lit.end(), s + lit_start, s + pos);
-        uint32_t off = pos - (uint32_t)cand;
-        tok.push_back((uint8_t)off);
-        tok.push_back((uint8_t)(off >> 8));
-        tok.insert(tok.end(), tmp, tmp + leb128(tmp, len - kLzMinMatch));
+        lens.insert(lens.end(), tmp, tmp + leb128(tmp, len - kLzMinMatch));
+        const uint32_t off = pos - (uint32_t)cand;
+        offs.push_back((uint8_t)off);
+        offs.push_back((uint8_t)(off >> 8));
         ntok++;
         for (uint32_t q = pos + 1; q < pos + len && q + kLzMinMatch <= m; q++) table[hash(q)] = (int32_t)q;
         pos += len;
         lit_start = pos;
     }
-    uint32_t ll = m - lit_start;
-    tok.insert(tok.end(), tmp, tmp + leb128(tmp, ll));
+    lens.insert(lens.end(), tmp, tmp + leb128(tmp, m - lit_start));
     lit.insert(lit.end(), s + lit_start, s + m);
     ntok++;
-    if (tok.size() + lit.size() >= m) {
+    if (lens.size() + offs.size() + lit.size() >= m) {
         o.b.assign(align16(kChunkHeader + m), 0);
         ChunkWriter w(o);
         w.header(ZF_LZ77, ZF_BYTES, 0, 1, m, 0, 0);
@@ -271,13 +271,15 @@ void enc_lz(const uint8_t* s, uint32_t m, Out& o) {
         if (m) memcpy(&o.b[off], s, m);
         return;
     }
-    o.b.assign(align16(align16(kChunkHeader + tok.size()) + lit.size()), 0);
+    o.b.assign(align16(align16(align16(kChunkHeader + lens.size()) + offs.size()) + lit.size()), 0);
     ChunkWriter w(o);
     w.header(ZF_LZ77, ZF_BYTES, 0, 0, m, ntok, 0);
-    uint64_t toff = w.section(0, tok.size());
-    memcpy(&o.b[toff], tok.data(), tok.size());
-    uint64_t loff = w.section(1, lit.size());
-    if (!lit.empty()) memcpy(&o.b[loff], lit.data(), lit.size());
+    uint64_t a = w.section(0, lens.size());
+    memcpy(&o.b[a], lens.data(), lens.size());
+    uint64_t b = w.section(1, offs.size());
+    if (!offs.empty()) memcpy(&o.b[b], offs.data(), offs.size());
+    uint64_t c = w.section(2, lit.size());
+    if (!lit.empty()) memcpy(&o.b[c], lit.data(), lit.size());
 }
 
 // ------------------------------------------------------------------ column assembly
@@ -519,7 +521,7 @@ bool check_chunk(const uint8_t* c, uint64_t len, int scheme, int dtype, uint32_t
     case ZF_DICT_BP: nsec = 2; break;
     case ZF_DELTA_BP: nsec = 2; break;
     case ZF_RLE: nsec = 3; break;
-    case ZF_LZ77: nsec = (c[7] & 1) ? 1 : 2; break;
+    case ZF_LZ77: nsec = (c[7] & 1) ? 1 : 3; break;
     default: return fail(why, "unknown scheme");
     }
     for (int s = 0; s < nsec; s++)
@@ -561,6 +563,8 @@ bool check_chunk(const uint8_t* c, uint64_t len, int scheme, int dtype, uint32_t
     case ZF_LZ77:
         if (rows > kLzBlock) return fail(why, "LZ77 block above 64 KiB");
         if ((c[7] & 1) && ln[0] != rows) return fail(why, "raw LZ77 block length");
+        if (!(c[7] & 1) && (n_aux == 0 || ln[1] != 2ull * (n_aux - 1) || ln[0] < 2ull * n_aux - 1))
+            return fail(why, "LZ77 token streams");
         break;
     }
     return true;

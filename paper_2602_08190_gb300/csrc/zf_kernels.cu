@@ -134,14 +134,110 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) tiles_kernel(LaunchAr
 }
 
 // ---------------------------------------------------------------- LZ77 (Non-Parallel)
-// One warp decodes one block.  Every lane parses the same token: the eight
-// bytes at the token's start arrive as three aligned words (broadcast loads)
-// and the LEB128 literal length, u16 offset and LEB128 match length are taken
-// from them with shifts, so a token costs one round of loads.  The lanes then
-// copy the literals and the match 32 bytes at a time.  A match of offset
-// `off` reads out[p - off + (k mod off)], which lies before p, so all lanes
-// copy in parallel even when the match overlaps itself.
-__device__ void lz_block(const ZfDevChunk& c, uint32_t* err) {
+// One warp decodes one block, 32 tokens at a time (lane i holds token t0+i).
+//   Lengths: the LEB128 lengths stream is read 32 bytes per step, one byte per
+//   lane; a ballot of the bytes without a continuation bit locates the ends
+//   of the varints, each end lane assembles its value from the bytes of the
+//   lanes before it (shuffles), and the values go to a ring in shared memory.
+//   Positions: two warp scans of the lengths give every token of the batch
+//   its literal range in s2 and its output range, so the whole batch is
+//   validated before a byte moves.
+//   Literals: the batch's literal bytes are contiguous in s2; the lanes copy
+//   them 32 at a time, each finding its token by a binary search over the
+//   lanes' literal starts.
+//   Matches: rounds.  Every output byte before the first unfinished match is
+//   final, so every match whose source ends there is ready; the ready matches'
+//   bytes are copied as one flat list (all loads of a group issued before its
+//   stores), and the round repeats until the batch is done.  The first
+//   unfinished match is always ready, so there are at most 32 rounds.  A match
+//   of offset `off` reads out[p - off + (k mod off)] for its k-th byte, which
+//   lies before p: a match that overlaps its own output repeats its source.
+constexpr uint32_t kLzLenRing = 512;   // pre-parsed lengths per warp
+constexpr uint32_t kLzBatch = 480;     // lengths parsed ahead per refill (at most ring - 32)
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+
+struct LzParse {
+    uint32_t vp = 0;        // next byte of the lengths stream
+    uint32_t parsed = 0;    // lengths parsed so far
+    uint32_t carry = 0;     // value bits of a varint cut by the last step
+    uint32_t carry_n = 0;   // its bytes so far
+    bool bad = false;
+};
+
+// One 32-byte step of the lengths stream; `byte` is this lane's byte (0x80
+// past the end).
+__device__ __forceinline__ void lz_parse_step(uint32_t byte, uint32_t l0, uint32_t* lr, LzParse& ps, uint32_t lane) {
+    const bool valid = ps.vp + lane < l0;
+    const uint32_t ends = __ballot_sync(kFull, valid && !(byte & 0x80u));
+    const uint32_t b1 = __shfl_up_sync(kFull, byte, 1);
+    const uint32_t b2 = __shfl_up_sync(kFull, byte, 2);
+    bool bad = false;
+    if ((ends >> lane) & 1) {
+        const uint32_t below = ends & ((1u << lane) - 1u);
+        const int pt = below ? 31 - __clz(below) : -1;   // previous end in this step
+        const uint32_t n = lane - pt;                    // bytes of this varint in this step
+        uint32_t v = byte & 0x7Fu, nb = n;
+        if (n >= 2) v = (b1 & 0x7Fu) | (v << 7);
+        if (n >= 3) v = (b2 & 0x7Fu) | (v << 7);
+        if (pt < 0 && ps.carry_n) {                      // continues the varint cut by the last step
+            v = ps.carry | (v << (7 * ps.carry_n));
+            nb += ps.carry_n;
+        }
+        bad = nb > 3;
+        lr[(ps.parsed + __popc(below)) & (kLzLenRing - 1)] = v;
+    }
+    // bytes after the last end start a varint that the next step finishes
+    const int last = ends ? 31 - __clz(ends) : -1;
+    uint32_t tail = min(32u, l0 - ps.vp) - (uint32_t)(last + 1);
+    uint32_t tv = 0;
+    for (uint32_t j = 0; j < tail && j < 3; j++)
+        tv |= (__shfl_sync(kFull, byte, last + 1 + j) & 0x7Fu) << (7 * j);
+    if (last < 0) {                                      // the whole step continued the varint
+        tv = ps.carry | (tv << (7 * ps.carry_n));
+        tail += ps.carry_n;
+    }
+    ps.carry = tv;
+    ps.carry_n = tail;
+    ps.parsed += __popc(ends);
+    ps.vp += 32;
+    ps.bad = __any_sync(kFull, bad || tail > 3) || ps.bad;
+}
+
+// Parse lengths until `upto` are available (or the stream ends); the bytes of
+// four steps are loaded before the first is used.
+__device__ __forceinline__ void lz_parse(const uint8_t* s0, uint32_t l0, uint32_t* lr, LzParse& ps, uint32_t upto,
+                                         uint32_t lane) {
+    while (!ps.bad && ps.parsed < upto && ps.vp < l0) {
+        uint32_t by[4];
+#pragma unroll
+        for (uint32_t q = 0; q < 4; q++) {
+            const uint32_t pos = ps.vp + 32 * q + lane;
+            by[q] = pos < l0 ? __ldg(s0 + pos) : 0x80u;
+        }
+#pragma unroll
+        for (uint32_t q = 0; q < 4; q++) {
+            if (ps.bad || ps.parsed >= upto || ps.vp >= l0) break;
+            lz_parse_step(by[q], l0, lr, ps, lane);
+        }
+    }
+    if (ps.vp > l0) ps.vp = l0;
+    __syncwarp();
+}
+
+// Largest lane i whose `start` (nondecreasing over the lanes) is <= j.
+__device__ __forceinline__ uint32_t lz_find(uint32_t start, uint32_t j) {
+    uint32_t i = 0;
+#pragma unroll
+    for (uint32_t s = 16; s; s >>= 1)
+        if (__shfl_sync(kFull, start, i + s) <= j) i += s;
+    return i;
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+__device__ void lz_block(const ZfDevChunk& c, uint32_t* lr, uint32_t* err) {
     const uint32_t lane = threadIdx.x & 31;
     zfd::Hdr h;
     zfd::load_hdr(c.blob, h);
@@ -158,72 +254,110 @@ __device__ void lz_block(const ZfDevChunk& c, uint32_t* err) {
         for (uint32_t i = n16 * 16 + lane; i < h.rows; i += 32) dst[i] = s0[i];
         return;
     }
-    const uint8_t* lit = c.blob + h.off[1];
-    const uint32_t tl = h.len[0], ll_total = h.len[1], rows = h.rows;
-    // words readable from the token section to the end of the blob (16-byte granules)
-    const uint32_t s0_words = (c.blob_bytes - h.off[0]) >> 2;
-    const uint32_t* s0w = reinterpret_cast<const uint32_t*>(s0);
-    uint32_t tp = 0, lp = 0, op = 0;
-    bool ok = true;
-    for (uint32_t t = 0; t < h.n_aux; t++) {
-        const uint32_t w = tp >> 2, sh = (tp & 3) * 8;
-        const uint32_t a = w < s0_words ? __ldg(s0w + w) : 0u;
-        const uint32_t b = w + 1 < s0_words ? __ldg(s0w + w + 1) : 0u;
-        const uint32_t cc = w + 2 < s0_words ? __ldg(s0w + w + 2) : 0u;
-        uint64_t x = ((uint64_t)__funnelshift_r(b, cc, sh) << 32) | __funnelshift_r(a, b, sh);
-        // literal length: LEB128, at most 3 bytes in a 64 KiB block
-        uint32_t ll = (uint32_t)x & 0x7F, n = 1;
-        if (x & 0x80) {
-            ll |= ((uint32_t)(x >> 8) & 0x7F) << 7;
-            n = 2;
-            if (x & 0x8000) {
-                ll |= ((uint32_t)(x >> 16) & 0x7F) << 14;
-                n = 3;
-                if (x & 0x800000) { ok = false; break; }
-            }
-        }
-        tp += n;
-        if (tp > tl || lp + ll > ll_total || op + ll > rows) { ok = false; break; }
-        for (uint32_t i = lane; i < ll; i += 32) dst[op + i] = __ldg(lit + lp + i);
-        op += ll;
-        lp += ll;
-        if (t + 1 == h.n_aux) break;
-        x >>= 8 * n;
-        const uint32_t off = (uint32_t)x & 0xFFFF;
-        x >>= 16;
-        uint32_t ml = (uint32_t)x & 0x7F, m = 1;
-        if (x & 0x80) {
-            ml |= ((uint32_t)(x >> 8) & 0x7F) << 7;
-            m = 2;
-            if (x & 0x8000) {
-                ml |= ((uint32_t)(x >> 16) & 0x7F) << 14;
-                m = 3;
-                if (x & 0x800000) { ok = false; break; }
-            }
-        }
-        tp += 2 + m;
-        ml += zf::kLzMinMatch;
-        if (tp > tl || off == 0 || off > op || op + ml > rows) { ok = false; break; }
-        __syncwarp();
-        if (off >= ml) {
-            for (uint32_t k = lane; k < ml; k += 32) dst[op + k] = dst[op - off + k];
-        } else {
-            for (uint32_t k = lane; k < ml; k += 32) dst[op + k] = dst[op - off + k % off];
-        }
-        op += ml;
-        __syncwarp();
-    }
-    if (!ok || op != rows || tp != tl || lp != ll_total) {
+    const uint16_t* offs = reinterpret_cast<const uint16_t*>(c.blob + h.off[1]);
+    const uint8_t* lit = c.blob + h.off[2];
+    const uint32_t T = h.n_aux, l0 = h.len[0], l2 = h.len[2], rows = h.rows;
+    const uint32_t nlen = 2 * T - 1;                         // lengths in the stream
+    bool ok = T > 0 && h.len[1] == 2 * (T - 1);
+    if (!ok) {
         if (lane == 0) zfd::report(err, ZF_ECORRUPT, c.chunk_id);
+        return;
     }
+    // the three streams are read once, front to back: start them towards L2
+    for (uint32_t i = 128 * lane; i < l0; i += 4096) prefetch_l2(s0 + i);
+    for (uint32_t i = 128 * lane; i < h.len[1]; i += 4096) prefetch_l2(c.blob + h.off[1] + i);
+    for (uint32_t i = 128 * lane; i < l2; i += 4096) prefetch_l2(lit + i);
+    LzParse ps;
+    uint32_t lp = 0, op = 0;                                 // literal and output bytes done
+    for (uint32_t t0 = 0; t0 < T; t0 += 32) {
+        const uint32_t nt = min(32u, T - t0);
+        const uint32_t need = min(nlen, 2 * (t0 + nt));      // the last token has no match length
+        if (ps.parsed < need) {
+            lz_parse(s0, l0, lr, ps, min(nlen, 2 * t0 + kLzBatch), lane);
+            if (ps.bad || ps.parsed < need) { ok = false; break; }
+        }
+        const uint32_t t = t0 + lane;
+        const bool has_m = lane < nt && t + 1 < T;
+        const uint32_t ll = lane < nt ? lr[(2 * t) & (kLzLenRing - 1)] : 0;
+        const uint32_t ml = has_m ? lr[(2 * t + 1) & (kLzLenRing - 1)] + zf::kLzMinMatch : 0;
+        const uint32_t off = has_m ? __ldg(offs + t) : 0;
+        uint32_t lend = ll, oend = ll + ml;                  // inclusive sums over the lanes
+#pragma unroll
+        for (uint32_t d = 1; d < 32; d <<= 1) {
+            const uint32_t a = __shfl_up_sync(kFull, lend, d), b = __shfl_up_sync(kFull, oend, d);
+            if (lane >= d) { lend += a; oend += b; }
+        }
+        lend += lp;
+        oend += op;
+        const uint32_t lstart = lend - ll, mpos = oend - ml, ostart = mpos - ll;
+        // lengths are below 2^21, so none of the sums wrap
+        const bool bad = lend > l2 || oend > rows || (has_m && (off == 0 || off > mpos));
+        if (__any_sync(kFull, bad)) { ok = false; break; }
+        // literals
+        const uint32_t lb = __shfl_sync(kFull, lend, 31) - lp;
+        for (uint32_t base = 0; base < lb; base += 128) {
+            uint32_t v[4];
+#pragma unroll
+            for (uint32_t q = 0; q < 4; q++) {
+                const uint32_t jj = base + 32 * q + lane;
+                v[q] = jj < lb ? __ldg(lit + lp + jj) : 0;
+            }
+#pragma unroll
+            for (uint32_t q = 0; q < 4; q++) {
+                if (base + 32 * q >= lb) break;
+                const uint32_t j = lp + base + 32 * q + lane;
+                const uint32_t i = lz_find(lstart, j);
+                const uint32_t os = __shfl_sync(kFull, ostart, i), ls = __shfl_sync(kFull, lstart, i);
+                if (j < lp + lb) dst[os + (j - ls)] = (uint8_t)v[q];
+            }
+        }
+        __syncwarp();
+        // matches, in rounds
+        const uint32_t src = mpos - off;
+        uint32_t pend = __ballot_sync(kFull, has_m);
+        while (pend) {
+            const uint32_t hwm = __shfl_sync(kFull, mpos, __ffs(pend) - 1);
+            const bool ready = ((pend >> lane) & 1) && src + min(ml, off) <= hwm;
+            const uint32_t len = ready ? ml : 0;
+            uint32_t cend = len;
+#pragma unroll
+            for (uint32_t d = 1; d < 32; d <<= 1) {
+                const uint32_t a = __shfl_up_sync(kFull, cend, d);
+                if (lane >= d) cend += a;
+            }
+            const uint32_t total = __shfl_sync(kFull, cend, 31), cstart = cend - len;
+            for (uint32_t base = 0; base < total; base += 128) {
+                uint32_t v[4], to[4];
+#pragma unroll
+                for (uint32_t q = 0; q < 4; q++) {
+                    const uint32_t jj = base + 32 * q + lane;
+                    const uint32_t i = lz_find(cstart, jj);
+                    const uint32_t k = jj - __shfl_sync(kFull, cstart, i);
+                    const uint32_t o = __shfl_sync(kFull, off, i), m = __shfl_sync(kFull, ml, i);
+                    const uint32_t s = __shfl_sync(kFull, src, i) + (o >= m ? k : k % o);
+                    to[q] = __shfl_sync(kFull, mpos, i) + k;
+                    v[q] = jj < total ? dst[s] : 0;
+                }
+#pragma unroll
+                for (uint32_t q = 0; q < 4; q++)
+                    if (base + 32 * q + lane < total) dst[to[q]] = (uint8_t)v[q];
+            }
+            __syncwarp();
+            pend &= ~__ballot_sync(kFull, ready);
+        }
+        lp = __shfl_sync(kFull, lend, 31);
+        op = __shfl_sync(kFull, oend, 31);
+    }
+    // every length used, no varint left open, every literal and output byte accounted for
+    if (ok) ok = !ps.bad && ps.parsed == nlen && ps.carry_n == 0 && ps.vp >= l0 && op == rows && lp == l2;
+    if (!ok && lane == 0) zfd::report(err, ZF_ECORRUPT, c.chunk_id);
 }
 
-__global__ void __launch_bounds__(128) lz_kernel(const ZfDevChunk* chunks, uint32_t n, uint32_t* err) {
-    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t k = warp; k < n; k += nw) {
+__global__ void __launch_bounds__(32) lz_kernel(const ZfDevChunk* chunks, uint32_t n, uint32_t* err) {
+    __shared__ uint32_t lens[kLzLenRing];
+    for (uint32_t k = blockIdx.x; k < n; k += gridDim.x) {
         const ZfDevChunk c = chunks[k];
-        lz_block(c, err);
+        lz_block(c, lens, err);
         __syncwarp();
     }
 }
@@ -316,10 +450,12 @@ cudaError_t launch_tiles(const TileLaunch& L, cudaStream_t s) {
 
 cudaError_t launch_lz(const ZfDevChunk* chunks, uint32_t n, uint32_t* err, int num_sms, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    uint32_t blocks = (n + 3) / 4;
-    uint32_t cap = (uint32_t)num_sms * 16;
+    // one warp (one block) per CTA, so a small launch still spreads over
+    // every SM; up to 32 CTAs per SM, then warps loop over the rest
+    uint32_t blocks = n;
+    uint32_t cap = (uint32_t)num_sms * 32;
     if (blocks > cap) blocks = cap;
-    lz_kernel<<<blocks, 128, 0, s>>>(chunks, n, err);
+    lz_kernel<<<blocks, 32, 0, s>>>(chunks, n, err);
     return cudaGetLastError();
 }
 

@@ -285,33 +285,42 @@ def pin_lz(orc):
     assert np.array_equal(orc.decode(buf), t)
 
 
-def _lz_blob(tokens: bytes, lits: bytes, rows: int, ntok: int) -> bytes:
-    """A hand-built LZ77 chunk: header, tokens at 64, literals at the next 16-byte boundary."""
-    t_off = 64
-    l_off = (t_off + len(tokens) + 15) // 16 * 16
-    end = (l_off + len(lits) + 15) // 16 * 16
-    b = bytearray(end)
-    struct.pack_into("<IBBBBIIq", b, 0, 0x4B48435A, O.LZ77, O.BYTES, 0, 0, rows, ntok, 0)
-    struct.pack_into("<3I3I", b, 24, t_off, l_off, 0, len(tokens), len(lits), 0)
-    b[t_off:t_off + len(tokens)] = tokens
-    b[l_off:l_off + len(lits)] = lits
-    return bytes(b)
+def _lz_blob(lengths: bytes, offsets: bytes, lits: bytes, rows: int, ntok: int) -> bytes:
+    """A hand-built LZ77 chunk: header, then the lengths, offsets and literal
+    streams, each at the next 16-byte boundary."""
+    a = 64
+    b = (a + len(lengths) + 15) // 16 * 16
+    c = (b + len(offsets) + 15) // 16 * 16
+    end = (c + len(lits) + 15) // 16 * 16
+    blob = bytearray(end)
+    struct.pack_into("<IBBBBIIq", blob, 0, 0x4B48435A, O.LZ77, O.BYTES, 0, 0, rows, ntok, 0)
+    struct.pack_into("<3I3I", blob, 24, a, b, c, len(lengths), len(offsets), len(lits))
+    blob[a:a + len(lengths)] = lengths
+    blob[b:b + len(offsets)] = offsets
+    blob[c:c + len(lits)] = lits
+    return bytes(blob)
 
 
 def pin_lz_hand_streams(orc):
     # one literal then a back-reference of offset 1: the byte repeats (source overlaps output)
-    blob = _lz_blob(bytes([1, 1, 0, 3, 0]), b"z", 8, 2)
+    blob = _lz_blob(bytes([1, 3, 0]), bytes([1, 0]), b"z", 8, 2)
     assert orc.decode_chunk(blob, np.uint8).tobytes() == b"zzzzzzzz"
     # offset 2 over "xy": xyxyxyx
-    blob = _lz_blob(bytes([2, 2, 0, 1, 0]), b"xy", 7, 2)
+    blob = _lz_blob(bytes([2, 1, 0]), bytes([2, 0]), b"xy", 7, 2)
     assert orc.decode_chunk(blob, np.uint8).tobytes() == b"xyxyxyx"
+    # a length may take up to three LEB128 bytes, padded or not: 0x81 0x80 0x00 is 1
+    blob = _lz_blob(bytes([0x81, 0x80, 0x00, 0x83, 0x00, 0]), bytes([1, 0]), b"z", 8, 2)
+    assert orc.decode_chunk(blob, np.uint8).tobytes() == b"zzzzzzzz"
     # malformed streams are rejected, not decoded
     bad = [
-        _lz_blob(bytes([1, 0, 0, 3, 0]), b"z", 8, 2),     # offset 0
-        _lz_blob(bytes([1, 2, 0, 3, 0]), b"z", 8, 2),     # offset beyond the bytes produced
-        _lz_blob(bytes([1, 1, 0, 9, 0]), b"z", 8, 2),     # match runs past the block
-        _lz_blob(bytes([3]), b"z", 3, 1),                 # literals past the literal stream
-        _lz_blob(bytes([1, 1, 0, 3, 0, 0]), b"z", 8, 2),  # unread token bytes
+        _lz_blob(bytes([1, 3, 0]), bytes([0, 0]), b"z", 8, 2),      # offset 0
+        _lz_blob(bytes([1, 3, 0]), bytes([2, 0]), b"z", 8, 2),      # offset beyond the bytes produced
+        _lz_blob(bytes([1, 9, 0]), bytes([1, 0]), b"z", 8, 2),      # match runs past the block
+        _lz_blob(bytes([3]), b"", b"z", 3, 1),                      # literals past the literal stream
+        _lz_blob(bytes([1, 3, 0, 0]), bytes([1, 0]), b"z", 8, 2),   # unread length bytes
+        _lz_blob(bytes([1, 3, 0]), bytes([1, 0, 1, 0]), b"z", 8, 2),  # offsets stream of the wrong size
+        _lz_blob(bytes([0x81, 0x80, 0x80, 0x00, 3, 0]), bytes([1, 0]), b"z", 8, 2),  # 4-byte length
+        _lz_blob(bytes([1, 3, 0x80]), bytes([1, 0]), b"z", 8, 2),   # last length left open
     ]
     for blob in bad:
         try:

@@ -214,8 +214,15 @@ def test_device_detects_corrupt_streams(gpu):
     o = np.array([0, len(t)], np.int32)
     b = oracle.encode_strings(t, o)
     off, ln, r0, rows, ch = chunks_of(oracle.default(), b)[0]
-    bad = _corrupt(b, lambda bb: struct.pack_into("<H", bb, off + ch["offs"][0] + 1, 9000))
+    bad = _corrupt(b, lambda bb: struct.pack_into("<H", bb, off + ch["offs"][1], 9000))
     h = zf.zf_compressed_from_bytes(bad)
+    gpu.decode([h], out_specs(t, o), expect=zf.ZF_ECORRUPT)
+    zf.zf_compressed_free(h)
+    # an LZ77 length of four LEB128 bytes (at most three are allowed)
+    def four_byte_length(bb):
+        p = off + ch["offs"][0]
+        bb[p:p + 4] = bytes([0x80, 0x80, 0x80, 0x00])
+    h = zf.zf_compressed_from_bytes(_corrupt(b, four_byte_length))
     gpu.decode([h], out_specs(t, o), expect=zf.ZF_ECORRUPT)
     zf.zf_compressed_free(h)
     # the context stays usable after a reported error
