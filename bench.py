@@ -294,7 +294,7 @@ def run_batched(args, zf, torch):
     zf.zf_ctx_destroy(ctx)
 
 
-TEXT_WORKLOAD = ("non_parallel: 268,435,456-byte string column, Zipf(1.1) words from a 5,000-word vocabulary "
+TEXT_WORKLOAD = ("non_parallel: {:,}-byte string column, Zipf(1.1) words from a 5,000-word vocabulary "
                  "(3-12 letters), 1-8 words per row; LZ77 in 64 KiB blocks (one warp per block), int32 offsets "
                  "delta-packed in 65,536-row chunks")
 
@@ -302,7 +302,7 @@ TEXT_WORKLOAD = ("non_parallel: 268,435,456-byte string column, Zipf(1.1) words 
 def run_text(args, zf, torch):
     """The Non-Parallel workload: decode of a 256 MB LZ77 string column."""
     import zf_workloads as W
-    t, o = W.text_column(1, 1 << 28)
+    t, o = W.text_column(1, int(args.text_mb * (1 << 20)))
     col = zf.Column(t, o)
     h = zf.zf_compress_host(zf.zf_plan(None, col, scheme=zf.ZF_LZ77), col)
     raw, comp, nch = zf.zf_compressed_info(h)
@@ -338,7 +338,7 @@ def run_text(args, zf, torch):
     line = {"metric": METRIC, "value": round(raw / (td * 1e-3) / 1e9, 2), "unit": "GB/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(td, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8/int32", "data": "synthetic",
-            "config": {"workload": TEXT_WORKLOAD, "raw_bytes_per_step": raw, "comp_bytes_per_step": comp,
+            "config": {"workload": TEXT_WORKLOAD.format(t.nbytes), "raw_bytes_per_step": raw, "comp_bytes_per_step": comp,
                        "compression_ratio": round(raw / comp, 3), "blocks": nch,
                        "l2": "flushed (256 MiB write) before every resident step"},
             "e2e": {"value": round(raw / (te * 1e-3) / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": comp,
@@ -526,6 +526,7 @@ def main():
     ap.add_argument("--workload", choices=["group_parallel", "batched", "selector", "text"], default="group_parallel",
                     help="group_parallel: the benchmark line; batched: the 40 GB fact table; "
                          "selector: train and evaluate the learned selector")
+    ap.add_argument("--text-mb", type=float, default=256, help="string column size (text workload), MiB")
     ap.add_argument("--sel-train", type=int, default=2000)
     ap.add_argument("--sel-test", type=int, default=200)
     ap.add_argument("--sel-cap", type=int, default=2_000_000, help="row cap for label collection")

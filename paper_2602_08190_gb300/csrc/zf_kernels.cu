@@ -142,18 +142,25 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) tiles_kernel(LaunchAr
 //   Positions: two warp scans of the lengths give every token of the batch
 //   its literal range in s2 and its output range, so the whole batch is
 //   validated before a byte moves.
-//   Literals: the batch's literal bytes are contiguous in s2; the lanes copy
-//   them 32 at a time, each finding its token by a binary search over the
-//   lanes' literal starts.
-//   Matches: rounds.  Every output byte before the first unfinished match is
-//   final, so every match whose source ends there is ready; the ready matches'
-//   bytes are copied as one flat list (all loads of a group issued before its
-//   stores), and the round repeats until the batch is done.  The first
-//   unfinished match is always ready, so there are at most 32 rounds.  A match
-//   of offset `off` reads out[p - off + (k mod off)] for its k-th byte, which
-//   lies before p: a match that overlaps its own output repeats its source.
+//   Window (a batch whose output fits kLzWin): the batch is assembled in a
+//   shared-memory window placed at the output's alignment mod 16, then written
+//   out with 16-byte stores.  Literals: the batch's literal bytes are
+//   contiguous in s2; the lanes copy them 32 at a time, each finding its token
+//   by a binary search over the lanes' literal starts.  Matches: byte k of a
+//   match at p with offset `off` equals out[p + k - off].  Every lane first
+//   copies, from global memory, the bytes of its match whose source precedes
+//   the batch (final already); then the matches whose sources reach into the
+//   batch are finished in token order inside the window: the bytes k < off
+//   from before p, then the bytes k >= off as out[p + (k mod off)], so a match
+//   that overlaps its own output repeats its source.
+//   Direct (any other batch): output goes straight to global memory in
+//   rounds.  Every output byte before the first unfinished match is final, so
+//   every match whose source ends there is ready; the ready matches' bytes are
+//   copied as one flat list (all loads of a group issued before its stores),
+//   and the round repeats.  The first unfinished match is always ready.
 constexpr uint32_t kLzLenRing = 512;   // pre-parsed lengths per warp
 constexpr uint32_t kLzBatch = 480;     // lengths parsed ahead per refill (at most ring - 32)
+constexpr uint32_t kLzWin = 4096;      // batch output window per warp
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 
 struct LzParse {
@@ -237,7 +244,7 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
-__device__ void lz_block(const ZfDevChunk& c, uint32_t* lr, uint32_t* err) {
+__device__ void lz_block(const ZfDevChunk& c, uint32_t* lr, uint8_t* win, uint32_t* err) {
     const uint32_t lane = threadIdx.x & 31;
     zfd::Hdr h;
     zfd::load_hdr(c.blob, h);
@@ -293,8 +300,66 @@ __device__ void lz_block(const ZfDevChunk& c, uint32_t* lr, uint32_t* err) {
         // lengths are below 2^21, so none of the sums wrap
         const bool bad = lend > l2 || oend > rows || (has_m && (off == 0 || off > mpos));
         if (__any_sync(kFull, bad)) { ok = false; break; }
-        // literals
         const uint32_t lb = __shfl_sync(kFull, lend, 31) - lp;
+        const uint32_t src = mpos - off;
+        const uint32_t ob = __shfl_sync(kFull, oend, 31) - op;
+        if (ob + 16 <= kLzWin) {
+            // window byte x holds output byte op + x - a; base + x is its global address
+            const uint32_t a = (uint32_t)(reinterpret_cast<uintptr_t>(dst + op) & 15);
+            uint8_t* base = dst + op - a;
+            for (uint32_t bl = 0; bl < lb; bl += 128) {
+                uint32_t v[4];
+#pragma unroll
+                for (uint32_t q = 0; q < 4; q++) {
+                    const uint32_t jj = bl + 32 * q + lane;
+                    v[q] = jj < lb ? __ldg(lit + lp + jj) : 0;
+                }
+#pragma unroll
+                for (uint32_t q = 0; q < 4; q++) {
+                    if (bl + 32 * q >= lb) break;
+                    const uint32_t j = lp + bl + 32 * q + lane;
+                    const uint32_t i = lz_find(lstart, j);
+                    const uint32_t os = __shfl_sync(kFull, ostart, i), ls = __shfl_sync(kFull, lstart, i);
+                    if (j < lp + lb) win[a + os - op + (j - ls)] = (uint8_t)v[q];
+                }
+            }
+            // the bytes of each match whose source precedes the batch
+            const uint32_t d = a + mpos - op;
+            const uint32_t g = (has_m && src < op) ? min(min(ml, off), op - src) : 0;
+#pragma unroll 4
+            for (uint32_t k = 0; k < g; k++) win[d + k] = dst[src + k];
+            __syncwarp();
+            // the rest, in token order, inside the window
+            uint32_t todo = __ballot_sync(kFull, has_m && g < ml);
+            while (todo) {
+                const uint32_t i = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const uint32_t di = __shfl_sync(kFull, d, i), mi = __shfl_sync(kFull, ml, i);
+                const uint32_t oi = __shfl_sync(kFull, off, i), gi = __shfl_sync(kFull, g, i);
+                const uint32_t c1 = min(mi, oi);
+                for (uint32_t k = gi + lane; k < c1; k += 32) win[di + k] = win[di + k - oi];
+                __syncwarp();
+                if (oi < mi) {
+                    for (uint32_t k = oi + lane; k < mi; k += 32) win[di + k] = win[di + k % oi];
+                    __syncwarp();
+                }
+            }
+            // write the window out: head bytes, 16-byte words, tail bytes
+            const uint32_t e = a + ob, x0 = (a + 15) & ~15u, x1 = e & ~15u;
+            if (x0 <= x1) {
+                if (lane < x0 - a) base[a + lane] = win[a + lane];
+                for (uint32_t w = (x0 >> 4) + lane; w < (x1 >> 4); w += 32)
+                    reinterpret_cast<uint4*>(base)[w] = reinterpret_cast<const uint4*>(win)[w];
+                if (lane < e - x1) base[x1 + lane] = win[x1 + lane];
+            } else {
+                if (lane < ob) base[a + lane] = win[a + lane];
+            }
+            __syncwarp();
+            lp = __shfl_sync(kFull, lend, 31);
+            op = __shfl_sync(kFull, oend, 31);
+            continue;
+        }
+        // direct: literals
         for (uint32_t base = 0; base < lb; base += 128) {
             uint32_t v[4];
 #pragma unroll
@@ -313,7 +378,6 @@ __device__ void lz_block(const ZfDevChunk& c, uint32_t* lr, uint32_t* err) {
         }
         __syncwarp();
         // matches, in rounds
-        const uint32_t src = mpos - off;
         uint32_t pend = __ballot_sync(kFull, has_m);
         while (pend) {
             const uint32_t hwm = __shfl_sync(kFull, mpos, __ffs(pend) - 1);
@@ -353,11 +417,12 @@ __device__ void lz_block(const ZfDevChunk& c, uint32_t* lr, uint32_t* err) {
     if (!ok && lane == 0) zfd::report(err, ZF_ECORRUPT, c.chunk_id);
 }
 
-__global__ void __launch_bounds__(32) lz_kernel(const ZfDevChunk* chunks, uint32_t n, uint32_t* err) {
+__global__ void __launch_bounds__(32, 32) lz_kernel(const ZfDevChunk* chunks, uint32_t n, uint32_t* err) {
     __shared__ uint32_t lens[kLzLenRing];
+    __shared__ __align__(16) uint8_t win[kLzWin];
     for (uint32_t k = blockIdx.x; k < n; k += gridDim.x) {
         const ZfDevChunk c = chunks[k];
-        lz_block(c, lens, err);
+        lz_block(c, lens, win, err);
         __syncwarp();
     }
 }
