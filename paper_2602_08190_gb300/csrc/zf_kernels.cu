@@ -211,18 +211,18 @@ __device__ __forceinline__ void lz_parse_step(uint32_t byte, uint32_t l0, uint32
 }
 
 // Parse lengths until `upto` are available (or the stream ends); the bytes of
-// four steps are loaded before the first is used.
+// eight steps are loaded before the first is used.
 __device__ __forceinline__ void lz_parse(const uint8_t* s0, uint32_t l0, uint32_t* lr, LzParse& ps, uint32_t upto,
                                          uint32_t lane) {
     while (!ps.bad && ps.parsed < upto && ps.vp < l0) {
-        uint32_t by[4];
+        uint32_t by[8];
 #pragma unroll
-        for (uint32_t q = 0; q < 4; q++) {
+        for (uint32_t q = 0; q < 8; q++) {
             const uint32_t pos = ps.vp + 32 * q + lane;
             by[q] = pos < l0 ? __ldg(s0 + pos) : 0x80u;
         }
 #pragma unroll
-        for (uint32_t q = 0; q < 4; q++) {
+        for (uint32_t q = 0; q < 8; q++) {
             if (ps.bad || ps.parsed >= upto || ps.vp >= l0) break;
             lz_parse_step(by[q], l0, lr, ps, lane);
         }
@@ -276,6 +276,7 @@ __device__ void lz_block(const ZfDevChunk& c, uint32_t* lr, uint8_t* win, uint32
     for (uint32_t i = 128 * lane; i < l2; i += 4096) prefetch_l2(lit + i);
     LzParse ps;
     uint32_t lp = 0, op = 0;                                 // literal and output bytes done
+    uint32_t off_next = lane + 1 < T ? __ldg(offs + lane) : 0;  // offsets are loaded one batch ahead
     for (uint32_t t0 = 0; t0 < T; t0 += 32) {
         const uint32_t nt = min(32u, T - t0);
         const uint32_t need = min(nlen, 2 * (t0 + nt));      // the last token has no match length
@@ -287,7 +288,8 @@ __device__ void lz_block(const ZfDevChunk& c, uint32_t* lr, uint8_t* win, uint32
         const bool has_m = lane < nt && t + 1 < T;
         const uint32_t ll = lane < nt ? lr[(2 * t) & (kLzLenRing - 1)] : 0;
         const uint32_t ml = has_m ? lr[(2 * t + 1) & (kLzLenRing - 1)] + zf::kLzMinMatch : 0;
-        const uint32_t off = has_m ? __ldg(offs + t) : 0;
+        const uint32_t off = has_m ? off_next : 0;
+        off_next = t + 33 < T ? __ldg(offs + t + 32) : 0;
         uint32_t lend = ll, oend = ll + ml;                  // inclusive sums over the lanes
 #pragma unroll
         for (uint32_t d = 1; d < 32; d <<= 1) {
@@ -326,8 +328,25 @@ __device__ void lz_block(const ZfDevChunk& c, uint32_t* lr, uint8_t* win, uint32
             // the bytes of each match whose source precedes the batch
             const uint32_t d = a + mpos - op;
             const uint32_t g = (has_m && src < op) ? min(min(ml, off), op - src) : 0;
-#pragma unroll 4
-            for (uint32_t k = 0; k < g; k++) win[d + k] = dst[src + k];
+            if (g) {
+                // aligned words over [src, src + g): the last ends before op + 3,
+                // inside the block, because this match still has ml >= 4 bytes
+                // from mpos >= op
+                const uint32_t sh = src & 3u, nw = (sh + g + 3) >> 2;
+                const uint32_t* ws = reinterpret_cast<const uint32_t*>(dst + (src - sh));
+                for (uint32_t w0 = 0; w0 < nw; w0 += 4) {
+                    uint32_t x[4];
+#pragma unroll
+                    for (uint32_t q = 0; q < 4; q++) x[q] = w0 + q < nw ? ws[w0 + q] : 0;
+#pragma unroll
+                    for (uint32_t q = 0; q < 4; q++)
+#pragma unroll
+                        for (uint32_t b = 0; b < 4; b++) {
+                            const uint32_t kb = 4 * (w0 + q) + b;
+                            if (kb >= sh && kb < sh + g) win[d + kb - sh] = (uint8_t)(x[q] >> (8 * b));
+                        }
+                }
+            }
             __syncwarp();
             // the rest, in token order, inside the window
             uint32_t todo = __ballot_sync(kFull, has_m && g < ml);
