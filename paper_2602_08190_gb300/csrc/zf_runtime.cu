@@ -5,10 +5,13 @@
 // stages of about kcfg.stage_bytes compressed bytes.  Stage s is copied by
 // cudaMemcpyAsync on the copy stream into staging slot s % nslots, after the
 // decode of the stage that last used the slot has finished (event
-// slot_free); the compute stream waits for the copy (event slot_copied) and
-// decodes the stage into the caller's buffers.  Copies of stage s+1.. run
-// while stage s decodes.  All descriptors of a call are built on the host and
-// copied once, ahead of the first stage.
+// slot_free); decode stream s % nslots waits for the copy (event
+// slot_copied) and decodes the stage into the caller's buffers.  Copies of
+// stage s+1.. run while stage s decodes, and the decodes of different stages
+// may run at once (stages are independent): a launch too small to fill the
+// GPU -- an LZ77 stage has one warp per 64 KiB block -- overlaps the next.
+// The compute stream joins every decode stream at the end.  All descriptors
+// of a call are built on the host and copied once, ahead of the first stage.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -39,6 +42,7 @@ struct zf_ctx {
     int device = 0;
     int num_sms = 0;
     cudaStream_t copy = nullptr, compute = nullptr;
+    cudaStream_t lane[kMaxSlots] = {};  // decode stream of each staging slot
     bool own_copy = false, own_compute = false;
     uint32_t nslots = 3;
     uint64_t slot_req = 0;
@@ -46,7 +50,7 @@ struct zf_ctx {
     uint64_t slot_cap = 0;
     cudaEvent_t ev_copied[kMaxSlots] = {}, ev_free[kMaxSlots] = {};
     cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;
-    uint32_t* d_err = nullptr;     // [0] status bits, [1] first failing chunk, [2..3] work queue
+    uint32_t* d_err = nullptr;     // [0] status bits, [1] first failing chunk, [2 + 2s, 3 + 2s] work queue of stream s
     uint32_t* h_err = nullptr;     // pinned copy of d_err[0..1]
     ZfDevChunk* d_desc = nullptr;
     ZfDevChunk* h_desc = nullptr;  // pinned
@@ -236,17 +240,18 @@ void build_groups(const std::vector<Work>& w, size_t b, size_t e, const zf_kcfg&
     }
 }
 
-zf_status launch_groups(zf_ctx* ctx, const std::vector<Group>& groups, const ZfDevChunk* d_desc, const zf_kcfg& k) {
+zf_status launch_groups(zf_ctx* ctx, const std::vector<Group>& groups, const ZfDevChunk* d_desc, const zf_kcfg& k,
+                        cudaStream_t stream, uint32_t* queue) {
     for (const Group& g : groups) {
         const ZfDevChunk* dchunks = d_desc + g.first;
         cudaError_t e;
         if (g.scheme == ZF_LZ77) {
-            e = zf::launch_lz(dchunks, g.count, ctx->d_err, ctx->num_sms, ctx->compute);
+            e = zf::launch_lz(dchunks, g.count, ctx->d_err, ctx->num_sms, stream);
         } else {
             uint32_t smem = ((g.warp_smem + 15) & ~15u) * (k.threads / 32);
             zf::TileLaunch L{dchunks, g.count, g.ntiles, g.scheme, g.dtype, k.tile_rows, k.threads,
-                             k.ctas_per_sm, smem, ctx->num_sms, ctx->d_err, ctx->d_err + 2};
-            e = zf::launch_tiles(L, ctx->compute);
+                             k.ctas_per_sm, smem, ctx->num_sms, ctx->d_err, queue};
+            e = zf::launch_tiles(L, stream);
         }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "decode launch");
         ctx->st.n_launches++;
@@ -301,13 +306,14 @@ zf_status zf_ctx_create(int device, void* copy_stream, void* compute_stream, zf_
     else return fail(ZF_ECUDA);
     for (uint32_t s = 0; s < kMaxSlots; s++)
         if (cudaEventCreateWithFlags(&ctx->ev_copied[s], cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&ctx->ev_free[s], cudaEventDisableTiming) != cudaSuccess)
+            cudaEventCreateWithFlags(&ctx->ev_free[s], cudaEventDisableTiming) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&ctx->lane[s], cudaStreamNonBlocking) != cudaSuccess)
             return fail(ZF_ECUDA);
     if (cudaEventCreate(&ctx->ev_t0) != cudaSuccess || cudaEventCreate(&ctx->ev_t1) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess)
         return fail(ZF_ECUDA);
-    if (cudaMalloc(&ctx->d_err, 64) != cudaSuccess || cudaMemset(ctx->d_err, 0, 64) != cudaSuccess)
+    if (cudaMalloc(&ctx->d_err, 128) != cudaSuccess || cudaMemset(ctx->d_err, 0, 128) != cudaSuccess)
         return fail(ZF_ENOMEM);
     uint32_t init[2] = {0, 0xFFFFFFFFu};
     if (cudaMemcpy(ctx->d_err, init, 8, cudaMemcpyHostToDevice) != cudaSuccess) return fail(ZF_ECUDA);
@@ -322,7 +328,10 @@ zf_status zf_ctx_destroy(zf_ctx* ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->compute) cudaStreamSynchronize(ctx->compute);
     if (ctx->copy) cudaStreamSynchronize(ctx->copy);
+    for (uint32_t s = 0; s < kMaxSlots; s++)
+        if (ctx->lane[s]) cudaStreamSynchronize(ctx->lane[s]);
     for (uint32_t s = 0; s < kMaxSlots; s++) {
+        if (ctx->lane[s]) cudaStreamDestroy(ctx->lane[s]);
         if (ctx->slots[s]) cudaFree(ctx->slots[s]);
         if (ctx->ev_copied[s]) cudaEventDestroy(ctx->ev_copied[s]);
         if (ctx->ev_free[s]) cudaEventDestroy(ctx->ev_free[s]);
@@ -566,6 +575,7 @@ zf_status zf_transfer_decompress(zf_ctx* ctx, const zf_compressed* const* cols, 
         }
         cudaStreamSynchronize(ctx->copy);
         cudaStreamSynchronize(ctx->compute);
+        for (uint32_t q = 0; q < ctx->nslots; q++) cudaStreamSynchronize(ctx->lane[q]);
         return s2;
     };
 #define ZF_CAP(call)                                                          \
@@ -585,11 +595,13 @@ zf_status zf_transfer_decompress(zf_ctx* ctx, const zf_compressed* const* cols, 
         for (const Piece& p : pieces[s])
             ZF_CAP(cudaMemcpyAsync(ctx->slots[slot] + p.slot_off, p.src, p.bytes, cudaMemcpyHostToDevice, ctx->copy));
         ZF_CAP(cudaEventRecord(ctx->ev_copied[slot], ctx->copy));
-        ZF_CAP(cudaStreamWaitEvent(ctx->compute, ctx->ev_copied[slot], 0));
-        st = launch_groups(ctx, groups[s], d_desc, k);
+        ZF_CAP(cudaStreamWaitEvent(ctx->lane[slot], ctx->ev_copied[slot], 0));
+        st = launch_groups(ctx, groups[s], d_desc, k, ctx->lane[slot], ctx->d_err + 2 + 2 * slot);
         if (st) return abort_capture(st);
-        ZF_CAP(cudaEventRecord(ctx->ev_free[slot], ctx->compute));
+        ZF_CAP(cudaEventRecord(ctx->ev_free[slot], ctx->lane[slot]));
     }
+    for (size_t q = 0; q < std::min<size_t>(ctx->nslots, stages.size()); q++)
+        ZF_CAP(cudaStreamWaitEvent(ctx->compute, ctx->ev_free[q], 0));
     ZF_CAP(cudaMemcpyAsync(ctx->h_err, ctx->d_err, 8, cudaMemcpyDeviceToHost, ctx->compute));
 #undef ZF_CAP
     ctx->st.raw_bytes = raw;
@@ -716,7 +728,7 @@ zf_status zf_decompress_resident(zf_ctx* ctx, const zf_resident* const* cols, ui
         }
         ctx->resident_cache = desc;
     }
-    st = launch_groups(ctx, groups, ctx->d_desc, k);
+    st = launch_groups(ctx, groups, ctx->d_desc, k, ctx->compute, ctx->d_err + 2);
     if (st) {
         cudaStreamSynchronize(ctx->compute);
         return st;
