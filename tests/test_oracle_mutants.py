@@ -42,6 +42,8 @@ MUTANTS = {
     "lz_min_match_3": ("ml += LZ_MIN_MATCH;", "ml += 3;"),
     "lz_varint_8bit_shift": ("ll |= (uint32_t)(byte & 0x7F) << sh;\n                sh += 7;",
                              "ll |= (uint32_t)(byte & 0x7F) << sh;\n                sh += 8;"),
+    "lz_varint_five_bytes": ("if (vp >= l0 || sh > 14) return ORC_ECORRUPT; /* at most 3 bytes */",
+                             "if (vp >= l0 || sh > 28) return ORC_ECORRUPT;"),
     "lz_no_raw_fallback": ("if ((uint64_t)nl + no + nlit >= m) {", "if (0) {"),
     "lz_offset_of_next_token": ("uint32_t off = get_u16(s1 + 2ull * t);", "uint32_t off = get_u16(s1 + 2ull * (t + 1 < n_aux - 1 ? t + 1 : t));"),
 }
