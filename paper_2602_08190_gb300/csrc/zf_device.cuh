@@ -362,69 +362,134 @@ __device__ __forceinline__ void delta_rows_pair(T* dst, const uint32_t* wsm, uin
     }
 }
 
+// Swizzle of the 16-byte chunks of a lane's 128-byte line in the transpose
+// buffer: x = 4a + c (a < 2, c < 4) -> 2c + a.  Eight consecutive lanes
+// writing chunk k land in eight different bank groups, and so do the eight
+// lanes of a read phase (two lane quads reading the even or the odd chunks of
+// owners 4 apart, whose swizzles differ in parity).
+__device__ __forceinline__ uint32_t xswz(uint32_t l) {
+    l &= 7;
+    return ((l & 3) << 1) | (l >> 2);
+}
+
+// Stores of lane-owned lines, four lanes per line: every lane has put its
+// 128-byte line (eight 16-byte chunks, swizzled) in `xb`; in step r the lanes
+// of quad q write the four 32-byte sectors of lane 4q + r's line, so each
+// 256-bit store instruction writes eight whole 128-byte lines instead of 32
+// single sectors of 32 lines (the L2 takes a quarter of the requests).
+// `line0` is lane 0's line; lane o's is line0 + o * lane_bytes.
+__device__ __forceinline__ void store_lines_x4(char* line0, uint32_t lane_bytes, const uint4* xb, uint32_t lane) {
+    const uint32_t q4 = lane & ~3u, i4 = lane & 3u;
+#pragma unroll
+    for (uint32_t r = 0; r < 4; r++) {
+        const uint32_t o = q4 + r, fo = xswz(o);
+        const uint4 a = xb[o * 8 + ((2 * i4) ^ fo)], c = xb[o * 8 + ((2 * i4 + 1) ^ fo)];
+        store32(line0 + o * lane_bytes + 32 * i4, ((unsigned long long)a.y << 32) | a.x,
+                ((unsigned long long)a.w << 32) | a.z, ((unsigned long long)c.y << 32) | c.x,
+                ((unsigned long long)c.w << 32) | c.z);
+    }
+}
+
 // One 1024-row block with each lane owning 32 consecutive values
 // [32*lane, 32*lane + 32): a single warp scan per block.  The lane's bits
 // start on a word boundary (32*lane*b bits = lane*b words), so every lane
 // walks the same bit positions and the refill of the two-word bit reader is
-// uniform across the warp.  The 32 differences are read once into registers
-// and summed in place; values leave in 32-byte stores (four int64 or eight
-// int32), each a whole L2 sector.  WIDE (b > 21): 64-bit sums and
-// funnel-shift extraction; otherwise 32-bit sums (32 * 1024 * (2^21 - 1) < 2^32).
+// uniform across the warp.  The lane's differences are read twice: once for
+// their sum (the warp scan needs it first), once to rebuild the values, so no
+// array of prefixes stays live in registers.  Full blocks at a 32-byte
+// aligned address leave through the transpose buffer `xb` (4 KiB per warp),
+// four lanes per 128-byte line (store_lines_x4); other blocks in 32-byte
+// stores (four int64 or eight int32), each a whole L2 sector.  WIDE
+// (b > 21): 64-bit sums and funnel-shift extraction; otherwise 32-bit sums
+// (32 * 1024 * (2^21 - 1) < 2^32).
 template <class T, bool WIDE, bool WS>
 __device__ __forceinline__ void delta_block_lanes(T* dst, const uint32_t* wsm, uint32_t mk, uint32_t b, uint64_t base,
-                                                  uint64_t min_d, uint32_t lane) {
+                                                  uint64_t min_d, uint32_t lane, uint4* xb) {
     using U = typename std::conditional<sizeof(T) == 8, unsigned long long, unsigned int>::type;
     using S = typename std::conditional<WIDE, unsigned long long, unsigned int>::type;
     constexpr int PER = 32 / sizeof(T);           // values per 32-byte store
     const uint32_t j0 = lane * 32;
     const uint32_t nv = mk > j0 ? min(32u, mk - j0) : 0u;   // valid values of this lane
-    // inclusive prefix of the lane's differences (u_0 of the block counts as 0)
-    S pre[32];
-    if constexpr (!WIDE) {
-        const uint32_t mask = (1u << b) - 1u;
-        uint32_t wi = lane * b;
-        uint32_t lo = wsm[wi], hi = wsm[wi + 1];
-        wi += 2;
-        uint32_t pos = 0;
-        uint32_t run = 0;
-#pragma unroll
-        for (int k = 0; k < 32; k++) {
-            const uint32_t u = __funnelshift_r(lo, hi, pos) & mask;
-            run += ((uint32_t)k < nv && (j0 + k) > 0) ? u : 0u;
-            pre[k] = run;
+    const uint32_t mask = WIDE ? 0u : (1u << b) - 1u;
+    // bit reader over the lane's differences (narrow: two words in registers)
+    uint32_t wi = 0, lo = 0, hi = 0, pos = 0;
+    auto start = [&]() {
+        if constexpr (!WIDE) {
+            wi = lane * b;
+            lo = wsm[wi];
+            hi = wsm[wi + 1];
+            wi += 2;
+            pos = 0;
+        }
+    };
+    // difference k of the lane (u_0 of the block and slots past the block count as 0)
+    auto diff = [&](uint32_t k, bool full) -> S {
+        S u;
+        if constexpr (!WIDE) {
+            u = __funnelshift_r(lo, hi, pos) & mask;
             pos += b;
             if (pos >= 32) {
                 lo = hi;
                 hi = wsm[wi++];
                 pos -= 32;
             }
+        } else {
+            u = (full || k < nv) ? (S)extract(wsm, (j0 + k) * b, b) : (S)0;
         }
-    } else {
-        // wide differences: the total first, the values re-read below
-        S run = 0;
-        for (uint32_t k = 0; k < nv; k++)
-            if (j0 + k > 0) run += (S)extract(wsm, (j0 + k) * b, b);
-        pre[31] = run;
-    }
-    const S total = pre[31];
+        if ((!full && k >= nv) || (k == 0 && lane == 0)) u = 0;
+        return u;
+    };
+    start();
+    S total = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < 32; k++) total += diff(k, false);
     const S excl = warp_incl_sum<S>(total, lane) - total;
     const U md = (U)min_d;
-    U t = (U)base + (U)j0 * md + (U)excl;        // x_j = t + (j - j0) * min_d + pre[j - j0]
+    // x_{j0+k} = base + (j0 + k) * min_d + (differences up to j0 + k): acc after
+    // step k, where each step adds min_d + u_k
+    U acc = (U)base + (U)j0 * md + (U)excl - md;
+    start();
     const bool al32 = WS && (reinterpret_cast<uintptr_t>(dst + j0) & 31) == 0;
-    S wrun = 0;
+    if constexpr (WS && !WIDE) {
+        if (al32 && mk == zf::kDeltaBlock) {   // warp-uniform: dst is the block's first row
+            constexpr uint32_t LANE_BYTES = 32 * sizeof(T), LINES = LANE_BYTES / 128;
+            const uint32_t f = xswz(lane);
+#pragma unroll
+            for (uint32_t h = 0; h < LINES; h++) {
+#pragma unroll
+                for (uint32_t k8 = 0; k8 < 8; k8++) {
+                    uint4 w;
+                    if constexpr (sizeof(T) == 8) {
+                        const uint32_t k = h * 16 + k8 * 2;
+                        acc += md + (U)diff(k, true);
+                        const U v0 = acc;
+                        acc += md + (U)diff(k + 1, true);
+                        w = make_uint4((uint32_t)v0, (uint32_t)(v0 >> 32), (uint32_t)acc, (uint32_t)(acc >> 32));
+                    } else {
+                        uint32_t a[4];
+#pragma unroll
+                        for (uint32_t e = 0; e < 4; e++) {
+                            acc += md + (U)diff(k8 * 4 + e, true);
+                            a[e] = (uint32_t)acc;
+                        }
+                        w = make_uint4(a[0], a[1], a[2], a[3]);
+                    }
+                    xb[lane * 8 + (k8 ^ f)] = w;
+                }
+                __syncwarp();
+                store_lines_x4(reinterpret_cast<char*>(dst) + h * 128, LANE_BYTES, xb, lane);
+                __syncwarp();
+            }
+            return;
+        }
+    }
 #pragma unroll
     for (int q = 0; q < 32 / PER; q++) {
         T v[PER];
 #pragma unroll
         for (int e = 0; e < PER; e++) {
-            const int k = q * PER + e;
-            if constexpr (WIDE) {
-                if ((uint32_t)k < nv && (j0 + k) > 0) wrun += (S)extract(wsm, (j0 + k) * b, b);
-                v[e] = (T)(t + (U)wrun);
-            } else {
-                v[e] = (T)(t + (U)pre[k]);
-            }
-            t += md;
+            acc += md + (U)diff(q * PER + e, false);
+            v[e] = (T)acc;
         }
         if ((uint32_t)(q * PER + PER) <= nv) {
             if (WS && al32) {
@@ -443,6 +508,16 @@ __device__ __forceinline__ void delta_block_lanes(T* dst, const uint32_t* wsm, u
             for (uint32_t e = 0; q * PER + e < nv; e++) dst[j0 + q * PER + e] = v[e];
         }
     }
+}
+
+// Blocks of more than 21 bits per difference are rare; out of line, they do
+// not add to the registers of the common path.  They keep 16-byte stores: in
+// an out-of-line function a 256-bit store from inline PTX wrote only part of
+// its data (seen on GB300; the same store inlined is exact).
+template <class T>
+__device__ __noinline__ void delta_block_wide(T* dst, const uint32_t* wsm, uint32_t mk, uint32_t b, uint64_t base,
+                                              uint64_t min_d, uint32_t lane) {
+    delta_block_lanes<T, true, false>(dst, wsm, mk, b, base, min_d, lane, nullptr);
 }
 
 // Blocks of rows [r0, r0 + nrows) (r0 a multiple of 1024, at most 32 blocks).
@@ -499,8 +574,9 @@ __device__ void delta_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32
             T* dst = reinterpret_cast<T*>(c.dst) + r0 + i * zf::kDeltaBlock;
             const bool al32 = (reinterpret_cast<uintptr_t>(dst) & 31) == 0;
             const uint32_t* buf = wsm + (i & 1) * sb;
-            if (b <= 21) delta_block_lanes<T, false, WS>(dst, buf, mk, b, base, md, lane);
-            else delta_block_lanes<T, true, WS>(dst, buf, mk, b, base, md, lane);
+            uint4* xb = reinterpret_cast<uint4*>(wsm + 2 * sb);
+            if (b <= 21) delta_block_lanes<T, false, WS>(dst, buf, mk, b, base, md, lane, xb);
+            else delta_block_wide<T>(dst, buf, mk, b, base, md, lane);
             (void)al32;
         }
         __syncwarp();
@@ -705,7 +781,8 @@ __device__ __forceinline__ void rle_warp(const ZfDevChunk& c, const Hdr& h, uint
 // the widest bit width of the chunks it decodes (two staging buffers).
 __host__ __device__ inline uint32_t warp_smem(int scheme, uint32_t value_bytes, uint32_t bmax) {
     switch (scheme) {
-    case ZF_FOR_BP: case ZF_DICT_BP: case ZF_DELTA_BP: return 2 * stage_bytes_for(bmax);
+    case ZF_FOR_BP: case ZF_DICT_BP: return 2 * stage_bytes_for(bmax);
+    case ZF_DELTA_BP: return 2 * stage_bytes_for(bmax) + 4096;   // + the store transpose buffer
     case ZF_RLE: return kWarpRows * 2 + 2 * rle_buf_bytes(value_bytes);
     }
     return 0;
