@@ -15,7 +15,8 @@ chunks (805,306,368 uncompressed bytes per step).
   roofline  the dominant kernel (delta decode of the keys) timed alone:
           algorithmic bytes (compressed read + plain written) per launch over
           its CUDA-event duration, against the measured HBM copy peak.
-  cpu_baseline  the CPU oracle decoding a bounded sample of the same chunks.
+  cpu_baseline  the CPU oracle decoding a bounded sample of the same chunks on
+          all host cores (threads over chunks), and on one thread.
 
 --impl reference times the CPU oracle alone on the same metric.
 With torchrun (--gpus N) every rank decodes its own replica (no collective on
@@ -146,29 +147,48 @@ def make_workload(seed: int, rows: int = N_ROWS):
     return keys, dates
 
 
-def oracle_sample(handles, dtypes, budget_s: float, min_chunks: int = 1):
-    """Decode chunks of each column with the CPU oracle, round-robin, until
-    `budget_s` seconds pass; returns (bytes, seconds, description)."""
+def oracle_sample(handles, dtypes, budget_s: float, threads: int = 1):
+    """Decode chunks of each column with the CPU oracle until `budget_s`
+    seconds pass, `threads` host threads taking the chunks round-robin (the
+    oracle's C decoder runs outside the GIL); returns (bytes, seconds,
+    description)."""
+    import concurrent.futures
     import oracle
     import paper_2602_08190_gb300 as zf
-    blobs = []
+    per_col = []
     for h, dt in zip(handles, dtypes):
         b = zf.zf_compressed_bytes(h)
-        info = oracle.column_info(b)
-        blobs.append((b, info["n_chunks"], dt))
-    done_bytes, done_chunks, t0 = 0, 0, time.perf_counter()
-    k = 0
-    while True:
-        for b, nch, dt in blobs:
-            off, ln, r0, rows = oracle.chunk_span(b, k % nch)
-            out = oracle.decode_chunk(b[off:off + ln], dt)
-            done_bytes += out.nbytes
-            done_chunks += 1
-        k += 1
-        if time.perf_counter() - t0 >= budget_s and k >= min_chunks:
-            break
+        nch = oracle.column_info(b)["n_chunks"]
+        blobs = []
+        for c in range(nch):
+            off, ln, r0, rows = oracle.chunk_span(b, c)
+            blobs.append((b[off:off + ln], dt))
+        per_col.append(blobs)
+    order = [col[k] for k in range(max(len(c) for c in per_col)) for col in per_col if k < len(col)]
+    t0 = time.perf_counter()
+
+    def worker(w):
+        nb = nc = 0
+        i = w
+        while True:
+            blob, dt = order[i % len(order)]
+            nb += oracle.decode_chunk(blob, dt).nbytes
+            nc += 1
+            i += threads
+            if time.perf_counter() - t0 >= budget_s:
+                return nb, nc
+
+    with concurrent.futures.ThreadPoolExecutor(threads) as ex:
+        res = list(ex.map(worker, range(threads)))
     dt_s = time.perf_counter() - t0
-    return done_bytes, dt_s, f"{done_chunks} chunks of 1M rows ({k} per column), single thread"
+    done_bytes = sum(r[0] for r in res)
+    done_chunks = sum(r[1] for r in res)
+    return done_bytes, dt_s, (f"{done_chunks} chunks of 1M rows taken round-robin over the columns, "
+                              f"{threads} host thread{'s' if threads > 1 else ''}")
+
+
+def host_threads() -> int:
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
 
 
 def run_reference(args, rank: int):
@@ -181,12 +201,13 @@ def run_reference(args, rank: int):
                              zf.Column(keys))
     hd = zf.zf_compress_host(zf.zf_plan(None, zf.Column(dates), scheme=zf.ZF_RLE, chunk_rows=CHUNK_ROWS),
                              zf.Column(dates))
+    nt = host_threads()
     for _ in range(args.warmup):
-        oracle_sample([hk, hd], [np.int64, np.int32], 0.0)
+        oracle_sample([hk, hd], [np.int64, np.int32], 0.0, nt)
     tot_b, tot_s = 0, 0.0
     desc = ""
     for _ in range(args.steps):
-        b, s, desc = oracle_sample([hk, hd], [np.int64, np.int32], args.ref_step_s)
+        b, s, desc = oracle_sample([hk, hd], [np.int64, np.int32], args.ref_step_s, nt)
         tot_b += b
         tot_s += s
     v = tot_b / tot_s / 1e9
@@ -195,16 +216,16 @@ def run_reference(args, rank: int):
             "scaling": "weak", "vs_baseline": None, "dtype": "int64/int32", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": WORKLOAD, "sample": desc},
-            "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": nt, "kind": "oracle", "sample": desc},
             "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     zf.zf_compressed_free(hk)
     zf.zf_compressed_free(hd)
     print(json.dumps(line), flush=True)
 
 
-# Schemes of the fact table's column kinds (the task's mix: FOR for small
-# integers and scaled decimals, delta for sorted keys, RLE for dates,
-# dictionary for the 25-value codes).
+# Schemes of the fact table's column kinds: FOR for small integers and
+# scaled decimals, delta for sorted keys, RLE for dates, dictionary for the
+# 25-value codes.
 FACT_SCHEMES = {"uniform_1_50": "for_bp", "lognormal_cents": "for_bp", "sorted_keys": "delta_bp",
                 "dates": "rle", "codes_25": "dict_bp"}
 FACT_ROWS = 400_000_000
@@ -245,7 +266,8 @@ def run_batched(args, zf, torch):
     stage = int((args.stage_mb or 64) * (1 << 20))
     zf.zf_ctx_set_kcfg(ctx, args.tile_rows, args.threads, args.ctas_per_sm, stage,
                        zf.ZF_KCFG_BATCHED | zf.ZF_KCFG_GRAPH)
-    zf.zf_ctx_set_ring(ctx, args.slots or 3)
+    if args.slots:
+        zf.zf_ctx_set_ring(ctx, args.slots)
     dev = [torch.empty(rows * np.dtype(dt).itemsize, dtype=torch.uint8, device="cuda")
            for _, dt, _ in W.FACT_COLUMNS]
     handles = [h for h, _, _, _ in pieces]
@@ -308,8 +330,9 @@ def run_text(args, zf, torch):
     raw, comp, nch = zf.zf_compressed_info(h)
     copy_s, comp_s = torch.cuda.Stream(), torch.cuda.Stream()
     ctx = zf.zf_ctx_create(0, copy_s.cuda_stream, comp_s.cuda_stream)
-    zf.zf_ctx_set_kcfg(ctx, args.tile_rows, args.threads, args.ctas_per_sm, int((args.stage_mb or 16) * (1 << 20)), 0)
-    zf.zf_ctx_set_ring(ctx, args.slots or 3)
+    zf.zf_ctx_set_kcfg(ctx, args.tile_rows, args.threads, args.ctas_per_sm, int(args.stage_mb * (1 << 20)), 0)
+    if args.slots:
+        zf.zf_ctx_set_ring(ctx, args.slots)
     ob = torch.empty(t.nbytes, dtype=torch.uint8, device="cuda")
     oo = torch.empty(o.nbytes, dtype=torch.uint8, device="cuda")
     outs, caps = [ob.data_ptr(), oo.data_ptr()], [t.nbytes, o.nbytes]
@@ -418,8 +441,6 @@ def run_selector(args, zf, torch):
     import zf_workloads as W
     n_train, n_test = args.sel_train, args.sel_test
     ctx = zf.zf_ctx_create(0)
-    zf.zf_ctx_set_kcfg(ctx, 0, 0, 0, 16 << 20, 0)
-    zf.zf_ctx_set_ring(ctx, 3)
     t0 = time.perf_counter()
     F, T, fam, dts = selector_dataset(zf, ctx, range(1, n_train + n_test + 1), args.sel_cap)
     collect_s = time.perf_counter() - t0
@@ -472,17 +493,23 @@ def run_selector(args, zf, torch):
 
 def run_profile(args, zf, torch):
     """Resident decode of one workload column, nothing else (ncu target)."""
-    keys, dates = make_workload(1, args.rows)
+    import zf_workloads as W
     ctx = zf.zf_ctx_create(0)
     if any((args.tile_rows, args.threads, args.ctas_per_sm)):
         zf.zf_ctx_set_kcfg(ctx, args.tile_rows, args.threads, args.ctas_per_sm, 0, 0)
     hs, outs, caps, bufs = [], [], [], []
-    for x, s, on in ((keys, zf.ZF_DELTA_BP, args.profile in ("keys", "both")),
-                     (dates, zf.ZF_RLE, args.profile in ("dates", "both"))):
-        if not on:
-            continue
+    if args.profile == "for":
+        # the Fully-Parallel column at scale: int32 uniform on [0, 4096) (the top
+        # 12 bits of the counter-based generator), FOR + 12-bit packing,
+        # 65,536-row chunks
+        cols = [(W.uniform_int(1, 0, 0, args.rows, 0, 4096).astype(np.int32), zf.ZF_FOR_BP, 65536)]
+    else:
+        keys, dates = make_workload(1, args.rows)
+        cols = [(x, s, CHUNK_ROWS) for x, s, on in ((keys, zf.ZF_DELTA_BP, args.profile in ("keys", "both")),
+                                                   (dates, zf.ZF_RLE, args.profile in ("dates", "both"))) if on]
+    for x, s, cr in cols:
         c = zf.Column(x)
-        h = zf.zf_compress_host(zf.zf_plan(ctx, c, scheme=s, chunk_rows=CHUNK_ROWS), c)
+        h = zf.zf_compress_host(zf.zf_plan(ctx, c, scheme=s, chunk_rows=cr), c)
         hs.append(h)
         b = torch.empty(x.nbytes, dtype=torch.uint8, device="cuda")
         bufs.append(b)
@@ -497,8 +524,11 @@ def run_profile(args, zf, torch):
             ms.append(stats.total_ms)
     raw = sum(caps)
     comp = sum(zf.zf_compressed_info(h)[1] for h in hs)
+    hbm, kind = peaks()
+    alg = (raw + comp) / np.median(ms) / 1e6
     print(json.dumps({"profile": args.profile, "rows": args.rows, "raw_bytes": raw, "comp_bytes": comp,
-                      "ms": round(float(np.median(ms)), 4), "gbs": round(raw / np.median(ms) / 1e6, 1)}))
+                      "ms": round(float(np.median(ms)), 4), "gbs": round(raw / np.median(ms) / 1e6, 1),
+                      "algorithmic_gbs": round(alg, 1), "frac_of_" + kind + "_hbm": round(alg / hbm, 4)}))
     for r in rs:
         zf.zf_resident_free(r)
     for h in hs:
@@ -520,7 +550,7 @@ def main():
     ap.add_argument("--slots", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--no-graph", action="store_true", help="enqueue transfers call by call (no CUDA graph)")
-    ap.add_argument("--profile", choices=["keys", "dates", "both"], default=None,
+    ap.add_argument("--profile", choices=["keys", "dates", "both", "for"], default=None,
                     help="only decode the resident column(s) --steps times (for ncu captures)")
     ap.add_argument("--rows", type=int, default=N_ROWS, help="rows per column (profile / batched runs)")
     ap.add_argument("--workload", choices=["group_parallel", "batched", "selector", "text"], default="group_parallel",
@@ -667,7 +697,9 @@ def main():
     if rank == 0:
         import oracle
         oracle.build()
-        cpu_b, cpu_s, cpu_desc = oracle_sample([hk, hd], [np.int64, np.int32], args.cpu_budget_s)
+        nt = host_threads()
+        cpu_b, cpu_s, cpu_desc = oracle_sample([hk, hd], [np.int64, np.int32], args.cpu_budget_s * 2 / 3, nt)
+        one_b, one_s, _ = oracle_sample([hk, hd], [np.int64, np.int32], args.cpu_budget_s / 3, 1)
         traffic = measured_traffic()
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -684,8 +716,8 @@ def main():
                          "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
                          "traffic": traffic, "algorithmic_bytes_per_launch": kern_bytes,
                          "launch_ms": round(t_kern, 4)},
-            "cpu_baseline": {"value": round(cpu_b / cpu_s / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": cpu_desc},
+            "cpu_baseline": {"value": round(cpu_b / cpu_s / 1e9, 4), "unit": "GB/s", "cores": nt, "kind": "oracle",
+                             "sample": cpu_desc, "single_thread_value": round(one_b / one_s / 1e9, 4)},
             "clocks": clk.summary(),
             "gpu_launches": launches,
         }

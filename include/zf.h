@@ -110,7 +110,7 @@ typedef struct {
     uint32_t tile_rows;       /* rows per warp job: a multiple of 1024, <= 16384 (default 4096) */
     uint32_t threads;         /* 128, 256 or 512 (default 128) */
     uint32_t ctas_per_sm;     /* batched launch: persistent grid = ctas_per_sm x SM count (0 = occupancy limit) */
-    uint32_t stage_bytes;     /* pipeline stage: compressed bytes per H2D copy + decode step (default 16 MiB) */
+    uint32_t stage_bytes;     /* pipeline stage: compressed bytes per H2D copy + decode step (default 64 MiB) */
     uint32_t flags;           /* ZF_KCFG_BATCHED: one work-queue launch per stage for all schemes
                                  (else one launch per (scheme, dtype) group);
                                  ZF_KCFG_GRAPH: capture repeated transfers in a CUDA graph */
@@ -159,7 +159,8 @@ zf_status zf_ctx_destroy(zf_ctx* ctx);
 const char* zf_last_error(const zf_ctx* ctx);
 /* Override the kernel geometry used when a plan does not carry one. */
 zf_status zf_ctx_set_kcfg(zf_ctx* ctx, const zf_kcfg* kcfg);
-/* Number of staging slots (2..8, default 3) and bytes per slot (0 = sized per call). */
+/* Number of staging slots (2..8, default 8) and bytes per slot (0 = sized per call).
+ * Each slot has its own decode stream, so up to `slots` stages decode at once. */
 zf_status zf_ctx_set_ring(zf_ctx* ctx, uint32_t slots, uint64_t slot_bytes);
 
 /* ---- planning and host compression (Section 3, offline path) ------------ */

@@ -46,7 +46,7 @@ struct zf_ctx {
     cudaStream_t copy = nullptr, compute = nullptr;
     cudaStream_t lane[kMaxSlots] = {};  // decode stream of each staging slot
     bool own_copy = false, own_compute = false;
-    uint32_t nslots = 3;
+    uint32_t nslots = 8;
     uint64_t slot_req = 0;
     uint8_t* slots[kMaxSlots] = {};
     uint64_t slot_cap = 0;
@@ -58,7 +58,7 @@ struct zf_ctx {
     ZfDevChunk* h_desc = nullptr;  // pinned
     size_t desc_cap = 0;
     std::vector<ZfDevChunk> resident_cache;   // descriptors last uploaded for resident decode
-    zf_kcfg kcfg{0, 128, 0, 16u << 20, 0};
+    zf_kcfg kcfg{0, 128, 0, 64u << 20, 0};
     uint64_t slots_gen = 0;        // bumped whenever the staging slots are reallocated
     // CUDA graph of the last transfer (ZF_KCFG_GRAPH) and what it was built for
     cudaGraph_t graph = nullptr;
@@ -97,7 +97,7 @@ zf_kcfg effective_kcfg(const zf_ctx* ctx) {
     zf_kcfg k = ctx->kcfg;
     if (!k.threads) k.threads = 128;
     if (!k.tile_rows) k.tile_rows = 4096;
-    if (!k.stage_bytes) k.stage_bytes = 16u << 20;
+    if (!k.stage_bytes) k.stage_bytes = 64u << 20;
     return k;
 }
 
@@ -406,7 +406,7 @@ zf_status zf_ctx_set_kcfg(zf_ctx* ctx, const zf_kcfg* k) {
     zf_kcfg n = *k;
     if (!n.threads) n.threads = 128;
     if (!n.tile_rows) n.tile_rows = 4096;
-    if (!n.stage_bytes) n.stage_bytes = 16u << 20;
+    if (!n.stage_bytes) n.stage_bytes = 64u << 20;
     if (!kcfg_valid(n)) {
         ctx->last_error = "invalid kernel geometry";
         return ZF_EINVAL;
@@ -913,7 +913,7 @@ extern "C" zf_status zf_plan(zf_ctx* ctx, const zf_column* col, const zf_plan_op
         if (ctx) ctx->last_error = "chunk_rows must be a multiple of 1024 and at most 2^30";
         return ZF_EINVAL;
     }
-    p.kcfg = ctx ? ctx->kcfg : zf_kcfg{0, 128, 0, 16u << 20, 0};
+    p.kcfg = ctx ? ctx->kcfg : zf_kcfg{0, 128, 0, 64u << 20, 0};
     if (o.scheme >= 0) {
         if (o.scheme >= ZF_NSCHEMES) return ZF_EINVAL;
         p.scheme = o.scheme;
@@ -996,7 +996,7 @@ extern "C" zf_status zf_tune(zf_ctx* ctx, const zf_compressed* const* cols, uint
                 k.tile_rows = tr;
                 k.threads = th;
                 k.flags = saved.flags & ~ZF_KCFG_GRAPH;
-                k.stage_bytes = transfer ? (kTuneStageMiB[si] << 20) : (saved.stage_bytes ? saved.stage_bytes : 16u << 20);
+                k.stage_bytes = transfer ? (kTuneStageMiB[si] << 20) : (saved.stage_bytes ? saved.stage_bytes : 64u << 20);
                 ctx->kcfg = k;
                 std::vector<float> ms;
                 for (uint32_t rep = 0; rep < reps + 1; rep++) {   // first run warms up
