@@ -189,7 +189,11 @@ zf_status zf_compressed_from_bytes(const uint8_t* data, uint64_t len, zf_compres
 
 /* Enqueue, for every column, the host-to-device copies of its chunks into
  * the staging ring (copy stream) and their decode into the caller's device
- * buffers (compute stream).  Asynchronous: returns once enqueued.  d_out has
+ * buffers (one decode stream per staging slot, joined into the compute
+ * stream at the end).  Asynchronous: returns once enqueued.  Only the
+ * context's streams are used: work of other streams on the output buffers
+ * must be finished (or ordered before the copy stream with an event) by the
+ * caller, and the outputs are complete once zf_sync returns.  d_out has
  * one device buffer per I32/I64 column and two per BYTES column (bytes,
  * then int32 offsets); d_out_bytes gives each buffer's capacity.  Returns
  * ZF_EBUSY if the previous call was not synced. */

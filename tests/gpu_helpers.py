@@ -44,6 +44,8 @@ class Gpu:
             nb = max(16, np.dtype(dt).itemsize * n)
             b = t.full((nb,), SENTINEL, dtype=t.uint8, device="cuda")
             bufs.append(b)
+        # the library runs on its own streams: the fills must be done first
+        t.cuda.synchronize()
         return bufs
 
     def decode(self, handles, specs, resident=False, expect=zf.ZF_OK):

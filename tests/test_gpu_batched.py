@@ -33,6 +33,7 @@ def test_fact_table_40gb_batched_graph():
         for rep in range(2):                       # capture, then replay
             for d in dev:
                 d.fill_(0x5A)
+            torch.cuda.synchronize()               # the library runs on its own streams
             zf.zf_transfer_decompress(ctx, handles, outs, caps)
             st, stats = zf.zf_sync(ctx)
             assert stats.raw_bytes == raw and stats.n_chunks == len(pieces)

@@ -35,6 +35,7 @@ def test_graph_replay(columns, flags):
         for rep in range(3):                      # capture once, then replay
             for b in bufs:
                 b.fill_(0x5A)
+            g.torch.cuda.synchronize()            # the library runs on its own streams
             zf.zf_transfer_decompress(g.ctx, hs, outs, caps)
             st, stats = zf.zf_sync(g.ctx)
             assert stats.n_stages > 2
@@ -68,6 +69,7 @@ def test_tune_visits_every_point_and_keeps_the_fastest(columns, transfer, npts):
         # the context now decodes with the chosen geometry, bit-exact
         for b in bufs:
             b.fill_(0)
+        g.torch.cuda.synchronize()
         zf.zf_transfer_decompress(g.ctx, hs, outs, caps)
         zf.zf_sync(g.ctx)
         for (x, s, cr), b in zip(cols, bufs):

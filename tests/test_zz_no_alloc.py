@@ -37,6 +37,7 @@ def test_noalloc_matches_transfer_decompress_twice():
                 stream = torch.cuda.Stream()
                 for call in range(2):                  # two calls in a row share the scratch array
                     out = torch.full((x.nbytes,), 0x5A, dtype=torch.uint8, device="cuda")
+                    torch.cuda.synchronize()           # the fill runs on another stream
                     st = zf.zf_decompress_device_noalloc(dcol.data_ptr(), dcol.numel(), out.data_ptr(),
                                                          out.numel(), stream.cuda_stream)
                     assert st == zf.ZF_OK, (scheme, call, st)
