@@ -107,7 +107,8 @@ typedef struct {
  * tiles of one chunk, staging the next tile while it decodes the current
  * one.  Zero fields take the built-in values. */
 typedef struct {
-    uint32_t tile_rows;       /* rows per warp job: a multiple of 1024, <= 16384 (default 4096) */
+    uint32_t tile_rows;       /* rows per warp job: a multiple of 1024, <= 16384 (0 = 2048 for
+                                 delta launches, 4096 for the others) */
     uint32_t threads;         /* 128, 256 or 512 (default 128) */
     uint32_t ctas_per_sm;     /* batched launch: persistent grid = ctas_per_sm x SM count (0 = occupancy limit) */
     uint32_t stage_bytes;     /* pipeline stage: compressed bytes per H2D copy + decode step (default 64 MiB) */

@@ -90,19 +90,23 @@ zf_status cuda_fail(zf_ctx* ctx, cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
     } while (0)
 
-// Zero fields take the built-in geometry: 128 threads, warp jobs of four
-// 1024-row tiles (the fastest or within 1% of it for delta and RLE columns of
-// 1M-row chunks in a full search on GB300).
+// Zero fields take the built-in geometry: 128 threads; warp jobs of two
+// 1024-row tiles for delta launches and four for the others (the fastest, or
+// within 1% of it, for delta and RLE columns of 1M-row chunks in a full
+// search on GB300).  tile_rows stays 0 here and is resolved per launch group.
 zf_kcfg effective_kcfg(const zf_ctx* ctx) {
     zf_kcfg k = ctx->kcfg;
     if (!k.threads) k.threads = 128;
-    if (!k.tile_rows) k.tile_rows = 4096;
     if (!k.stage_bytes) k.stage_bytes = 64u << 20;
     return k;
 }
 
+uint32_t group_tile_rows(const zf_kcfg& k, int scheme) {
+    return k.tile_rows ? k.tile_rows : (scheme == ZF_DELTA_BP ? 2048u : 4096u);
+}
+
 bool kcfg_valid(const zf_kcfg& k) {
-    return k.tile_rows % 1024 == 0 && k.tile_rows >= 1024 && k.tile_rows <= zf::kMaxTileRows &&
+    return (k.tile_rows == 0 || (k.tile_rows % 1024 == 0 && k.tile_rows >= 1024 && k.tile_rows <= zf::kMaxTileRows)) &&
            (k.threads == 128 || k.threads == 256 || k.threads == 512) && k.ctas_per_sm <= 64;
 }
 
@@ -198,6 +202,7 @@ struct Group {
     int scheme, dtype;   // (-1, -1): batched work-queue kernel; (LZ77, BYTES): LZ kernel
     uint32_t first, count, ntiles;
     uint32_t warp_smem;  // widest per-warp shared memory of the group's chunks
+    uint32_t tile_rows;  // rows of a warp job in this launch
 };
 
 // Append descriptors of works[b, e) to `desc`, grouped for launching.
@@ -216,7 +221,7 @@ void build_groups(const std::vector<Work>& w, size_t b, size_t e, const zf_kcfg&
         if (std::find(keys.begin(), keys.end(), std::make_pair(s, d)) == keys.end()) keys.push_back({s, d});
     }
     for (auto& key : keys) {
-        Group g{key.first, key.second, (uint32_t)desc.size(), 0, 0, 16};
+        Group g{key.first, key.second, (uint32_t)desc.size(), 0, 0, 16, group_tile_rows(k, key.first)};
         for (size_t i = b; i < e; i++) {
             int s = w[i].ch->scheme, d = w[i].ch->dtype;
             bool lz = s == ZF_LZ77;
@@ -228,7 +233,7 @@ void build_groups(const std::vector<Work>& w, size_t b, size_t e, const zf_kcfg&
             dc.dst_cap = w[i].cap;
             dc.rows = w[i].ch->rows;
             dc.tile0 = g.ntiles;
-            dc.ntiles = zf::tiles_of(*w[i].ch, k.tile_rows);
+            dc.ntiles = zf::tiles_of(*w[i].ch, g.tile_rows);
             dc.blob_bytes = (uint32_t)w[i].ch->bytes;
             dc.chunk_id = w[i].id;
             dc.scheme = (uint8_t)s;
@@ -252,7 +257,7 @@ zf_status launch_groups(zf_ctx* ctx, const std::vector<Group>& groups, const ZfD
             e = zf::launch_lz(dchunks, g.count, ctx->d_err, ctx->num_sms, stream);
         } else {
             uint32_t smem = ((g.warp_smem + 15) & ~15u) * (k.threads / 32);
-            zf::TileLaunch L{dchunks, g.count, g.ntiles, g.scheme, g.dtype, k.tile_rows, k.threads,
+            zf::TileLaunch L{dchunks, g.count, g.ntiles, g.scheme, g.dtype, g.tile_rows, k.threads,
                              k.ctas_per_sm, smem, ctx->num_sms, ctx->d_err, queue};
             e = zf::launch_tiles(L, stream);
         }
@@ -405,7 +410,6 @@ zf_status zf_ctx_set_kcfg(zf_ctx* ctx, const zf_kcfg* k) {
     if (!ctx || !k) return ZF_EINVAL;
     zf_kcfg n = *k;
     if (!n.threads) n.threads = 128;
-    if (!n.tile_rows) n.tile_rows = 4096;
     if (!n.stage_bytes) n.stage_bytes = 64u << 20;
     if (!kcfg_valid(n)) {
         ctx->last_error = "invalid kernel geometry";
