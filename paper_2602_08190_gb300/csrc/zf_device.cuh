@@ -586,18 +586,18 @@ __device__ void delta_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32
 // ---------------------------------------------------------------- RLE (Group-Parallel)
 // Expansion of one 1024-row tile whose runs [rf, rf+m) have their lengths at
 // `lens` and values at `vals` (staged in shared memory, or in global memory
-// when the tile has more runs than a staging buffer holds).  `mark` is the
-// warp's 1024 u16 row marks.
+// when the tile has more runs than a staging buffer holds).  `bm` is the
+// warp's 32-word bitmask of the tile's rows.
 template <class T, bool WS>
 __device__ __forceinline__ void rle_rows(const ZfDevChunk& c, const Hdr& h, T* dst, const uint32_t* lens,
-                                         const T* vals, uint16_t* mark, uint32_t m, uint32_t skip, uint32_t nr,
+                                         const T* vals, uint32_t* bm, uint32_t m, uint32_t skip, uint32_t nr,
                                          bool last_tile, uint32_t next_skip, uint32_t lane, uint32_t* err) {
-#pragma unroll
-    for (int q = 0; q < 4; q++) reinterpret_cast<uint4*>(mark)[lane + 32 * q] = make_uint4(0, 0, 0, 0);
+    bm[lane] = 0;
     __syncwarp();
-    // presum: start row of each run relative to the tile, 32 runs per step.
-    // Lengths are at most the chunk's rows (< 2^30), and only the first and
-    // last run of a tile can be longer than the tile, so 32-bit sums hold.
+    // presum: start row of each run relative to the tile, 32 runs per step;
+    // every run but the first sets the bit of its start row.  Lengths are at
+    // most the chunk's rows (< 2^30), and only the first and last run of a
+    // tile can be longer than the tile, so 32-bit sums hold.
     bool bad = false;
     uint32_t end = 0;                 // rows covered so far, counted from the first run's start
     uint32_t first_len = 0, last_start = 0;
@@ -607,7 +607,10 @@ __device__ __forceinline__ void rle_rows(const ZfDevChunk& c, const Hdr& h, T* d
         bad |= i < m && (L == 0 || L > h.rows);
         const uint32_t incl = warp_incl_sum<uint32_t>(L, lane);
         const uint32_t start = end + incl - L;   // relative to the first run's start
-        if (i < m && i > 0 && start >= skip && start - skip < nr) mark[start - skip] = (uint16_t)i;
+        if (i < m && i > 0 && start >= skip && start - skip < nr) {
+            const uint32_t r = start - skip;
+            atomicOr(&bm[r >> 5], 1u << (r & 31));
+        }
         if (g == 0) first_len = __shfl_sync(0xFFFFFFFFu, L, 0);
         const uint32_t ls = __shfl_sync(0xFFFFFFFFu, start, (m - 1 - g) & 31);
         if (m - 1 - g < 32) last_start = ls;
@@ -622,59 +625,41 @@ __device__ __forceinline__ void rle_rows(const ZfDevChunk& c, const Hdr& h, T* d
     const bool any_bad = __any_sync(0xFFFFFFFFu, bad);
     if (lane == 0 && (!ok || any_bad)) report(err, ZF_ECORRUPT, c.chunk_id);
     __syncwarp();
-    // Expansion, two rows of 128 per step: lane l takes rows 4l..4l+3 of each.
-    // A row's run index is the largest mark at or before it: a running max
-    // over the lane's four marks, then one shuffle max-scan over lanes for
-    // both rows at once (16-bit halves, __vmaxu2; run indices are <= 1025).
+    // A row's run (relative to the tile's first) is the number of run starts
+    // at or before it: lane l holds word l of the bitmask and the starts in
+    // the words before it (one shuffle scan of the popcounts).  Expansion, 128
+    // rows per step: lane l takes rows 4l..4l+3, which lie in one word.
+    const uint32_t word = bm[lane];
+    const uint32_t cnt = __popc(word);
+    const uint32_t before = warp_incl_sum<uint32_t>(cnt, lane) - cnt;
     constexpr int V = 4;
     const bool al32 = WS && (reinterpret_cast<uintptr_t>(dst) & 31) == 0;
-    uint32_t carry = 0;
-    for (uint32_t row = 0; row * 128 < nr; row += 2) {
-        const uint32_t ja = row * 128 + lane * V, jb = ja + 128;
-        const uint2 ma = reinterpret_cast<const uint2*>(mark)[ja / 4];
-        const uint2 mb = reinterpret_cast<const uint2*>(mark)[jb / 4];
-        uint32_t ra[V], rb[V];
-        ra[0] = ma.x & 0xFFFF;
-        ra[1] = max(ra[0], ma.x >> 16);
-        ra[2] = max(ra[1], ma.y & 0xFFFF);
-        ra[3] = max(ra[2], ma.y >> 16);
-        rb[0] = mb.x & 0xFFFF;
-        rb[1] = max(rb[0], mb.x >> 16);
-        rb[2] = max(rb[1], mb.y & 0xFFFF);
-        rb[3] = max(rb[2], mb.y >> 16);
-        uint32_t x = ra[3] | (rb[3] << 16);
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
-            if (lane >= (uint32_t)d) x = __vmaxu2(x, y);
-        }
-        const uint32_t tot = __shfl_sync(0xFFFFFFFFu, x, 31);
-        uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, x, 1);
-        if (lane == 0) prev = 0;
-        const uint32_t before_a = max(prev & 0xFFFFu, carry);
-        const uint32_t before_b = max(max(prev >> 16, carry), tot & 0xFFFFu);
-        T va[V], vb[V];
+    const uint32_t o = (lane & 7) * 4;
+    for (uint32_t row = 0; row * 128 < nr; row++) {
+        const uint32_t j = row * 128 + lane * V;
+        const uint32_t w = row * 4 + (lane >> 3);
+        const uint32_t ww = __shfl_sync(0xFFFFFFFFu, word, w);
+        uint32_t idx = __shfl_sync(0xFFFFFFFFu, before, w) + __popc(ww & ((1u << o) - 1u));
+        const uint32_t b4 = ww >> o;
+        T v[V];
 #pragma unroll
         for (int k = 0; k < V; k++) {
-            va[k] = vals[min(max(before_a, ra[k]), m - 1)];
-            vb[k] = vals[min(max(before_b, rb[k]), m - 1)];
+            idx += (b4 >> k) & 1u;
+            v[k] = vals[min(idx, m - 1)];
         }
-        if (ja + V <= nr) store_vec<T, V>(dst + ja, va, al32);
+        if (j + V <= nr) store_vec<T, V>(dst + j, v, al32);
         else
-            for (uint32_t k = 0; ja + k < nr; k++) dst[ja + k] = va[k];
-        if (jb + V <= nr) store_vec<T, V>(dst + jb, vb, al32);
-        else
-            for (uint32_t k = 0; jb + k < nr; k++) dst[jb + k] = vb[k];
-        carry = max(carry, max(tot & 0xFFFFu, tot >> 16));
+            for (uint32_t k = 0; j + k < nr; k++) dst[j + k] = v[k];
     }
     __syncwarp();
 }
 
 constexpr uint32_t kRleStageRuns = 256;   // runs per staging buffer
 
-// Shared memory of one RLE staging buffer: lengths then values.
+// Shared memory of one RLE staging buffer: lengths then values, each with
+// room for the 16-byte aligned copy that starts up to 3 entries early.
 __host__ __device__ inline uint32_t rle_buf_bytes(uint32_t value_bytes) {
-    return kRleStageRuns * 4 + ((kRleStageRuns * value_bytes + 15) & ~15u);
+    return (kRleStageRuns + 4) * 4 + (((kRleStageRuns + 4) * value_bytes + 15) & ~15u);
 }
 
 // Tiles of rows [r0, r0 + nrows) (r0 a multiple of 1024, at most 31 tiles).
@@ -693,9 +678,10 @@ __device__ void rle_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t
     const uint32_t tiles_in_chunk = (h.rows + zf::kRleDirRows - 1) / zf::kRleDirRows;
     uint2 d = make_uint2(0, 0);
     if (lane <= nt && t0 + lane < tiles_in_chunk) d = __ldg(dir + t0 + lane);
-    uint16_t* mark = reinterpret_cast<uint16_t*>(wsm);
-    uint8_t* bufs = reinterpret_cast<uint8_t*>(wsm) + zf::kRleDirRows * 2;
+    uint32_t* bm = wsm;
+    uint8_t* bufs = reinterpret_cast<uint8_t*>(wsm) + 128;
     const uint32_t bb = rle_buf_bytes(sizeof(T));
+    constexpr uint32_t VPER = 16 / sizeof(T);   // values per 16-byte copy
     // run range [rf, rf + m) of tile i, or m = 0 if its directory entries are inconsistent
     auto runs = [&](uint32_t i, uint32_t& rf, uint32_t& skip, uint32_t& m, uint32_t& next_skip, bool& last) {
         rf = __shfl_sync(0xFFFFFFFFu, d.x, i);
@@ -720,13 +706,15 @@ __device__ void rle_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t
         bool last;
         runs(i, rf, skip, m, ns, last);
         if (m && m <= kRleStageRuns) {
+            // 16-byte copies from the aligned entries at or before rf (the
+            // sections are 16-byte aligned and padded, so they stay inside)
             uint8_t* b = bufs + (i & 1) * bb;
-            uint32_t* ls = reinterpret_cast<uint32_t*>(b);
-            T* vs = reinterpret_cast<T*>(b + kRleStageRuns * 4);
-            for (uint32_t k = lane; k < m; k += 32) {
-                __pipeline_memcpy_async(ls + k, lens + rf + k, 4);
-                __pipeline_memcpy_async(vs + k, vals + rf + k, sizeof(T));
-            }
+            const uint32_t l0 = rf & ~3u, nl = (rf + m - l0 + 3) / 4;
+            const uint32_t v0 = rf & ~(VPER - 1), nv = (rf + m - v0 + VPER - 1) / VPER;
+            for (uint32_t k = lane; k < nl; k += 32)
+                __pipeline_memcpy_async(b + 16 * k, lens + l0 + 4 * k, 16);
+            for (uint32_t k = lane; k < nv; k += 32)
+                __pipeline_memcpy_async(b + (kRleStageRuns + 4) * 4 + 16 * k, vals + v0 + VPER * k, 16);
         }
         __pipeline_commit();
     };
@@ -749,10 +737,11 @@ __device__ void rle_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t
             T* dst = reinterpret_cast<T*>(c.dst) + rr;
             if (m <= kRleStageRuns) {
                 const uint8_t* b = bufs + (i & 1) * bb;
-                rle_rows<T, WS>(c, h, dst, reinterpret_cast<const uint32_t*>(b),
-                            reinterpret_cast<const T*>(b + kRleStageRuns * 4), mark, m, skip, nr, last, ns, lane, err);
+                rle_rows<T, WS>(c, h, dst, reinterpret_cast<const uint32_t*>(b) + (rf & 3u),
+                                reinterpret_cast<const T*>(b + (kRleStageRuns + 4) * 4) + (rf & (VPER - 1)), bm, m,
+                                skip, nr, last, ns, lane, err);
             } else {
-                rle_rows<T, WS>(c, h, dst, lens + rf, vals + rf, mark, m, skip, nr, last, ns, lane, err);
+                rle_rows<T, WS>(c, h, dst, lens + rf, vals + rf, bm, m, skip, nr, last, ns, lane, err);
             }
         }
         __syncwarp();
@@ -783,7 +772,7 @@ __host__ __device__ inline uint32_t warp_smem(int scheme, uint32_t value_bytes, 
     switch (scheme) {
     case ZF_FOR_BP: case ZF_DICT_BP: return 2 * stage_bytes_for(bmax);
     case ZF_DELTA_BP: return 2 * stage_bytes_for(bmax) + 4096;   // + the store transpose buffer
-    case ZF_RLE: return kWarpRows * 2 + 2 * rle_buf_bytes(value_bytes);
+    case ZF_RLE: return 128 + 2 * rle_buf_bytes(value_bytes);   // row bitmask + two staging buffers
     }
     return 0;
 }
