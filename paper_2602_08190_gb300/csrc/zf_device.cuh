@@ -627,29 +627,39 @@ __device__ __forceinline__ void rle_rows(const ZfDevChunk& c, const Hdr& h, T* d
     __syncwarp();
     // A row's run (relative to the tile's first) is the number of run starts
     // at or before it: lane l holds word l of the bitmask and the starts in
-    // the words before it (one shuffle scan of the popcounts).  Expansion, 128
-    // rows per step: lane l takes rows 4l..4l+3, which lie in one word.
+    // the words before it (one shuffle scan of the popcounts).  Expansion, 256
+    // rows per step: lane l takes rows 8l..8l+7, a quarter of one word.  Each
+    // run sets at most one bit and the first sets none, so a count never
+    // passes m - 1.
     const uint32_t word = bm[lane];
     const uint32_t cnt = __popc(word);
     const uint32_t before = warp_incl_sum<uint32_t>(cnt, lane) - cnt;
-    constexpr int V = 4;
+    constexpr int V = 8;
     const bool al32 = WS && (reinterpret_cast<uintptr_t>(dst) & 31) == 0;
-    const uint32_t o = (lane & 7) * 4;
-    for (uint32_t row = 0; row * 128 < nr; row++) {
-        const uint32_t j = row * 128 + lane * V;
-        const uint32_t w = row * 4 + (lane >> 3);
+    const uint32_t o = (lane & 3) * 8;
+    for (uint32_t row = 0; row * 256 < nr; row++) {
+        const uint32_t j = row * 256 + lane * V;
+        const uint32_t w = row * 8 + (lane >> 2);
         const uint32_t ww = __shfl_sync(0xFFFFFFFFu, word, w);
         uint32_t idx = __shfl_sync(0xFFFFFFFFu, before, w) + __popc(ww & ((1u << o) - 1u));
-        const uint32_t b4 = ww >> o;
+        const uint32_t b8 = ww >> o;
         T v[V];
 #pragma unroll
         for (int k = 0; k < V; k++) {
-            idx += (b4 >> k) & 1u;
-            v[k] = vals[min(idx, m - 1)];
+            idx += (b8 >> k) & 1u;
+            v[k] = vals[idx];
         }
-        if (j + V <= nr) store_vec<T, V>(dst + j, v, al32);
-        else
+        if (j + V <= nr) {
+            if constexpr (sizeof(T) == 4) {
+                store_vec<T, V>(dst + j, v, al32);
+            } else {
+                const T a[4] = {v[0], v[1], v[2], v[3]}, z[4] = {v[4], v[5], v[6], v[7]};
+                store_vec<T, 4>(dst + j, a, al32);
+                store_vec<T, 4>(dst + j + 4, z, al32);
+            }
+        } else {
             for (uint32_t k = 0; j + k < nr; k++) dst[j + k] = v[k];
+        }
     }
     __syncwarp();
 }
