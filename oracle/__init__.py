@@ -20,19 +20,21 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-RAW, FOR_BP, DICT_BP, DELTA_BP, RLE, LZ77 = range(6)
-I32, I64, BYTES = range(3)
+RAW, FOR_BP, DICT_BP, DELTA_BP, RLE, LZ77, FLOAT2INT = range(7)
+I32, I64, BYTES, F64 = range(4)
 OK, EINVAL, ENOMEM, ECUDA, ECORRUPT = 0, 1, 2, 3, 4
-SCHEMES = {"raw": RAW, "for_bp": FOR_BP, "dict_bp": DICT_BP, "delta_bp": DELTA_BP, "rle": RLE, "lz77": LZ77}
-_DT = {np.dtype(np.int32): I32, np.dtype(np.int64): I64, np.dtype(np.uint8): BYTES}
-_NP = {I32: np.int32, I64: np.int64, BYTES: np.uint8}
+SCHEMES = {"raw": RAW, "for_bp": FOR_BP, "dict_bp": DICT_BP, "delta_bp": DELTA_BP, "rle": RLE, "lz77": LZ77,
+           "float2int": FLOAT2INT}
+_DT = {np.dtype(np.int32): I32, np.dtype(np.int64): I64, np.dtype(np.uint8): BYTES, np.dtype(np.float64): F64}
+_NP = {I32: np.int32, I64: np.int64, BYTES: np.uint8, F64: np.float64}
 
 
 def build(force: bool = False, src: str = _SRC, out: str = _LIB) -> str:
     """Compile the oracle's C file into a shared library (default: next to it)."""
     if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
         tmp = out + f".{os.getpid()}.tmp"
-        subprocess.run(["gcc", "-O1", "-std=c11", "-Wall", "-shared", "-fPIC", "-o", tmp, src], check=True)
+        subprocess.run(["gcc", "-O1", "-std=c11", "-Wall", "-ffp-contract=off", "-shared", "-fPIC", "-o", tmp, src, "-lm"],
+                       check=True)
         os.replace(tmp, out)
     return out
 

@@ -12,6 +12,7 @@
  *   Delta encoding                     Section 2.1 ("Delta encoding")
  *   Run-length encoding, presum        Section 2.1 ("RLE"); Section 3.2
  *   LZ77 back-references               Section 2.1 (LZ77-based algorithms)
+ *   Float2Int (+ bit-packing)          Section 2.1 ("Float2Int"); Table 2
  *   Independent chunks                 Section 3.1 (Non-Parallel "file chunking")
  *
  * Decoders are the definitions written out: values are read bit by bit,
@@ -27,6 +28,7 @@
  *             zero padding, blob length a multiple of 16
  * The layout constants below are typed in from that description.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -34,8 +36,8 @@
 /* ---- status codes (values of the library's zf_status) ---- */
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_ECORRUPT = 4 };
 /* ---- schemes and dtypes ---- */
-enum { ORC_RAW = 0, ORC_FOR_BP = 1, ORC_DICT_BP = 2, ORC_DELTA_BP = 3, ORC_RLE = 4, ORC_LZ77 = 5 };
-enum { ORC_I32 = 0, ORC_I64 = 1, ORC_BYTES = 2 };
+enum { ORC_RAW = 0, ORC_FOR_BP = 1, ORC_DICT_BP = 2, ORC_DELTA_BP = 3, ORC_RLE = 4, ORC_LZ77 = 5, ORC_F2I = 6 };
+enum { ORC_I32 = 0, ORC_I64 = 1, ORC_BYTES = 2, ORC_F64 = 3 };
 
 #define COL_MAGIC 0x4C4F435Au   /* "ZCOL" */
 #define CHK_MAGIC 0x4B48435Au   /* "ZCHK" */
@@ -64,7 +66,7 @@ uint32_t orc_bits(uint64_t x) {
 }
 
 static unsigned width_of(int dtype) { return dtype == ORC_I64 ? 64u : 32u; }
-static unsigned size_of(int dtype) { return dtype == ORC_I64 ? 8u : (dtype == ORC_I32 ? 4u : 1u); }
+static unsigned size_of(int dtype) { return (dtype == ORC_I64 || dtype == ORC_F64) ? 8u : (dtype == ORC_I32 ? 4u : 1u); }
 static uint64_t mask_of(unsigned w) { return w >= 64 ? ~0ull : ((1ull << w) - 1); }
 
 /* value i of a typed array as a sign-extended 64-bit integer */
@@ -152,6 +154,7 @@ static uint64_t chunk_bound(int scheme, int dtype, uint64_t rows) {
     case ORC_DELTA_BP: return b + (rows / DELTA_BLOCK + 1) * (24 + 16) + rows * sz + 16;
     case ORC_RLE: return b + rows * (sz + 4) + (rows / RLE_DIR_ROWS + 1) * 8;
     case ORC_LZ77: return b + rows + rows / 2 + 64;
+    case ORC_F2I: return b + rows * (8 + 4 + 8) + 32;
     }
     return 0;
 }
@@ -358,6 +361,85 @@ static uint64_t enc_lz(uint8_t* p, const uint8_t* src, uint32_t m) {
     return align16(w.end);
 }
 
+/* ---- Float2Int + bit-packing (Section 2.1 "Float2Int", Table 2) ----
+ * A double v becomes the integer d with v = d / 10^e for a decimal exponent
+ * e of the chunk (0..18); the integers are stored FOR + bit-packed.  The
+ * decoded value of d is q + r * 10^-e with q = d * 10^-e and r = d - q * 10^e
+ * (both products in fused multiply-adds), which is the double nearest to
+ * d / 10^e; a value that does not come back bit for bit from its rounded
+ * integer (non-decimal values, NaN, infinities, -0.0, |v * 10^e| >= 2^53) is
+ * an exception, stored as its row and its 64 bits.  The chunk's e has the
+ * fewest exceptions (the smallest e on a tie). */
+#define F2I_EMAX 18
+static double f2i_pow10(int e) {
+    double p = 1.0;
+    for (int k = 0; k < e; k++) p *= 10.0;   /* exact up to 10^22 */
+    return p;
+}
+static double f2i_value(int64_t d, int e) {
+    double p = f2i_pow10(e), inv = 1.0 / p;  /* the double nearest 10^-e */
+    double x = (double)d;
+    double q = x * inv;
+    double r = fma(-q, p, x);
+    return fma(r, inv, q);
+}
+static int f2i_fits(double v, int e, int64_t* d) {
+    if (!isfinite(v)) return 0;
+    double t = v * f2i_pow10(e);
+    if (!(fabs(t) < 9007199254740992.0)) return 0;
+    int64_t k = (int64_t)nearbyint(t);        /* round half to even */
+    double back = f2i_value(k, e);
+    if (memcmp(&back, &v, 8) != 0) return 0;
+    *d = k;
+    return 1;
+}
+static uint64_t enc_f2i(uint8_t* p, const void* x, uint32_t m) {
+    const double* v = (const double*)x;
+    int best_e = 0;
+    uint32_t best_ex = 0xFFFFFFFFu;
+    for (int e = 0; e <= F2I_EMAX; e++) {
+        uint32_t ex = 0;
+        int64_t d;
+        for (uint32_t i = 0; i < m; i++) ex += !f2i_fits(v[i], e, &d);
+        if (ex < best_ex) { best_ex = ex; best_e = e; }
+    }
+    int64_t* d = (int64_t*)malloc(sizeof(int64_t) * (m + 1));
+    uint8_t* ok = (uint8_t*)malloc(m + 1);
+    uint64_t* u = (uint64_t*)malloc(sizeof(uint64_t) * (m + 1));
+    int64_t mn = 0;
+    int have = 0;
+    for (uint32_t i = 0; i < m; i++) {
+        ok[i] = (uint8_t)f2i_fits(v[i], best_e, &d[i]);
+        if (ok[i] && (!have || d[i] < mn)) { mn = d[i]; have = 1; }
+    }
+    uint64_t mx = 0;
+    for (uint32_t i = 0; i < m; i++) {
+        u[i] = ok[i] ? (uint64_t)d[i] - (uint64_t)mn : 0;
+        if (u[i] > mx) mx = u[i];
+    }
+    uint32_t b = orc_bits(mx);
+    chunk_w w = {p, 64};
+    chunk_header(p, ORC_F2I, ORC_F64, b, 0, m, best_ex, (uint64_t)mn);
+    p[48] = (uint8_t)best_e;
+    uint64_t o0 = sec_begin(&w, 0, orc_packed_bytes(m, b));
+    orc_pack(u, m, b, p + o0);
+    uint64_t o1 = sec_begin(&w, 1, 4ull * best_ex);
+    uint64_t o2 = sec_begin(&w, 2, 8ull * best_ex);
+    uint32_t k = 0;
+    for (uint32_t i = 0; i < m; i++)
+        if (!ok[i]) {
+            uint64_t bits;
+            memcpy(&bits, &v[i], 8);
+            put_u32(p + o1 + 4ull * k, i);
+            put_u64(p + o2 + 8ull * k, bits);
+            k++;
+        }
+    free(d);
+    free(ok);
+    free(u);
+    return align16(w.end);
+}
+
 /* ------------------------------------------------------------------------- */
 /* column encoder                                                            */
 /* ------------------------------------------------------------------------- */
@@ -369,6 +451,7 @@ uint64_t orc_encode_bound(int scheme, int dtype, uint64_t n, uint32_t chunk_rows
 
 static int scheme_ok(int scheme, int dtype) {
     if (dtype == ORC_BYTES) return scheme == ORC_RAW || scheme == ORC_LZ77;
+    if (dtype == ORC_F64) return scheme == ORC_RAW || scheme == ORC_F2I;
     if (dtype != ORC_I32 && dtype != ORC_I64) return 0;
     return scheme >= ORC_RAW && scheme <= ORC_RLE;
 }
@@ -397,6 +480,7 @@ int orc_encode(int scheme, int dtype, const void* data, uint64_t n, uint32_t chu
         case ORC_DELTA_BP: len = enc_delta(p, dtype, x, m); break;
         case ORC_RLE: len = enc_rle(p, dtype, x, m); break;
         case ORC_LZ77: len = enc_lz(p, x, m); break;
+        case ORC_F2I: len = enc_f2i(p, x, m); break;
         }
         if (err) return err;
         uint8_t* d = out + 64 + 32 * c;
@@ -500,6 +584,22 @@ int orc_decode_chunk(const uint8_t* c, uint64_t len, void* out, uint64_t out_cap
         }
         if (presum != m) return ORC_ECORRUPT;
         (void)s2; (void)l2;
+        return ORC_OK;
+    }
+    case ORC_F2I: {
+        /* v_i = f2i_value(ref + u_i, e); the rows listed in s1 take the 64 bits in s2 */
+        uint32_t e = c[48];
+        if (!sec_ok(c, len, 0) || !sec_ok(c, len, 1) || !sec_ok(c, len, 2) || b > 64 || e > F2I_EMAX ||
+            n_aux > m || l0 != orc_packed_bytes(m, b) || l1 != 4ull * n_aux || l2 != 8ull * n_aux)
+            return ORC_ECORRUPT;
+        double* o = (double*)out;
+        for (uint32_t i = 0; i < m; i++) o[i] = f2i_value((int64_t)(ref + orc_unpack_one(s0, i, b)), (int)e);
+        for (uint32_t k = 0; k < n_aux; k++) {
+            uint32_t pos = get_u32(s1 + 4ull * k);
+            if (pos >= m || (k > 0 && pos <= get_u32(s1 + 4ull * (k - 1)))) return ORC_ECORRUPT;
+            uint64_t bits = get_u64(s2 + 8ull * k);
+            memcpy(&o[pos], &bits, 8);
+        }
         return ORC_OK;
     }
     case ORC_LZ77: {

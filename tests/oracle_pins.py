@@ -383,4 +383,110 @@ def pin_strings(orc):
     assert o[0] == 0 and o[-1] == len(t) and np.all(np.diff(o) > 0)
 
 
+
+# ---- Float2Int (Section 2.1 "Float2Int"; Table 2 pairs it with bit-packing) ----
+
+def _f2i_blob(e: int, b: int, ref: int, packed: bytes, pos, vals, rows: int) -> bytes:
+    """A hand-built Float2Int chunk: header (exponent e in byte 48), then the
+    packed integers, the exception rows and the exception bit patterns."""
+    ex_pos = b"".join(struct.pack("<I", p) for p in pos)
+    ex_val = b"".join(struct.pack("<d", v) for v in vals)
+    a = 64
+    bb = (a + len(packed) + 15) // 16 * 16
+    c = (bb + len(ex_pos) + 15) // 16 * 16
+    end = (c + len(ex_val) + 15) // 16 * 16
+    blob = bytearray(max(end, 64))
+    struct.pack_into("<IBBBBIIq", blob, 0, 0x4B48435A, O.FLOAT2INT, O.F64, b, 0, rows, len(pos), ref)
+    struct.pack_into("<3I3I", blob, 24, a, bb, c, len(packed), len(ex_pos), len(ex_val))
+    blob[48] = e
+    blob[a:a + len(packed)] = packed
+    blob[bb:bb + len(ex_pos)] = ex_pos
+    blob[c:c + len(ex_val)] = ex_val
+    return bytes(blob)
+
+
+def _same_bits(x, y) -> bool:
+    return np.array_equal(np.asarray(x, np.float64).view(np.uint64), np.asarray(y, np.float64).view(np.uint64))
+
+
+def pin_f2i_hand_example(orc):
+    # 1.25, 3.5, 10, 0.75 are the integers 125, 350, 1000, 75 at e = 2 (at e = 1,
+    # 1.25 * 10 = 12.5 rounds to 12 and 1.2 != 1.25): reference 75, u = 50,
+    # 275, 925, 0, b = bits(925) = 10, packed LSB-first
+    x = np.array([1.25, 3.5, 10.0, 0.75])
+    buf = orc.encode(x, O.FLOAT2INT, 1000)
+    (off, ln, r0, rows, ch), = chunks_of(orc, buf)
+    blob = buf[off:off + ln]
+    assert (ch["bw"], ch["ref"], ch["n_aux"], blob[48]) == (10, 75, 0, 2)
+    assert ch["secs"][0] == bigint_pack([50, 275, 925, 0], 10) == bytes.fromhex("324cd43900")
+    assert _same_bits(orc.decode(buf), x)
+
+
+def pin_f2i_value_is_the_nearest_double(orc):
+    # the decoded value of integer d at exponent e is the double nearest to
+    # d / 10^e: Python's Fraction -> float conversion rounds correctly
+    from fractions import Fraction
+    rng = np.random.default_rng(5)
+    for e in range(0, 19):
+        for scale in (10, 10**6, 2**40, 2**53 - 1):
+            d = [int(v) for v in rng.integers(-scale, scale, 200, dtype=np.int64)] + [scale, -scale, 0, 1, -1]
+            ref = min(d)
+            u = [v - ref for v in d]
+            b = max(u).bit_length()
+            blob = _f2i_blob(e, b, ref, bigint_pack(u, b), [], [], len(d))
+            got = orc.decode_chunk(blob, np.float64)
+            want = np.array([float(Fraction(v, 10 ** e)) for v in d])
+            assert _same_bits(got, want), (e, scale)
+
+
+def pin_f2i_decimal_prices(orc):
+    # prices with two decimals (the double nearest cents / 100) all come back
+    # from their integer cents at e = 2: no exceptions, reference = the
+    # chunk's smallest cents, width = bits(max - min)
+    rng = np.random.default_rng(6)
+    cents = np.round(np.exp(rng.normal(11.5, 1.0, 30000))).astype(np.int64)
+    cents[::7] += 1                                   # make sure odd cents occur
+    x = cents / 100.0
+    buf = orc.encode(x, O.FLOAT2INT, 10000)
+    for off, ln, r0, rows, ch in chunks_of(orc, buf):
+        c = cents[r0:r0 + rows]
+        assert buf[off + 48] == 2 and ch["n_aux"] == 0
+        assert ch["ref"] == c.min() and ch["bw"] == int(c.max() - c.min()).bit_length()
+    assert _same_bits(orc.decode(buf), x)
+    # integer-valued doubles need no scaling
+    y = np.arange(-500, 500, dtype=np.float64) * 3
+    buf = orc.encode(y, O.FLOAT2INT, 4096)
+    (off, ln, r0, rows, ch), = chunks_of(orc, buf)
+    assert buf[off + 48] == 0 and ch["n_aux"] == 0 and ch["ref"] == -1500 and ch["bw"] == 12
+    assert _same_bits(orc.decode(buf), y)
+
+
+def pin_f2i_exceptions(orc):
+    # values that are not decimals of at most 18 digits after the point, or
+    # whose integer would reach 2^53, are kept bit for bit as exceptions
+    sp = np.array([np.nan, np.inf, -np.inf, -0.0, 0.0, 1e300, 5e-324, 0.1 + 0.2, 1 / 3, 2.0 ** 60, -7.5])
+    buf = orc.encode(sp, O.FLOAT2INT, 1000)
+    (off, ln, r0, rows, ch), = chunks_of(orc, buf)
+    # only 0.0 and -7.5 fit (at e = 1, the smallest exponent that takes -7.5)
+    assert buf[off + 48] == 1 and ch["n_aux"] == 9
+    assert list(struct.unpack_from("<9I", ch["secs"][1])) == [0, 1, 2, 3, 5, 6, 7, 8, 9]
+    assert _same_bits(orc.decode(buf), sp)
+    # a hand-built chunk: rows 1 and 3 are replaced by the stored bits
+    blob = _f2i_blob(0, 2, 5, bigint_pack([0, 1, 2, 3], 2), [1, 3], [-0.0, 0.5], 4)
+    assert _same_bits(orc.decode_chunk(blob, np.float64), [5.0, -0.0, 7.0, 0.5])
+    # malformed: rows out of order or out of range, exponent above 18, sizes
+    bad = [
+        _f2i_blob(0, 2, 5, bigint_pack([0, 1, 2, 3], 2), [3, 1], [1.0, 2.0], 4),
+        _f2i_blob(0, 2, 5, bigint_pack([0, 1, 2, 3], 2), [4], [1.0], 4),
+        _f2i_blob(19, 2, 5, bigint_pack([0, 1, 2, 3], 2), [], [], 4),
+        _f2i_blob(0, 3, 5, bigint_pack([0, 1, 2, 3], 2), [], [], 4),
+    ]
+    for blob in bad:
+        try:
+            orc.decode_chunk(blob, np.float64)
+        except O.OracleError as err:
+            assert err.code == O.ECORRUPT
+        else:
+            raise AssertionError("malformed Float2Int chunk accepted")
+
 PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

@@ -44,6 +44,13 @@ MUTANTS = {
                              "ll |= (uint32_t)(byte & 0x7F) << sh;\n                sh += 8;"),
     "lz_varint_five_bytes": ("if (vp >= l0 || sh > 14) return ORC_ECORRUPT; /* at most 3 bytes */",
                              "if (vp >= l0 || sh > 28) return ORC_ECORRUPT;"),
+    "f2i_multiply_only": ("    return fma(r, inv, q);", "    (void)r;\n    return q;"),
+    "f2i_no_exception_patch": ("            memcpy(&o[pos], &bits, 8);", "            (void)bits;"),
+    "f2i_truncates": ("int64_t k = (int64_t)nearbyint(t);", "int64_t k = (int64_t)t;"),
+    "f2i_largest_exponent_on_tie": ("if (ex < best_ex) { best_ex = ex; best_e = e; }",
+                                    "if (ex <= best_ex) { best_ex = ex; best_e = e; }"),
+    "f2i_reference_is_max": ("if (ok[i] && (!have || d[i] < mn)) { mn = d[i]; have = 1; }",
+                             "if (ok[i] && (!have || d[i] > mn)) { mn = d[i]; have = 1; }"),
     "lz_no_raw_fallback": ("if ((uint64_t)nl + no + nlit >= m) {", "if (0) {"),
     "lz_offset_of_next_token": ("uint32_t off = get_u16(s1 + 2ull * t);", "uint32_t off = get_u16(s1 + 2ull * (t + 1 < n_aux - 1 ? t + 1 : t));"),
 }
