@@ -503,6 +503,9 @@ def run_profile(args, zf, torch):
         # 12 bits of the counter-based generator), FOR + 12-bit packing,
         # 65,536-row chunks
         cols = [(W.uniform_int(1, 0, 0, args.rows, 0, 4096).astype(np.int32), zf.ZF_FOR_BP, 65536)]
+    elif args.profile == "float":
+        # float64 prices with two decimals (log-normal cents / 100), Float2Int + packing, 1M-row chunks
+        cols = [(W.decimal_prices(1, 7, 0, args.rows), zf.ZF_FLOAT2INT, CHUNK_ROWS)]
     else:
         keys, dates = make_workload(1, args.rows)
         cols = [(x, s, CHUNK_ROWS) for x, s, on in ((keys, zf.ZF_DELTA_BP, args.profile in ("keys", "both")),
@@ -550,7 +553,7 @@ def main():
     ap.add_argument("--slots", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--no-graph", action="store_true", help="enqueue transfers call by call (no CUDA graph)")
-    ap.add_argument("--profile", choices=["keys", "dates", "both", "for"], default=None,
+    ap.add_argument("--profile", choices=["keys", "dates", "both", "for", "float"], default=None,
                     help="only decode the resident column(s) --steps times (for ncu captures)")
     ap.add_argument("--rows", type=int, default=N_ROWS, help="rows per column (profile / batched runs)")
     ap.add_argument("--workload", choices=["group_parallel", "batched", "selector", "text"], default="group_parallel",

@@ -56,6 +56,13 @@
  *              length - 4 of token t at 2t+1; s1 = T-1 u16 offsets (1..65535);
  *              s2 = literal bytes.  Token t copies its literals, then (all but
  *              the last token) `length` bytes from `offset` bytes back
+ *     FLOAT2INT (F64 only) header byte 48 = decimal exponent e (0..18);
+ *              s0 = bit-packed (d - reference), b = bits(max - min), of the
+ *              integers d with v = d / 10^e; s1 = u32 rows of the n_aux
+ *              exceptions (ascending), s2 = their 64-bit patterns.  The value
+ *              of d is q + r * 10^-e with q = d * 10^-e and r = d - q * 10^e
+ *              (fused multiply-adds; 10^-e = the double nearest it): the
+ *              double nearest d / 10^e.  Exception rows hold u = 0 in s0.
  *   Bit-packing: value i occupies stream bits [i*b, i*b+b), least
  *   significant bit first; stream bit k is bit k%8 of byte k/8.
  */
@@ -80,18 +87,19 @@ typedef enum {
     ZF_EBUSY = 7          /* a transfer is in flight: call zf_sync first */
 } zf_status;
 
-typedef enum { ZF_I32 = 0, ZF_I64 = 1, ZF_BYTES = 2 } zf_dtype;
+typedef enum { ZF_I32 = 0, ZF_I64 = 1, ZF_BYTES = 2, ZF_F64 = 3 } zf_dtype;
 
 typedef enum {
     ZF_RAW = 0, ZF_FOR_BP = 1, ZF_DICT_BP = 2, ZF_DELTA_BP = 3, ZF_RLE = 4, ZF_LZ77 = 5,
-    ZF_NSCHEMES = 6
+    ZF_FLOAT2INT = 6,     /* float64 columns (Section 2.1 "Float2Int", with bit-packing as in Table 2) */
+    ZF_NSCHEMES = 7
 } zf_scheme;
 
 typedef struct zf_ctx zf_ctx;
 typedef struct zf_compressed zf_compressed;
 typedef struct zf_resident zf_resident;
 
-/* A raw column in host memory.  I32/I64: `data` holds n values.  BYTES:
+/* A raw column in host memory.  I32/I64/F64: `data` holds n values.  BYTES:
  * `data` holds offsets[n] bytes and `offsets` (host, int32) holds n+1
  * non-decreasing offsets with offsets[0] == 0. */
 typedef struct {
@@ -169,7 +177,9 @@ zf_status zf_ctx_set_ring(zf_ctx* ctx, uint32_t slots, uint64_t slot_bytes);
 /* Choose scheme, chunk size and kernel geometry for a column.  With
  * opts->scheme >= 0 the scheme is forced; otherwise opts->selector picks the
  * heuristic (0), the learned MLP (1, needs zf_selector_load) or exhaustive
- * measurement on the GPU (2).  `opts` may be NULL. */
+ * measurement on the GPU (2).  F64 columns take FLOAT2INT (or a forced RAW):
+ * the selector's classes cover integer and byte columns only.  `opts` may
+ * be NULL. */
 zf_status zf_plan(zf_ctx* ctx, const zf_column* col, const zf_plan_opts* opts, zf_plan_t* out);
 
 /* Compress a host column with a plan into pinned host memory owned by the

@@ -186,9 +186,12 @@ __host__ __device__ inline uint32_t stage_bytes_for(uint32_t bmax) { return ((kW
 // ---------------------------------------------------------------- Fully-Parallel
 // Extract and store the rows of a staged FOR/dictionary warp tile; returns
 // true if a dictionary code was out of range.
+// FLOAT2INT (T = int64 bits of the doubles): the integer d = reference + u
+// becomes q + r * 10^-e, q = d * 10^-e, r = d - q * 10^e (p10 = 10^e,
+// inv10 = the double nearest 10^-e).
 template <class T, int SCHEME, bool NARROW>
 __device__ __forceinline__ bool fp_rows(const ZfDevChunk& c, const Hdr& h, T* dst, const uint32_t* wsm, uint32_t nr,
-                                        uint32_t b, uint32_t lane) {
+                                        uint32_t b, uint32_t lane, double p10 = 1.0, double inv10 = 1.0) {
     constexpr int V = 16 / sizeof(T);
     const T* dict = reinterpret_cast<const T*>(c.blob + h.off[0]);
     const T ref = (T)h.ref;
@@ -210,6 +213,10 @@ __device__ __forceinline__ bool fp_rows(const ZfDevChunk& c, const Hdr& h, T* ds
         for (int k = 0; k < V; k++) {
             if constexpr (SCHEME == ZF_FOR_BP) {
                 v[k] = (T)(ref + (T)u[k]);
+            } else if constexpr (SCHEME == ZF_FLOAT2INT) {
+                const double x = __ll2double_rn((long long)(h.ref + u[k]));
+                const double q = __dmul_rn(x, inv10);
+                v[k] = (T)__double_as_longlong(__fma_rn(__fma_rn(-q, p10, x), inv10, q));
             } else {
                 const bool in = i0 + k < nr;
                 bad |= in && u[k] >= h.n_aux;
@@ -223,9 +230,44 @@ __device__ __forceinline__ bool fp_rows(const ZfDevChunk& c, const Hdr& h, T* ds
     return bad;
 }
 
-// SCHEME: ZF_FOR_BP, ZF_DICT_BP or ZF_RAW.  Rows [r0, r0 + nrows) of the chunk
-// (r0 a multiple of 1024).  The packed stream of consecutive tiles is
-// contiguous, so tile i+1 is staged while tile i decodes.
+// Float2Int exceptions of rows [r0, r0 + nrows): their rows are ascending,
+// so a 32-way search (one load per lane per round) finds the first at or
+// after r0, and the warp writes the stored 64 bits over the decoded rows.
+__device__ __forceinline__ void f2i_exceptions(const ZfDevChunk& c, const Hdr& h, unsigned long long* dst,
+                                               uint32_t r0, uint32_t nrows, uint32_t lane) {
+    const uint32_t n = h.n_aux;
+    if (n == 0) return;
+    const uint32_t* pos = reinterpret_cast<const uint32_t*>(c.blob + h.off[1]);
+    const unsigned long long* val = reinterpret_cast<const unsigned long long*>(c.blob + h.off[2]);
+    uint32_t lo = 0, hi = n;                      // rows at indices < lo are < r0; index hi counts as >= r0
+    while (hi - lo > 32) {
+        const uint32_t step = (hi - lo + 31) / 32, idx = lo + lane * step;
+        const uint32_t ge = __ballot_sync(0xFFFFFFFFu, idx >= hi || __ldg(pos + idx) >= r0);
+        if (ge & 1u) {
+            hi = lo;
+        } else {
+            const uint32_t f = ge ? __ffs(ge) - 1 : 32;   // first sample at or after r0 (32: none)
+            const uint32_t prev = lo + (f - 1) * step;
+            hi = f < 32 ? min(hi, lo + f * step) : hi;
+            lo = prev + 1;
+        }
+    }
+    const uint32_t idx = lo + lane;
+    const uint32_t ge = __ballot_sync(0xFFFFFFFFu, idx >= hi || __ldg(pos + idx) >= r0);
+    uint32_t k0 = ge ? lo + __ffs(ge) - 1 : hi;
+    __syncwarp();   // the decoded rows of this warp are written before they are replaced
+    for (;; k0 += 32) {
+        const uint32_t k = k0 + lane;
+        const uint32_t r = k < n ? __ldg(pos + k) : 0xFFFFFFFFu;
+        const bool in = r >= r0 && r - r0 < nrows;
+        if (in) dst[r - r0] = __ldg(val + k);
+        if (!__any_sync(0xFFFFFFFFu, in && k < n)) break;
+    }
+}
+
+// SCHEME: ZF_FOR_BP, ZF_DICT_BP, ZF_FLOAT2INT or ZF_RAW.  Rows [r0, r0 + nrows)
+// of the chunk (r0 a multiple of 1024).  The packed stream of consecutive
+// tiles is contiguous, so tile i+1 is staged while tile i decodes.
 template <class T, int SCHEME>
 __device__ void fp_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t nrows, uint32_t* wsm,
                        uint32_t* err) {
@@ -241,6 +283,16 @@ __device__ void fp_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t 
         }
     } else {
         const uint32_t b = h.b;
+        double p10 = 1.0, inv10 = 1.0;
+        if constexpr (SCHEME == ZF_FLOAT2INT) {
+            const uint32_t e = c.blob[48];
+            if (e > (uint32_t)zf::kF2IMaxExp) {
+                if (lane == 0) report(err, ZF_ECORRUPT, c.chunk_id);
+                return;
+            }
+            for (uint32_t k = 0; k < e; k++) p10 *= 10.0;   // exact: every power up to 10^22 is a double
+            inv10 = 1.0 / p10;                               // IEEE division: the double nearest 10^-e
+        }
         if (b > 8 * sizeof(T) || (SCHEME == ZF_DICT_BP && b > 16)) {
             if (lane == 0) report(err, ZF_ECORRUPT, c.chunk_id);
             return;
@@ -266,10 +318,12 @@ __device__ void fp_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t 
             const uint32_t nr = min(kWarpRows, nrows - i * kWarpRows);
             const uint32_t* buf = wsm + (i & 1) * sb;
             if (V == 4 && b <= 8) bad |= fp_rows<T, SCHEME, true>(c, h, dst + i * kWarpRows, buf, nr, b, lane);
-            else bad |= fp_rows<T, SCHEME, false>(c, h, dst + i * kWarpRows, buf, nr, b, lane);
+            else bad |= fp_rows<T, SCHEME, false>(c, h, dst + i * kWarpRows, buf, nr, b, lane, p10, inv10);
             __syncwarp();
         }
         if (bad) report(err, ZF_ECORRUPT, c.chunk_id);
+        if constexpr (SCHEME == ZF_FLOAT2INT)
+            f2i_exceptions(c, h, reinterpret_cast<unsigned long long*>(dst), r0, nrows, lane);
     }
 }
 
@@ -780,7 +834,7 @@ __device__ __forceinline__ void rle_warp(const ZfDevChunk& c, const Hdr& h, uint
 // the widest bit width of the chunks it decodes (two staging buffers).
 __host__ __device__ inline uint32_t warp_smem(int scheme, uint32_t value_bytes, uint32_t bmax) {
     switch (scheme) {
-    case ZF_FOR_BP: case ZF_DICT_BP: return 2 * stage_bytes_for(bmax);
+    case ZF_FOR_BP: case ZF_DICT_BP: case ZF_FLOAT2INT: return 2 * stage_bytes_for(bmax);
     case ZF_DELTA_BP: return 2 * stage_bytes_for(bmax) + 4096;   // + the store transpose buffer
     case ZF_RLE: return 128 + 2 * rle_buf_bytes(value_bytes);   // row bitmask + two staging buffers
     }

@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <cstring>
 #include <functional>
 #include <mutex>
@@ -86,6 +87,90 @@ void enc_raw(const T* x, uint32_t m, Out& o) {
     w.header(ZF_RAW, dtype_code<T>(), 0, 0, m, 0, 0);
     uint64_t off = w.section(0, (uint64_t)m * sizeof(T));
     if (m) memcpy(&o.b[off], x, (uint64_t)m * sizeof(T));
+}
+
+// ------------------------------------------------------------------ Float2Int + BP
+// A double v is stored as the integer d with v = d / 10^e, e the chunk's
+// decimal exponent (0..18), and the integers FOR + bit-packed (Section 2.1
+// "Float2Int"; Table 2 pairs it with bit-packing).  d decodes to
+// q + r * 10^-e, q = d * 10^-e, r = d - q * 10^e (fused multiply-adds), the
+// double nearest d / 10^e.  A value that does not come back bit for bit
+// from its rounded integer is an exception (row + 64 bits).  The chunk takes
+// the exponent with the fewest exceptions, the smallest on a tie.
+struct Pow10 {
+    double p[kF2IMaxExp + 1], inv[kF2IMaxExp + 1];
+    Pow10() {
+        double x = 1.0;   // exact: 10^18 < 2^63 and every power up to 10^22 is a double
+        for (int e = 0; e <= kF2IMaxExp; e++) {
+            p[e] = x;
+            inv[e] = 1.0 / x;
+            x *= 10.0;
+        }
+    }
+};
+const Pow10 kPow10;
+
+inline double f2i_value(int64_t d, int e) {
+    const double x = (double)d, q = x * kPow10.inv[e];
+    return std::fma(std::fma(-q, kPow10.p[e], x), kPow10.inv[e], q);
+}
+
+inline bool f2i_fits(double v, int e, int64_t* d) {
+    if (!std::isfinite(v)) return false;
+    const double t = v * kPow10.p[e];
+    if (!(std::fabs(t) < 9007199254740992.0)) return false;
+    const int64_t k = (int64_t)std::nearbyint(t);
+    const double back = f2i_value(k, e);
+    if (memcmp(&back, &v, 8) != 0) return false;
+    *d = k;
+    return true;
+}
+
+void enc_f2i(const double* x, uint32_t m, Out& o) {
+    int best_e = 0;
+    uint32_t best_ex = UINT32_MAX;
+    for (int e = 0; e <= kF2IMaxExp && best_ex > 0; e++) {
+        uint32_t ex = 0;
+        int64_t d;
+        for (uint32_t i = 0; i < m && ex < best_ex; i++) ex += !f2i_fits(x[i], e, &d);
+        if (ex < best_ex) {
+            best_ex = ex;
+            best_e = e;
+        }
+    }
+    std::vector<int64_t> d(m);
+    std::vector<uint8_t> ok(m);
+    int64_t mn = 0;
+    bool have = false;
+    for (uint32_t i = 0; i < m; i++) {
+        ok[i] = f2i_fits(x[i], best_e, &d[i]);
+        if (ok[i] && (!have || d[i] < mn)) {
+            mn = d[i];
+            have = true;
+        }
+    }
+    uint64_t mx = 0;
+    for (uint32_t i = 0; i < m; i++)
+        if (ok[i]) mx = std::max(mx, (uint64_t)d[i] - (uint64_t)mn);
+    const uint32_t b = bits_of(mx);
+    const uint64_t pb = packed_bytes(m, b);
+    o.b.assign(align16(align16(align16(kChunkHeader) + pb) + 4ull * best_ex) + align16(8ull * best_ex) + 16, 0);
+    ChunkWriter w(o);
+    w.header(ZF_FLOAT2INT, ZF_F64, b, 0, m, best_ex, (uint64_t)mn);
+    o.put8(48, (uint8_t)best_e);
+    const uint64_t o0 = w.section(0, pb);
+    pack_stream(m, b, [&](uint64_t i) { return ok[i] ? (uint64_t)d[i] - (uint64_t)mn : 0ull; }, &o.b[o0]);
+    const uint64_t o1 = w.section(1, 4ull * best_ex), o2 = w.section(2, 8ull * best_ex);
+    uint32_t k = 0;
+    for (uint32_t i = 0; i < m; i++)
+        if (!ok[i]) {
+            uint64_t bits;
+            memcpy(&bits, &x[i], 8);
+            memcpy(&o.b[o1 + 4ull * k], &i, 4);
+            memcpy(&o.b[o2 + 8ull * k], &bits, 8);
+            k++;
+        }
+    o.b.resize(align16(w.end));
 }
 
 // ------------------------------------------------------------------ FOR + BP
@@ -325,6 +410,16 @@ zf_status encode_part(const PartSpec& p, std::vector<Out>& blobs, std::string* w
                 uint64_t off = w.section(0, m);
                 if (m) memcpy(&o.b[off], x, m);
             }
+        } else if (p.dtype == ZF_F64) {
+            if (p.scheme == ZF_FLOAT2INT) {
+                enc_f2i(reinterpret_cast<const double*>(x), m, o);
+            } else {  // RAW doubles
+                o.b.assign(align16(kChunkHeader + 8ull * m), 0);
+                ChunkWriter w(o);
+                w.header(ZF_RAW, ZF_F64, 0, 0, m, 0, 0);
+                uint64_t off = w.section(0, 8ull * m);
+                if (m) memcpy(&o.b[off], x, 8ull * m);
+            }
         } else if (p.dtype == ZF_I32) {
             auto* v = reinterpret_cast<const int32_t*>(x);
             switch (p.scheme) {
@@ -397,6 +492,7 @@ void write_part(const PartSpec& p, const std::vector<Out>& blobs, uint8_t* dst, 
 
 bool scheme_fits(int scheme, int dtype) {
     if (dtype == ZF_BYTES) return scheme == ZF_RAW || scheme == ZF_LZ77;
+    if (dtype == ZF_F64) return scheme == ZF_RAW || scheme == ZF_FLOAT2INT;
     if (dtype != ZF_I32 && dtype != ZF_I64) return false;
     return scheme >= ZF_RAW && scheme <= ZF_RLE;
 }
@@ -437,7 +533,7 @@ void free_compressed(zf_compressed* c) {
 
 zf_status encode_column(const zf_plan_t& plan, const zf_column& col, zf_compressed** out, std::string* why) {
     int dt = col.dtype;
-    if (dt != ZF_I32 && dt != ZF_I64 && dt != ZF_BYTES) return ZF_EINVAL;
+    if (dt != ZF_I32 && dt != ZF_I64 && dt != ZF_BYTES && dt != ZF_F64) return ZF_EINVAL;
     if (col.n && !col.data && !(dt == ZF_BYTES && col.offsets)) return ZF_EINVAL;
     std::vector<PartSpec> specs;
     if (dt == ZF_BYTES) {
@@ -522,6 +618,7 @@ bool check_chunk(const uint8_t* c, uint64_t len, int scheme, int dtype, uint32_t
     case ZF_DELTA_BP: nsec = 2; break;
     case ZF_RLE: nsec = 3; break;
     case ZF_LZ77: nsec = (c[7] & 1) ? 1 : 3; break;
+    case ZF_FLOAT2INT: nsec = 3; break;
     default: return fail(why, "unknown scheme");
     }
     for (int s = 0; s < nsec; s++)
@@ -560,6 +657,19 @@ bool check_chunk(const uint8_t* c, uint64_t len, int scheme, int dtype, uint32_t
             ln[2] != 8ull * ((rows + kRleDirRows - 1) / kRleDirRows))
             return fail(why, "RLE sections");
         break;
+    case ZF_FLOAT2INT: {
+        if (b > 64 || c[48] > kF2IMaxExp || n_aux > rows || ln[0] != packed_bytes(rows, b) ||
+            ln[1] != 4ull * n_aux || ln[2] != 8ull * n_aux)
+            return fail(why, "Float2Int sections");
+        // exception rows strictly increasing and inside the chunk
+        for (uint32_t k = 0; k < n_aux; k++) {
+            const uint32_t r = rd<uint32_t>(c + off[1] + 4ull * k);
+            if (r >= rows || (k && r <= rd<uint32_t>(c + off[1] + 4ull * (k - 1))))
+                return fail(why, "Float2Int exception rows");
+        }
+        *bmax = (uint8_t)b;
+        break;
+    }
     case ZF_LZ77:
         if (rows > kLzBlock) return fail(why, "LZ77 block above 64 KiB");
         if ((c[7] & 1) && ln[0] != rows) return fail(why, "raw LZ77 block length");

@@ -25,7 +25,8 @@ constexpr uint32_t kMaxTileRows = 16384;   // rows per warp job (16 warp tiles)
 
 inline uint64_t align16(uint64_t x) { return (x + 15) & ~uint64_t(15); }
 inline uint32_t bits_of(uint64_t x) { return x ? 64u - (uint32_t)__builtin_clzll(x) : 0u; }
-inline uint32_t dtype_size(int dt) { return dt == ZF_I64 ? 8u : dt == ZF_I32 ? 4u : 1u; }
+inline uint32_t dtype_size(int dt) { return (dt == ZF_I64 || dt == ZF_F64) ? 8u : dt == ZF_I32 ? 4u : 1u; }
+constexpr int kF2IMaxExp = 18;                 // Float2Int decimal exponents 0..18
 inline uint64_t packed_bytes(uint64_t n, uint32_t b) { return (n * b + 7) / 8; }
 
 // Host-side description of one chunk of one part of a compressed column.

@@ -49,6 +49,9 @@ __device__ __forceinline__ void decode_one(const ZfDevChunk& c, const zfd::Hdr& 
             zfd::delta_job<T, WS>(c, h, r0, nrows, wsm, err, c.bmax);
         else if constexpr (SCHEME == ZF_RLE)
             zfd::rle_job<T, WS>(c, h, r0, nrows, wsm, err);
+    } else if constexpr (DT == ZF_F64) {
+        // doubles travel as their 64-bit patterns
+        if constexpr (SCHEME == ZF_RAW || SCHEME == ZF_FLOAT2INT) zfd::fp_job<int64_t, SCHEME>(c, h, r0, nrows, wsm, err);
     } else if constexpr (DT == ZF_BYTES && SCHEME == ZF_RAW) {
         // raw bytes: 16-byte copies
         const uint32_t lane = threadIdx.x & 31;
@@ -72,6 +75,7 @@ __device__ __noinline__ void decode_mixed(const ZfDevChunk& c, const zfd::Hdr& h
         ZF_CASE(ZF_DICT_BP, ZF_I32) ZF_CASE(ZF_DICT_BP, ZF_I64)
         ZF_CASE(ZF_DELTA_BP, ZF_I32) ZF_CASE(ZF_DELTA_BP, ZF_I64)
         ZF_CASE(ZF_RLE, ZF_I32) ZF_CASE(ZF_RLE, ZF_I64)
+        ZF_CASE(ZF_RAW, ZF_F64) ZF_CASE(ZF_FLOAT2INT, ZF_F64)
 #undef ZF_CASE
     default:
         if ((threadIdx.x & 31) == 0) zfd::report(err, ZF_EINVAL, c.chunk_id);
@@ -87,7 +91,7 @@ __device__ __forceinline__ void run_job(const LaunchArgs& a, uint32_t job, uint3
     zfd::Hdr h;
     zfd::load_hdr(c.blob, h);
     const uint32_t r0 = (job - c.tile0) * a.job_rows;
-    const uint32_t sz = c.dtype == ZF_I64 ? 8 : c.dtype == ZF_I32 ? 4 : 1;
+    const uint32_t sz = (c.dtype == ZF_I64 || c.dtype == ZF_F64) ? 8 : c.dtype == ZF_I32 ? 4 : 1;
     if (h.rows != c.rows || r0 >= c.rows || (uint64_t)c.rows * sz > c.dst_cap) {
         if ((threadIdx.x & 31) == 0) zfd::report(a.err, ZF_ECORRUPT, c.chunk_id);
         return;
@@ -145,6 +149,7 @@ KernelFn pick(int scheme, int dtype) {
         ZF_K(ZF_DICT_BP, ZF_I32) ZF_K(ZF_DICT_BP, ZF_I64)
         ZF_K(ZF_DELTA_BP, ZF_I32) ZF_K(ZF_DELTA_BP, ZF_I64)
         ZF_K(ZF_RLE, ZF_I32) ZF_K(ZF_RLE, ZF_I64)
+        ZF_K(ZF_RAW, ZF_F64) ZF_K(ZF_FLOAT2INT, ZF_F64)
 #undef ZF_K
     }
     if (scheme < 0) return tiles_kernel<-1, -1, THREADS>;
@@ -170,7 +175,7 @@ std::unordered_map<void*, bool> g_attr_set;
 namespace zf {
 
 uint32_t warp_smem_bytes(int scheme, int dtype, uint32_t bmax) {
-    return zfd::warp_smem(scheme, dtype == ZF_I64 ? 8 : dtype == ZF_I32 ? 4 : 1, bmax);
+    return zfd::warp_smem(scheme, (dtype == ZF_I64 || dtype == ZF_F64) ? 8 : dtype == ZF_I32 ? 4 : 1, bmax);
 }
 
 cudaError_t launch_tiles(const TileLaunch& L, cudaStream_t s) {

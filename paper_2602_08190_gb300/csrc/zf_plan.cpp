@@ -16,6 +16,7 @@ void scheme_sizes(const T* x, uint64_t n, uint32_t chunk_rows, uint64_t out[ZF_N
     using U = typename std::make_unsigned<T>::type;
     for (int s = 0; s < ZF_NSCHEMES; s++) out[s] = 0;
     out[ZF_LZ77] = ~0ull;
+    out[ZF_FLOAT2INT] = ~0ull;
     for (uint64_t r0 = 0; r0 < n; r0 += chunk_rows) {
         uint32_t m = (uint32_t)std::min<uint64_t>(chunk_rows, n - r0);
         const T* y = x + r0;
@@ -66,6 +67,7 @@ template void scheme_sizes<int64_t>(const int64_t*, uint64_t, uint32_t, uint64_t
 // the scheme with the cheaper decode (earlier in the enum).
 int heuristic_scheme(const zf_column& col, uint32_t chunk_rows) {
     if (col.dtype == ZF_BYTES) return ZF_LZ77;
+    if (col.dtype == ZF_F64) return ZF_FLOAT2INT;   // the one float scheme; non-decimals become exceptions
     uint64_t sz[ZF_NSCHEMES];
     if (col.dtype == ZF_I32) scheme_sizes((const int32_t*)col.data, col.n, chunk_rows, sz);
     else scheme_sizes((const int64_t*)col.data, col.n, chunk_rows, sz);

@@ -282,12 +282,13 @@ void johnson_order(std::vector<Work>& work) {
         double copy = 0, dec = 0;
         while (j < work.size() && work[j].host == work[i].host) {
             const zf::ChunkInfo& c = *work[j].ch;
-            const double plain = (double)c.rows * (c.dtype == ZF_I64 ? 8 : c.dtype == ZF_I32 ? 4 : 1);
+            const double plain = (double)c.rows * zf::dtype_size(c.dtype);
             double rate;   // GB/s of plain output
             switch (c.scheme) {
             case ZF_LZ77: rate = 300; break;
             case ZF_RLE: rate = 3500; break;
             case ZF_DELTA_BP: case ZF_DICT_BP: rate = 5000; break;
+            case ZF_FLOAT2INT: rate = 1500; break;
             default: rate = 6000; break;
             }
             copy += (double)c.bytes / 200.0;
@@ -906,9 +907,10 @@ extern "C" zf_status zf_ctx_set_selector(zf_ctx* ctx, zf_mlp* net, const float* 
 
 extern "C" zf_status zf_plan(zf_ctx* ctx, const zf_column* col, const zf_plan_opts* opts, zf_plan_t* out) {
     if (!col || !out) return ZF_EINVAL;
-    if (col->dtype != ZF_I32 && col->dtype != ZF_I64 && col->dtype != ZF_BYTES) return ZF_EINVAL;
+    if (col->dtype != ZF_I32 && col->dtype != ZF_I64 && col->dtype != ZF_BYTES && col->dtype != ZF_F64) return ZF_EINVAL;
     zf_plan_opts o{-1, 0, 0, -1};
     if (opts) o = *opts;
+    if (col->dtype == ZF_F64 && o.scheme < 0) o.selector = 0;   // the selector's classes cover integer and byte columns
     zf_plan_t p{};
     p.label = -1;
     p.offsets_scheme = o.offsets_scheme < 0 ? ZF_DELTA_BP : o.offsets_scheme;

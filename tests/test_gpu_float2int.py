@@ -1,0 +1,106 @@
+"""Float2Int + bit-packing on the GPU (Section 2.1 "Float2Int"; Table 2 pairs
+it with bit-packing): float64 columns decode bit for bit -- the same 64-bit
+patterns as the column and as the oracle's decode -- through the transfer
+pipeline, from HBM-resident bytes and in the batched kernel."""
+import numpy as np
+import pytest
+
+import oracle
+import zf_workloads as W
+from gpu_helpers import Gpu, compress, out_specs
+
+zf = pytest.importorskip("paper_2602_08190_gb300")
+pytestmark = pytest.mark.gpu
+
+
+def _bits(a):
+    return np.asarray(a, np.float64).view(np.uint64)
+
+
+def _cases():
+    rng = np.random.default_rng(41)
+    prices = W.decimal_prices(3, 5, 0, 300_001)
+    mixed = prices[:70_000].copy()
+    mixed[::997] = np.nan
+    mixed[5::1999] = np.inf
+    mixed[6::2003] = -np.inf
+    mixed[7::2999] = -0.0
+    mixed[11::3001] = 1.0 / 3.0
+    mixed[13::5003] = 2.0 ** 60
+    yield "prices_2dp", prices, 65536
+    yield "prices_4dp", W.decimal_prices(4, 5, 0, 100_000, 4), 16384
+    yield "integers", rng.integers(-10**12, 10**12, 50_000).astype(np.float64), 8192
+    yield "mixed_exceptions", mixed, 16384
+    yield "random_doubles", rng.standard_normal(20_000), 4096      # every row an exception
+    yield "one_row", np.array([12.5]), 1024
+
+
+CASES = list(_cases())
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    g = Gpu()
+    yield g
+    g.close()
+
+
+@pytest.mark.parametrize("scheme", [zf.ZF_FLOAT2INT, zf.ZF_RAW])
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c[0])
+def test_float_decode_equals_oracle(gpu, scheme, case):
+    name, x, cr = case
+    h = compress(x, scheme, cr)
+    try:
+        for resident in (False, True):
+            got, = gpu.decode([h], out_specs(x), resident=resident)
+            ref = oracle.decode(zf.zf_compressed_bytes(h))
+            assert np.array_equal(_bits(ref), _bits(x))
+            assert np.array_equal(_bits(got), _bits(ref)), (name, resident)
+    finally:
+        zf.zf_compressed_free(h)
+
+
+def test_oracle_encoded_float2int_on_gpu(gpu):
+    for name, x, cr in CASES:
+        h = zf.zf_compressed_from_bytes(oracle.encode(x, oracle.FLOAT2INT, cr))
+        got, = gpu.decode([h], out_specs(x))
+        zf.zf_compressed_free(h)
+        assert np.array_equal(_bits(got), _bits(x)), name
+
+
+def test_float2int_in_batched_and_mixed_calls():
+    cols = [(CASES[0][1], zf.ZF_FLOAT2INT), (W.sorted_keys(5, 200_000), zf.ZF_DELTA_BP),
+            (CASES[3][1], zf.ZF_FLOAT2INT), (W.dates_rle(5, 100_000), zf.ZF_RLE)]
+    handles = [compress(x, s, 32768) for x, s in cols]
+    specs = [sp for x, s in cols for sp in out_specs(x)]
+    try:
+        for flags in (0, zf.ZF_KCFG_BATCHED, zf.ZF_KCFG_BATCHED | zf.ZF_KCFG_GRAPH):
+            g = Gpu(stage_bytes=1 << 20, flags=flags)
+            try:
+                for rep in range(2):
+                    got = g.decode(handles, specs)
+                    for (x, s), y in zip(cols, got):
+                        assert np.array_equal(y.view(np.uint8), x.view(np.uint8)), (flags, s, rep)
+            finally:
+                g.close()
+    finally:
+        for h in handles:
+            zf.zf_compressed_free(h)
+
+
+def test_float2int_full_size_column(gpu):
+    """64M prices in 1M-row chunks: the whole column bit for bit, and sampled
+    chunks against the oracle's own decode of the library's bytes."""
+    x = W.decimal_prices(1, 7, 0, 1 << 26)
+    h = compress(x, zf.ZF_FLOAT2INT, 1 << 20)
+    try:
+        got, = gpu.decode([h], out_specs(x))
+        assert np.array_equal(_bits(got), _bits(x))
+        b = zf.zf_compressed_bytes(h)
+        orc = oracle.default()
+        for c in (0, 17, 63):
+            off, ln, r0, rows = orc.chunk_span(b, c)
+            ref = orc.decode_chunk(b[off:off + ln], np.float64)
+            assert np.array_equal(_bits(ref), _bits(got[r0:r0 + rows]))
+    finally:
+        zf.zf_compressed_free(h)

@@ -130,3 +130,55 @@ def test_plan_heuristic_picks_the_obvious_scheme():
     assert pick(W.dict_codes(1, 3, 0, 200000)) == zf.ZF_DICT_BP
     with pytest.raises(zf.ZfError):
         zf.zf_plan(None, zf.Column(np.zeros(10, np.int32)), scheme=zf.ZF_FOR_BP, chunk_rows=1000)
+
+
+def _float_cases():
+    rng = np.random.default_rng(31)
+    prices = W.decimal_prices(3, 5, 0, 100_000)
+    mixed = prices[:20_000].copy()
+    mixed[::997] = np.nan
+    mixed[5::1999] = np.inf
+    mixed[7::2999] = -0.0
+    mixed[11::3001] = 1.0 / 3.0
+    yield "prices_2dp", prices, 32768
+    yield "prices_3dp", W.decimal_prices(4, 5, 0, 50_000, 3), 16384
+    yield "integers", rng.integers(-10**12, 10**12, 30_000).astype(np.float64), 8192
+    yield "mixed_exceptions", mixed, 4096
+    yield "random_doubles", rng.standard_normal(9_000), 4096
+    yield "one_row", np.array([12.5]), 1024
+    yield "empty", np.zeros(0, np.float64), 1024
+
+
+FLOAT_CASES = list(_float_cases())
+
+
+@pytest.mark.parametrize("scheme", ["raw", "float2int"])
+@pytest.mark.parametrize("case", FLOAT_CASES, ids=lambda c: c[0])
+def test_float2int_encoder_bytes_equal_oracle(scheme, case):
+    """Float2Int is canonical (exponent with the fewest exceptions, smallest
+    on a tie): the library writes the oracle's bytes, and both decode to the
+    column bit for bit."""
+    name, x, cr = case
+    s = oracle.SCHEMES[scheme]
+    ob = oracle.encode(x, s, cr)
+    lb = lib_encode(x, s, cr)
+    assert lb == ob
+    assert np.array_equal(oracle.decode(lb).view(np.uint64), x.view(np.uint64))
+
+
+def test_float2int_plan_and_validation():
+    x = W.decimal_prices(1, 5, 0, 5000)
+    p = zf.zf_plan(None, zf.Column(x))
+    assert p.scheme == zf.ZF_FLOAT2INT
+    with pytest.raises(zf.ZfError):               # integer schemes do not take doubles
+        lib_encode(x, zf.ZF_FOR_BP, 1024)
+    b = lib_encode(np.array([1.5, np.nan, 2.25, np.inf]), zf.ZF_FLOAT2INT, 1024)
+    off, ln, r0, rows, ch = chunks_of(oracle.default(), b)[0]
+    assert ch["n_aux"] == 2
+    # exception rows out of order are rejected by the host check
+    bad = bytearray(b)
+    p1 = off + ch["offs"][1]
+    bad[p1:p1 + 8] = struct.pack("<II", 3, 1)
+    with pytest.raises(zf.ZfError) as e:
+        zf.zf_compressed_from_bytes(bytes(bad))
+    assert e.value.status == zf.ZF_ECORRUPT

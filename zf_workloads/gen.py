@@ -6,7 +6,7 @@ import numpy as np
 __all__ = [
     "splitmix64", "hash_u64", "uniform_int", "uniform_unit",
     "geometric_gaps", "sorted_keys", "run_lengths_geometric", "dates_rle",
-    "zipf_cdf", "zipf_ranks", "vocabulary", "text_column", "lognormal_cents",
+    "zipf_cdf", "zipf_ranks", "vocabulary", "text_column", "lognormal_cents", "decimal_prices",
     "dict_codes", "rle_distribution", "DATE_LO", "DATE_HI", "parallel_rows", "FACT_COLUMNS", "fact_column",
     "fact_pieces", "SELECTOR_FAMILIES", "selector_column",
 ]
@@ -246,6 +246,13 @@ def lognormal_cents(seed: int, stream: int, start: int, n: int, mu: float = 11.5
     z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
     v = np.rint(np.exp(mu + sigma * z))
     return np.clip(v, 1, (1 << 40) - 1).astype(np.int64)
+
+
+def decimal_prices(seed: int, stream: int, start: int, n: int, decimals: int = 2) -> np.ndarray:
+    """float64 prices with ``decimals`` digits after the point: log-normal
+    cents (lognormal_cents) divided by 10**decimals, i.e. the double nearest
+    each decimal value, as parsing its text would give."""
+    return lognormal_cents(seed, stream, start, n) / float(10 ** decimals)
 
 
 def dict_codes(seed: int, stream: int, start: int, n: int, ndistinct: int = 25, zipf_s: float = 1.1) -> np.ndarray:
