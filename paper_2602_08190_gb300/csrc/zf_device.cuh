@@ -186,6 +186,21 @@ __host__ __device__ inline uint32_t stage_bytes_for(uint32_t bmax) { return ((kW
 // ---------------------------------------------------------------- Fully-Parallel
 // Extract and store the rows of a staged FOR/dictionary warp tile; returns
 // true if a dictionary code was out of range.
+// The double of an integer d, exactly when |d| < 2^53, built with integer
+// instructions (sign, the leading bit's position as exponent, the bits below
+// it as fraction): the FP64 pipe -- a small part of a GB300 SM -- is left to
+// the multiply and the two fused multiply-adds.  Larger magnitudes (only in
+// malformed streams) take the rounding conversion.
+__device__ __forceinline__ double exact_i2d(long long d) {
+    const unsigned long long a = d < 0 ? 0ull - (unsigned long long)d : (unsigned long long)d;
+    if (a >= (1ull << 53)) return __ll2double_rn(d);
+    if (a == 0) return 0.0;
+    const int lz = __clzll((long long)a);
+    const unsigned long long bits = ((unsigned long long)(d < 0) << 63) |
+                                    ((unsigned long long)(1023 + 63 - lz) << 52) | (((a << lz) << 1) >> 12);
+    return __longlong_as_double((long long)bits);
+}
+
 // FLOAT2INT (T = int64 bits of the doubles): the integer d = reference + u
 // becomes q + r * 10^-e, q = d * 10^-e, r = d - q * 10^e (p10 = 10^e,
 // inv10 = the double nearest 10^-e).
@@ -214,7 +229,7 @@ __device__ __forceinline__ bool fp_rows(const ZfDevChunk& c, const Hdr& h, T* ds
             if constexpr (SCHEME == ZF_FOR_BP) {
                 v[k] = (T)(ref + (T)u[k]);
             } else if constexpr (SCHEME == ZF_FLOAT2INT) {
-                const double x = __ll2double_rn((long long)(h.ref + u[k]));
+                const double x = exact_i2d((long long)(h.ref + u[k]));
                 const double q = __dmul_rn(x, inv10);
                 v[k] = (T)__double_as_longlong(__fma_rn(__fma_rn(-q, p10, x), inv10, q));
             } else {
