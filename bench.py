@@ -187,6 +187,22 @@ def oracle_sample(handles, dtypes, budget_s: float, threads: int = 1):
                               f"{threads} host thread{'s' if threads > 1 else ''}")
 
 
+def max_over_ranks(values, dist, device: str):
+    """Each value's largest over the ranks: the slowest rank sets the whole
+    job's time.  Unchanged on a single process (dist None)."""
+    if not dist:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_gbs(total_bytes: float, ms: float) -> float:
+    """GB/s of `total_bytes` (every rank's bytes) over the job's time."""
+    return total_bytes / (ms * 1e-3) / 1e9
+
+
 def host_threads() -> int:
     return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
 
@@ -686,12 +702,9 @@ def main():
     t_dev = float(np.mean(dev_ms))
     t_e2e = float(np.mean(e2e_ms))
     t_kern = float(np.mean(kern_ms))
-    if dist:
-        t = torch.tensor([t_dev, t_e2e, t_kern], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_dev, t_e2e, t_kern = t.tolist()
-    value = world * raw / (t_dev * 1e-3) / 1e9
-    e2e = world * raw / (t_e2e * 1e-3) / 1e9
+    t_dev, t_e2e, t_kern = max_over_ranks([t_dev, t_e2e, t_kern], dist, "cuda")
+    value = whole_job_gbs(world * raw, t_dev)
+    e2e = whole_job_gbs(world * raw, t_e2e)
     hbm, peak_kind = peaks()
     kern_bytes = comp_k + raw_k
     achieved = kern_bytes / (t_kern * 1e-3) / 1e9
