@@ -185,6 +185,18 @@ __device__ void lz_block(const ZfDevChunk& c, uint32_t* lr, uint8_t* win, uint32
             // window byte x holds output byte op + x - a; base + x is its global address
             const uint32_t a = (uint32_t)(reinterpret_cast<uintptr_t>(dst + op) & 15);
             uint8_t* base = dst + op - a;
+            // the bytes of each match whose source precedes the batch: aligned
+            // words over [src, src + g) -- the last ends before op + 3, inside
+            // the block, because this match still has ml >= 4 bytes from
+            // mpos >= op.  The first four words are loaded here, so that their
+            // latency overlaps the literals' loads.
+            const uint32_t d = a + mpos - op;
+            const uint32_t g = (has_m && src < op) ? min(min(ml, off), op - src) : 0;
+            const uint32_t sh = src & 3u, nw = g ? (sh + g + 3) >> 2 : 0;
+            const uint32_t* ws = reinterpret_cast<const uint32_t*>(dst + (src - sh));
+            uint32_t x[4];
+#pragma unroll
+            for (uint32_t q = 0; q < 4; q++) x[q] = q < nw ? ws[q] : 0;
             for (uint32_t bl = 0; bl < lb; bl += 128) {
                 uint32_t v[4];
 #pragma unroll
@@ -201,27 +213,18 @@ __device__ void lz_block(const ZfDevChunk& c, uint32_t* lr, uint8_t* win, uint32
                     if (j < lp + lb) win[a + os - op + (j - ls)] = (uint8_t)v[q];
                 }
             }
-            // the bytes of each match whose source precedes the batch
-            const uint32_t d = a + mpos - op;
-            const uint32_t g = (has_m && src < op) ? min(min(ml, off), op - src) : 0;
-            if (g) {
-                // aligned words over [src, src + g): the last ends before op + 3,
-                // inside the block, because this match still has ml >= 4 bytes
-                // from mpos >= op
-                const uint32_t sh = src & 3u, nw = (sh + g + 3) >> 2;
-                const uint32_t* ws = reinterpret_cast<const uint32_t*>(dst + (src - sh));
-                for (uint32_t w0 = 0; w0 < nw; w0 += 4) {
-                    uint32_t x[4];
+            for (uint32_t w0 = 0; w0 < nw; w0 += 4) {
+                if (w0) {
 #pragma unroll
                     for (uint32_t q = 0; q < 4; q++) x[q] = w0 + q < nw ? ws[w0 + q] : 0;
-#pragma unroll
-                    for (uint32_t q = 0; q < 4; q++)
-#pragma unroll
-                        for (uint32_t b = 0; b < 4; b++) {
-                            const uint32_t kb = 4 * (w0 + q) + b;
-                            if (kb >= sh && kb < sh + g) win[d + kb - sh] = (uint8_t)(x[q] >> (8 * b));
-                        }
                 }
+#pragma unroll
+                for (uint32_t q = 0; q < 4; q++)
+#pragma unroll
+                    for (uint32_t b = 0; b < 4; b++) {
+                        const uint32_t kb = 4 * (w0 + q) + b;
+                        if (kb >= sh && kb < sh + g) win[d + kb - sh] = (uint8_t)(x[q] >> (8 * b));
+                    }
             }
             __syncwarp();
             // the rest, in token order, inside the window
