@@ -654,38 +654,59 @@ __device__ void delta_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32
 
 // ---------------------------------------------------------------- RLE (Group-Parallel)
 // Expansion of one 1024-row tile whose runs [rf, rf+m) have their lengths at
-// `lens` and values at `vals` (staged in shared memory, or in global memory
-// when the tile has more runs than a staging buffer holds).  `bm` is the
-// warp's 32-word bitmask of the tile's rows.
+// `lens_al` + sft, lens_al 16-byte aligned and sft = rf mod 4 (staged in shared
+// memory, or in global memory when the tile has more runs than a staging
+// buffer holds), and their values at `vals`.  `bm` is the warp's 32-word
+// bitmask of the tile's rows.
 template <class T, bool WS>
-__device__ __forceinline__ void rle_rows(const ZfDevChunk& c, const Hdr& h, T* dst, const uint32_t* lens,
-                                         const T* vals, uint32_t* bm, uint32_t m, uint32_t skip, uint32_t nr,
-                                         bool last_tile, uint32_t next_skip, uint32_t lane, uint32_t* err) {
+__device__ __forceinline__ void rle_rows(const ZfDevChunk& c, const Hdr& h, T* dst, const uint32_t* lens_al,
+                                         uint32_t sft, const T* vals, uint32_t* bm, uint32_t m, uint32_t skip,
+                                         uint32_t nr, bool last_tile, uint32_t next_skip, uint32_t lane,
+                                         uint32_t* err) {
     bm[lane] = 0;
     __syncwarp();
-    // presum: start row of each run relative to the tile, 32 runs per step;
-    // every run but the first sets the bit of its start row.  Lengths are at
-    // most the chunk's rows (< 2^30), and only the first and last run of a
-    // tile can be longer than the tile, so 32-bit sums hold.
+    // presum, 128 length entries per step: lane l reads entries 4l..4l+3 with
+    // one 16-byte load (entry sft is the tile's first run), one warp scan of
+    // the lanes' sums gives each run its start row relative to the first
+    // run's start, and every run but the first sets the bit of its start row.
+    // Lengths are at most the chunk's rows (< 2^30), and only the first and
+    // last run of a tile can be longer than the tile, so 32-bit sums hold.
     bool bad = false;
     uint32_t end = 0;                 // rows covered so far, counted from the first run's start
-    uint32_t first_len = 0, last_start = 0;
-    for (uint32_t g = 0; g < m; g += 32) {
-        const uint32_t i = g + lane;
-        const uint32_t L = i < m ? lens[i] : 0u;
-        bad |= i < m && (L == 0 || L > h.rows);
-        const uint32_t incl = warp_incl_sum<uint32_t>(L, lane);
-        const uint32_t start = end + incl - L;   // relative to the first run's start
-        if (i < m && i > 0 && start >= skip && start - skip < nr) {
-            const uint32_t r = start - skip;
-            atomicOr(&bm[r >> 5], 1u << (r & 31));
+    uint32_t first_len = 0, my_last = 0;
+    const uint32_t n = sft + m;       // entries from the aligned start
+    for (uint32_t g = 0; g < n; g += 128) {
+        const uint32_t k0 = g + 4 * lane;
+        const uint4 q = k0 < n ? reinterpret_cast<const uint4*>(lens_al)[k0 >> 2] : make_uint4(0, 0, 0, 0);
+        uint32_t L[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const uint32_t k = k0 + e;
+            const bool valid = k >= sft && k < n;
+            if (!valid) L[e] = 0;
+            bad |= valid && (L[e] == 0 || L[e] > h.rows);
         }
-        if (g == 0) first_len = __shfl_sync(0xFFFFFFFFu, L, 0);
-        const uint32_t ls = __shfl_sync(0xFFFFFFFFu, start, (m - 1 - g) & 31);
-        if (m - 1 - g < 32) last_start = ls;
+        const uint32_t s4 = L[0] + L[1] + L[2] + L[3];
+        const uint32_t incl = warp_incl_sum<uint32_t>(s4, lane);
+        uint32_t st = end + incl - s4;  // start of entry k0
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const uint32_t k = k0 + e;
+            if (k > sft && k < n && st >= skip && st - skip < nr) {
+                const uint32_t r = st - skip;
+                atomicOr(&bm[r >> 5], 1u << (r & 31));
+            }
+            if (k + 1 == n) my_last = st;
+            st += L[e];
+        }
+        if (g == 0) {
+            const uint32_t f0 = sft == 0 ? L[0] : sft == 1 ? L[1] : sft == 2 ? L[2] : L[3];
+            first_len = __shfl_sync(0xFFFFFFFFu, f0, 0);   // run 0: entry sft of lane 0
+        }
         end += __shfl_sync(0xFFFFFFFFu, incl, 31);
         if (end > 2u * (1u << 30) + 2048u) bad = true;
     }
+    const uint32_t last_start = __shfl_sync(0xFFFFFFFFu, my_last, ((n - 1) & 127) >> 2);
     // The runs cover exactly [0, nr): the first starts at or before row 0, the
     // last ends at nr or continues into the next tile by the directory's amount.
     bool ok = skip < first_len && end >= skip;
@@ -734,6 +755,7 @@ __device__ __forceinline__ void rle_rows(const ZfDevChunk& c, const Hdr& h, T* d
 }
 
 constexpr uint32_t kRleStageRuns = 256;   // runs per staging buffer
+constexpr uint32_t kRleStages = 2;        // staging buffers per warp: tile i+1 loads while tile i expands
 
 // Shared memory of one RLE staging buffer: lengths then values, each with
 // room for the 16-byte aligned copy that starts up to 3 entries early.
@@ -787,7 +809,7 @@ __device__ void rle_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t
         if (m && m <= kRleStageRuns) {
             // 16-byte copies from the aligned entries at or before rf (the
             // sections are 16-byte aligned and padded, so they stay inside)
-            uint8_t* b = bufs + (i & 1) * bb;
+            uint8_t* b = bufs + (i % kRleStages) * bb;
             const uint32_t l0 = rf & ~3u, nl = (rf + m - l0 + 3) / 4;
             const uint32_t v0 = rf & ~(VPER - 1), nv = (rf + m - v0 + VPER - 1) / VPER;
             for (uint32_t k = lane; k < nl; k += 32)
@@ -797,13 +819,17 @@ __device__ void rle_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t
         }
         __pipeline_commit();
     };
-    issue(0);
+    // The next kRleStages - 1 tiles are staged while a tile expands (one
+    // commit group per tile, empty ones included).  Deeper staging (four
+    // buffers) measured slower on GB300: it costs occupancy.
+    for (uint32_t i = 0; i + 1 < kRleStages && i < nt; i++) issue(i);
     for (uint32_t i = 0; i < nt; i++) {
-        if (i + 1 < nt) {
-            issue(i + 1);
-            __pipeline_wait_prior(1);
-        } else {
-            __pipeline_wait_prior(0);
+        if (i + kRleStages - 1 < nt) issue(i + kRleStages - 1);
+        switch (min(nt - 1, i + kRleStages - 1) - i) {   // groups committed after tile i's
+        case 0: __pipeline_wait_prior(0); break;
+        case 1: __pipeline_wait_prior(1); break;
+        case 2: __pipeline_wait_prior(2); break;
+        default: __pipeline_wait_prior(3); break;
         }
         __syncwarp();
         uint32_t rf, skip, m, ns;
@@ -815,12 +841,13 @@ __device__ void rle_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t
         } else {
             T* dst = reinterpret_cast<T*>(c.dst) + rr;
             if (m <= kRleStageRuns) {
-                const uint8_t* b = bufs + (i & 1) * bb;
-                rle_rows<T, WS>(c, h, dst, reinterpret_cast<const uint32_t*>(b) + (rf & 3u),
+                const uint8_t* b = bufs + (i % kRleStages) * bb;
+                rle_rows<T, WS>(c, h, dst, reinterpret_cast<const uint32_t*>(b), rf & 3u,
                                 reinterpret_cast<const T*>(b + (kRleStageRuns + 4) * 4) + (rf & (VPER - 1)), bm, m,
                                 skip, nr, last, ns, lane, err);
             } else {
-                rle_rows<T, WS>(c, h, dst, lens + rf, vals + rf, bm, m, skip, nr, last, ns, lane, err);
+                rle_rows<T, WS>(c, h, dst, lens + (rf & ~3u), rf & 3u, vals + rf, bm, m, skip, nr, last, ns, lane,
+                                err);
             }
         }
         __syncwarp();
@@ -851,7 +878,7 @@ __host__ __device__ inline uint32_t warp_smem(int scheme, uint32_t value_bytes, 
     switch (scheme) {
     case ZF_FOR_BP: case ZF_DICT_BP: case ZF_FLOAT2INT: return 2 * stage_bytes_for(bmax);
     case ZF_DELTA_BP: return 2 * stage_bytes_for(bmax) + 4096;   // + the store transpose buffer
-    case ZF_RLE: return 128 + 2 * rle_buf_bytes(value_bytes);   // row bitmask + two staging buffers
+    case ZF_RLE: return 128 + kRleStages * rle_buf_bytes(value_bytes);   // row bitmask + staging buffers
     }
     return 0;
 }

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -52,8 +53,13 @@ struct zf_ctx {
     uint64_t slot_cap = 0;
     cudaEvent_t ev_copied[kMaxSlots] = {}, ev_free[kMaxSlots] = {};
     cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;
-    uint32_t* d_err = nullptr;     // [0] status bits, [1] first failing chunk, [2 + 2s, 3 + 2s] work queue of stream s
-    uint32_t* h_err = nullptr;     // pinned copy of d_err[0..1]
+    uint32_t* d_err = nullptr;     // [2 + 2s, 3 + 2s]: work queue of decode stream s
+    // The decoders' error word, [0] status bits and [1] first failing chunk, in
+    // mapped pinned host memory: the host resets it before a call and reads it
+    // after the call's last event, and the kernels write it only when a stream
+    // is malformed -- no memset or read-back rides on the streams.
+    uint32_t* h_err = nullptr;
+    uint32_t* d_errw = nullptr;    // the device address of h_err
     ZfDevChunk* d_desc = nullptr;
     ZfDevChunk* h_desc = nullptr;  // pinned
     size_t desc_cap = 0;
@@ -254,11 +260,11 @@ zf_status launch_groups(zf_ctx* ctx, const std::vector<Group>& groups, const ZfD
         const ZfDevChunk* dchunks = d_desc + g.first;
         cudaError_t e;
         if (g.scheme == ZF_LZ77) {
-            e = zf::launch_lz(dchunks, g.count, ctx->d_err, ctx->num_sms, stream);
+            e = zf::launch_lz(dchunks, g.count, ctx->d_errw, ctx->num_sms, stream);
         } else {
             uint32_t smem = ((g.warp_smem + 15) & ~15u) * (k.threads / 32);
             zf::TileLaunch L{dchunks, g.count, g.ntiles, g.scheme, g.dtype, g.tile_rows, k.threads,
-                             k.ctas_per_sm, smem, ctx->num_sms, ctx->d_err, queue};
+                             k.ctas_per_sm, smem, ctx->num_sms, ctx->d_errw, queue};
             e = zf::launch_tiles(L, stream);
         }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "decode launch");
@@ -318,11 +324,14 @@ zf_status begin_call(zf_ctx* ctx) {
     ZF_CU(ctx, cudaSetDevice(ctx->device));
     ctx->st = zf_stats{};
     ctx->host_err = ZF_OK;
+    // the previous call has finished (zf_sync), so no kernel writes the word now
+    reinterpret_cast<volatile uint32_t*>(ctx->h_err)[0] = 0;
+    reinterpret_cast<volatile uint32_t*>(ctx->h_err)[1] = 0xFFFFFFFFu;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
     return ZF_OK;
 }
 
 zf_status finish_enqueue(zf_ctx* ctx) {
-    ZF_CU(ctx, cudaMemcpyAsync(ctx->h_err, ctx->d_err, 8, cudaMemcpyDeviceToHost, ctx->compute));
     ZF_CU(ctx, cudaEventRecord(ctx->ev_t1, ctx->compute));
     ctx->busy = true;
     return ZF_OK;
@@ -366,10 +375,10 @@ zf_status zf_ctx_create(int device, void* copy_stream, void* compute_stream, zf_
         return fail(ZF_ECUDA);
     if (cudaMalloc(&ctx->d_err, 128) != cudaSuccess || cudaMemset(ctx->d_err, 0, 128) != cudaSuccess)
         return fail(ZF_ENOMEM);
-    uint32_t init[2] = {0, 0xFFFFFFFFu};
-    if (cudaMemcpy(ctx->d_err, init, 8, cudaMemcpyHostToDevice) != cudaSuccess) return fail(ZF_ECUDA);
-    if (cudaHostAlloc(&ctx->h_err, 64, cudaHostAllocDefault) != cudaSuccess) return fail(ZF_ENOMEM);
+    if (cudaHostAlloc(&ctx->h_err, 64, cudaHostAllocMapped) != cudaSuccess) return fail(ZF_ENOMEM);
     memset(ctx->h_err, 0, 64);
+    ctx->h_err[1] = 0xFFFFFFFFu;
+    if (cudaHostGetDevicePointer((void**)&ctx->d_errw, ctx->h_err, 0) != cudaSuccess) return fail(ZF_ECUDA);
     *out = ctx;
     return ZF_OK;
 }
@@ -651,8 +660,6 @@ zf_status zf_transfer_decompress(zf_ctx* ctx, const zf_compressed* const* cols, 
     // the error word and the descriptors go first on the copy stream: an H2D
     // copy on another stream can queue behind the stage copies on the same
     // copy engine and hold every decode back
-    ZF_CAP(cudaMemsetAsync(ctx->d_err, 0, 4, ctx->copy));
-    ZF_CAP(cudaMemsetAsync(ctx->d_err + 1, 0xFF, 4, ctx->copy));
     if (!desc.empty())
         ZF_CAP(cudaMemcpyAsync(d_desc, h_desc, desc.size() * sizeof(ZfDevChunk), cudaMemcpyHostToDevice, ctx->copy));
     if (stages.empty()) ZF_CAP(cudaEventRecord(ctx->ev_copied[0], ctx->copy));
@@ -670,7 +677,6 @@ zf_status zf_transfer_decompress(zf_ctx* ctx, const zf_compressed* const* cols, 
     }
     for (size_t q = 0; q < std::min<size_t>(ctx->nslots, stages.size()); q++)
         ZF_CAP(cudaStreamWaitEvent(ctx->compute, ctx->ev_free[q], 0));
-    ZF_CAP(cudaMemcpyAsync(ctx->h_err, ctx->d_err, 8, cudaMemcpyDeviceToHost, ctx->compute));
 #undef ZF_CAP
     ctx->st.raw_bytes = raw;
     ctx->st.comp_bytes = comp;
@@ -718,11 +724,12 @@ zf_status zf_sync(zf_ctx* ctx, zf_stats* stats) {
     float ms = 0;
     cudaEventElapsedTime(&ms, ctx->ev_t0, ctx->ev_t1);
     ctx->st.total_ms = ms;
-    ctx->st.device_error = ctx->h_err[0];
+    const uint32_t bits = reinterpret_cast<volatile uint32_t*>(ctx->h_err)[0];
+    const uint32_t bad_chunk = reinterpret_cast<volatile uint32_t*>(ctx->h_err)[1];
+    ctx->st.device_error = bits;
     if (stats) *stats = ctx->st;
-    if (ctx->h_err[0]) {
-        uint32_t bits = ctx->h_err[0];
-        ctx->last_error = "device decoder reported an error in chunk " + std::to_string(ctx->h_err[1]);
+    if (bits) {
+        ctx->last_error = "device decoder reported an error in chunk " + std::to_string(bad_chunk);
         if (bits & (1u << ZF_ECORRUPT)) return ZF_ECORRUPT;
         if (bits & (1u << ZF_ETIMEOUT)) return ZF_ETIMEOUT;
         return ZF_EINVAL;
@@ -782,8 +789,6 @@ zf_status zf_decompress_resident(zf_ctx* ctx, const zf_resident* const* cols, ui
     std::vector<Group> groups;
     build_groups(work, 0, work.size(), k, desc, groups);
     ZF_CU(ctx, cudaEventRecord(ctx->ev_t0, ctx->compute));
-    ZF_CU(ctx, cudaMemsetAsync(ctx->d_err, 0, 4, ctx->compute));
-    ZF_CU(ctx, cudaMemsetAsync(ctx->d_err + 1, 0xFF, 4, ctx->compute));
     bool same = desc.size() == ctx->resident_cache.size() &&
                 (desc.empty() || memcmp(desc.data(), ctx->resident_cache.data(), desc.size() * sizeof(ZfDevChunk)) == 0);
     if (!same) {
