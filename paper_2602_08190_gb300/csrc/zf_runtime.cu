@@ -801,9 +801,27 @@ zf_status zf_decompress_resident(zf_ctx* ctx, const zf_resident* const* cols, ui
         }
         ctx->resident_cache = desc;
     }
-    st = launch_groups(ctx, groups, ctx->d_desc, k, ctx->compute, ctx->d_err + 2);
+    if (groups.size() <= 1) {
+        st = launch_groups(ctx, groups, ctx->d_desc, k, ctx->compute, ctx->d_err + 2);
+    } else {
+        // one launch per (scheme, dtype) group, each on its own decode stream,
+        // so a launch's tail overlaps the next launch's start
+        ZF_CU(ctx, cudaEventRecord(ctx->ev_fork, ctx->compute));
+        const size_t nl = std::min<size_t>(groups.size(), ctx->nslots);
+        for (size_t q = 0; q < nl; q++) ZF_CU(ctx, cudaStreamWaitEvent(ctx->lane[q], ctx->ev_fork, 0));
+        for (size_t gi = 0; gi < groups.size() && st == ZF_OK; gi++) {
+            const size_t q = gi % nl;
+            st = launch_groups(ctx, std::vector<Group>{groups[gi]}, ctx->d_desc, k, ctx->lane[q],
+                               ctx->d_err + 2 + 2 * q);
+        }
+        for (size_t q = 0; q < nl; q++) {
+            ZF_CU(ctx, cudaEventRecord(ctx->ev_free[q], ctx->lane[q]));
+            ZF_CU(ctx, cudaStreamWaitEvent(ctx->compute, ctx->ev_free[q], 0));
+        }
+    }
     if (st) {
         cudaStreamSynchronize(ctx->compute);
+        for (uint32_t q = 0; q < ctx->nslots; q++) cudaStreamSynchronize(ctx->lane[q]);
         return st;
     }
     ctx->st.raw_bytes = raw;
