@@ -8,20 +8,24 @@
 // into shared memory (cp.async, double-buffered) while it decodes the
 // current tile, so DRAM latency overlaps the decode.  The decoders follow
 // the parallel patterns of Section 3.1:
-//   fp_warp     Fully-Parallel: FOR / dictionary / raw.  The warp stages the
-//               tile's packed words in shared memory with coalesced 16-byte
-//               loads, then every lane extracts C = 16/sizeof(T) consecutive
-//               values with funnel shifts and writes them with one 16-byte
-//               store (128 or 64 rows per warp step, coalesced).
-//   delta_warp  Group-Parallel: one 1024-row delta block per warp tile, in
-//               rows of 128 values: 4 per lane, a lane-local prefix, a warp
-//               shuffle scan, and base + j*min_d added on the way out.
-//   rle_warp    Group-Parallel: the tile's runs (the chunk's 1024-row
-//               directory names the first) have their lengths scanned by warp
-//               shuffles into start rows (the presum of Section 3.2); each run
-//               start marks its row in shared memory and a running max over
-//               the rows gives every row its run.  Each tile writes exactly
-//               1024 rows, so long and short runs balance.
+//   fp_job      Fully-Parallel: FOR / dictionary / Float2Int / raw.  Every
+//               lane extracts C = 16/sizeof(T) consecutive values of the
+//               staged bits with funnel shifts and writes them with one
+//               16-byte store (coalesced).  Float2Int makes each integer a
+//               double (an integer-built conversion, one multiply, two fused
+//               multiply-adds) and then patches the chunk's exceptions.
+//   delta_job   Group-Parallel: one 1024-row block per step.  Lane l owns
+//               values [32l, 32l+32): it sums its differences, one warp
+//               shuffle scan gives every lane its offset, the values are
+//               rebuilt from a second read of the differences and leave
+//               through a shared-memory transpose, four lanes per 128-byte line.
+//   rle_job     Group-Parallel: the tile's run lengths (the chunk's 1024-row
+//               directory names the first run) are scanned into start rows,
+//               four per lane and one warp shuffle scan per 128 runs (the
+//               presum of Section 3.2); every run but the first sets its start
+//               row's bit in a 32-word bitmask, and a row's run is the number
+//               of set bits at or before it.  Each tile writes exactly 1024
+//               rows, so long and short runs balance.
 // A failed check of the stream sets a bit in the launch's error word; the
 // tile then writes in-bounds placeholder values.  Nothing traps.
 #pragma once
@@ -74,16 +78,6 @@ __device__ __forceinline__ uint64_t extract(const uint32_t* sm, uint32_t bitpos,
     uint32_t hi = __funnelshift_r(w1, sm[w + 2], sh);
     uint64_t v = ((uint64_t)hi << 32) | lo;
     return b == 64 ? v : (v & ((1ull << b) - 1ull));
-}
-
-// The warp copies `nbytes` from a 16-byte aligned global address into its
-// shared-memory slice, 16 bytes per lane per step, then zeroes 32 bytes after.
-__device__ __forceinline__ void warp_stage(uint32_t* wsm, const uint8_t* src, uint32_t nbytes, uint32_t lane) {
-    uint32_t nvec = (nbytes + 15) >> 4;
-    uint4* s4 = reinterpret_cast<uint4*>(wsm);
-    for (uint32_t i = lane; i < nvec; i += 32) s4[i] = ldg16(src + 16ull * i);
-    if (lane < 2) s4[nvec + lane] = make_uint4(0, 0, 0, 0);
-    __syncwarp();
 }
 
 // One 256-bit store of four 64-bit words to a 32-byte aligned global address:
@@ -142,15 +136,6 @@ __device__ __forceinline__ S warp_incl_sum(S x, uint32_t lane) {
     for (int d = 1; d < 32; d <<= 1) {
         S y = __shfl_up_sync(0xFFFFFFFFu, x, d);
         if (lane >= (uint32_t)d) x += y;
-    }
-    return x;
-}
-
-__device__ __forceinline__ uint32_t warp_incl_max(uint32_t x, uint32_t lane) {
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
-        if (lane >= (uint32_t)d) x = max(x, y);
     }
     return x;
 }
@@ -343,94 +328,6 @@ __device__ void fp_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t 
 }
 
 // ---------------------------------------------------------------- delta (Group-Parallel)
-// One 1024-row block: x_j = base + j*min_d + sum_{k=1..j} u_k (mod 2^width).
-template <class T, class S, bool NARROW>
-__device__ __forceinline__ void delta_rows(T* dst, const uint32_t* wsm, uint32_t mk, uint32_t b, uint64_t base,
-                                           uint64_t min_d, uint32_t lane, bool al32) {
-    using U = typename std::conditional<sizeof(T) == 8, unsigned long long, unsigned int>::type;
-    U acc = 0;
-    const U md = (U)min_d;
-    U t = (U)base + (U)(lane * 4) * md;          // base + j0 * min_d, advanced by 128 * min_d per row
-    const U row_step = (U)128 * md;
-    for (uint32_t row = 0; row * 128 < mk; row++) {
-        const uint32_t j0 = row * 128 + lane * 4;
-        S u[4];
-        extract4<NARROW, S>(wsm, j0 * b, b, u);
-        if (j0 == 0) u[0] = 0;                    // slot 0 carries no difference
-        if (j0 + 4 > mk) {
-#pragma unroll
-            for (int k = 0; k < 4; k++)
-                if (j0 + k >= mk) u[k] = 0;
-        }
-        S s1 = u[0] + u[1], s2 = s1 + u[2], s3 = s2 + u[3];
-        S incl = warp_incl_sum<S>(s3, lane);
-        S tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        U x0 = t + acc + (U)(incl - s3) + (U)u[0];
-        T out[4];
-        out[0] = (T)x0;
-        out[1] = (T)(x0 + md + (U)(s1 - u[0]));
-        out[2] = (T)(x0 + 2 * md + (U)(s2 - u[0]));
-        out[3] = (T)(x0 + 3 * md + (U)(s3 - u[0]));
-        if (j0 + 4 <= mk) store_vec<T, 4>(dst + j0, out, al32);
-        else
-            for (uint32_t k = 0; j0 + k < mk; k++) dst[j0 + k] = out[k];
-        acc += (U)tot;
-        t += row_step;
-    }
-}
-
-// b <= 8: two rows of 128 values per step.  A lane's four differences sum to
-// at most 4 * 255 and a row to at most 32,640 < 2^16, so both rows' lane sums
-// share one 32-bit word (row a low, row b high) and one shuffle scan.
-template <class T>
-__device__ __forceinline__ void delta_rows_pair(T* dst, const uint32_t* wsm, uint32_t mk, uint32_t b, uint64_t base,
-                                                uint64_t min_d, uint32_t lane, bool al32) {
-    using U = typename std::conditional<sizeof(T) == 8, unsigned long long, unsigned int>::type;
-    U acc = 0;
-    const U md = (U)min_d;
-    U t = (U)base + (U)(lane * 4) * md;
-    const U row_step = (U)128 * md;
-    for (uint32_t row = 0; row * 128 < mk; row += 2) {
-        const uint32_t ja = row * 128 + lane * 4, jb = ja + 128;
-        uint32_t ua[4], ub[4];
-        extract4<true, uint32_t>(wsm, ja * b, b, ua);
-        extract4<true, uint32_t>(wsm, jb * b, b, ub);
-        if (ja == 0) ua[0] = 0;
-        if (jb + 4 > mk) {
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                if (ja + k >= mk) ua[k] = 0;
-                if (jb + k >= mk) ub[k] = 0;
-            }
-        }
-        const uint32_t a1 = ua[0] + ua[1], a2 = a1 + ua[2], a3 = a2 + ua[3];
-        const uint32_t b1 = ub[0] + ub[1], b2 = b1 + ub[2], b3 = b2 + ub[3];
-        const uint32_t packed = a3 | (b3 << 16);
-        const uint32_t incl = warp_incl_sum<uint32_t>(packed, lane);
-        const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        const uint32_t excl = incl - packed;
-        const U xa = t + acc + (U)(excl & 0xFFFFu) + (U)ua[0];
-        const U xb = t + row_step + acc + (U)(tot & 0xFFFFu) + (U)(excl >> 16) + (U)ub[0];
-        T oa[4], ob[4];
-        oa[0] = (T)xa;
-        oa[1] = (T)(xa + md + (U)(a1 - ua[0]));
-        oa[2] = (T)(xa + 2 * md + (U)(a2 - ua[0]));
-        oa[3] = (T)(xa + 3 * md + (U)(a3 - ua[0]));
-        ob[0] = (T)xb;
-        ob[1] = (T)(xb + md + (U)(b1 - ub[0]));
-        ob[2] = (T)(xb + 2 * md + (U)(b2 - ub[0]));
-        ob[3] = (T)(xb + 3 * md + (U)(b3 - ub[0]));
-        if (ja + 4 <= mk) store_vec<T, 4>(dst + ja, oa, al32);
-        else
-            for (uint32_t k = 0; ja + k < mk; k++) dst[ja + k] = oa[k];
-        if (jb + 4 <= mk) store_vec<T, 4>(dst + jb, ob, al32);
-        else
-            for (uint32_t k = 0; jb + k < mk; k++) dst[jb + k] = ob[k];
-        acc += (U)(tot & 0xFFFFu) + (U)(tot >> 16);
-        t += 2 * row_step;
-    }
-}
-
 // Swizzle of the 16-byte chunks of a lane's 128-byte line in the transpose
 // buffer: x = 4a + c (a < 2, c < 4) -> 2c + a.  Eight consecutive lanes
 // writing chunk k land in eight different bank groups, and so do the eight
