@@ -115,9 +115,10 @@ typedef struct {
  * tiles of one chunk, staging the next tile while it decodes the current
  * one.  Zero fields take the built-in values. */
 typedef struct {
-    uint32_t tile_rows;       /* rows per warp job: a multiple of 1024, <= 16384 (0 = 2048 for
-                                 delta launches, 4096 for the others) */
-    uint32_t threads;         /* 128, 256 or 512 (default 128) */
+    uint32_t tile_rows;       /* rows per warp job: a multiple of 1024, <= 16384 (0 = the
+                                 class's tuned value, else 2048 for delta launches
+                                 and 4096 for the others) */
+    uint32_t threads;         /* 128, 256 or 512 (0 = the class's tuned value, else 128) */
     uint32_t ctas_per_sm;     /* batched launch: persistent grid = ctas_per_sm x SM count (0 = occupancy limit) */
     uint32_t stage_bytes;     /* pipeline stage: compressed bytes per H2D copy + decode step (default 64 MiB) */
     uint32_t flags;           /* ZF_KCFG_BATCHED: one work-queue launch per stage for all schemes
@@ -240,12 +241,23 @@ typedef struct {
  * {4, 8, 16, 32, 64} MiB is searched too (75 points), otherwise the decode of
  * the columns uploaded to HBM (15 points).  C is fixed by the store width.
  * Writes up to max_points points (every point is visited once, in that
- * order), sets *n_points to the number visited, stores the fastest geometry
- * in *best (nullable) and makes it the context's geometry.  Outputs as in
+ * order), sets *n_points to the number visited and stores the fastest
+ * geometry in *best (nullable).  When all chunks of the columns are of one
+ * class -- the same scheme, dtype and bit-width bucket (widest b <= 8, 16,
+ * 32, 64) -- the result is kept for that class: later launches of the class
+ * use it while the context's tile_rows / threads are 0 (automatic), so one
+ * tuning run per column kind gives every kind its own geometry.  Otherwise
+ * the result becomes the context's geometry.  Outputs as in
  * zf_transfer_decompress; the columns are decoded into them many times. */
 zf_status zf_tune(zf_ctx* ctx, const zf_compressed* const* cols, uint32_t ncols, void* const* d_out,
                   const uint64_t* d_out_bytes, int32_t transfer, uint32_t reps, zf_tune_point* points,
                   uint32_t max_points, uint32_t* n_points, zf_kcfg* best);
+
+/* The geometry a launch of one class would use now: the context's
+ * tile_rows / threads where set, else the class's tuned entry, else the
+ * built-in values (128 threads; warp jobs of 2048 rows for delta, 4096 for
+ * the others).  bmax = the widest bit width of the launch's chunks. */
+zf_status zf_ctx_tuned_geometry(const zf_ctx* ctx, int32_t scheme, int32_t dtype, uint32_t bmax, zf_kcfg* out);
 
 /* ---- learned selector ------------------------------------------------------ */
 

@@ -23,6 +23,7 @@ __all__ = [
     "zf_ctx_set_ring", "zf_plan", "zf_compress_host", "zf_compressed_info", "zf_compressed_free",
     "zf_compressed_bytes", "zf_compressed_from_bytes", "zf_transfer_decompress", "zf_sync", "zf_upload",
     "zf_resident_free", "zf_decompress_resident", "zf_decompress_device_noalloc", "zf_tune", "zf_tune_point",
+    "zf_ctx_tuned_geometry",
     "zf_column_features", "zf_measure_classes", "zf_ctx_set_selector", "zf_mlp_create", "zf_mlp_destroy",
     "zf_mlp_get_params", "zf_mlp_set_params", "zf_mlp_forward", "zf_mlp_grad", "zf_mlp_adam", "zf_mlp_train",
     "zf_mlp_predict", "ZF_MLP_PARAMS", "ZF_MLP_CLASSES", "EXPORTED", "LIB_PATH",
@@ -104,6 +105,7 @@ _SIGS = {
     "zf_mlp_adam": [_vp, _vp, ctypes.c_float, _vp],
     "zf_mlp_train": [_vp, _vp, _vp, _vp, _u32, _u32, _u32, ctypes.c_float, _u64, _vp],
     "zf_mlp_predict": [_vp, _vp, _vp, _u32, _vp],
+    "zf_ctx_tuned_geometry": [_vp, ctypes.c_int32, ctypes.c_int32, _u32, ctypes.POINTER(zf_kcfg)],
     "zf_tune": [_vp, ctypes.POINTER(_vp), _u32, ctypes.POINTER(_vp), ctypes.POINTER(_u64), ctypes.c_int32, _u32,
                 ctypes.POINTER(zf_tune_point), _u32, ctypes.POINTER(_u32), ctypes.POINTER(zf_kcfg)],
 }
@@ -249,6 +251,12 @@ def zf_tune(ctx: int, cols: list[int], outs: list[int], caps: list[int], transfe
     _check(_L.zf_tune(ctx, c, len(cols), o, k, 1 if transfer else 0, reps, pts, 128, ctypes.byref(n),
                       ctypes.byref(best)), "zf_tune", ctx)
     return [pts[i] for i in range(min(n.value, 128))], best
+
+
+def zf_ctx_tuned_geometry(ctx: int, scheme: int, dtype: int, bmax: int) -> zf_kcfg:
+    out = zf_kcfg()
+    _check(_L.zf_ctx_tuned_geometry(ctx, scheme, dtype, bmax, ctypes.byref(out)), "zf_ctx_tuned_geometry", ctx)
+    return out
 
 
 def _f32(a) -> np.ndarray:

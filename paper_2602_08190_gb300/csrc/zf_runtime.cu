@@ -64,7 +64,13 @@ struct zf_ctx {
     ZfDevChunk* h_desc = nullptr;  // pinned
     size_t desc_cap = 0;
     std::vector<ZfDevChunk> resident_cache;   // descriptors last uploaded for resident decode
-    zf_kcfg kcfg{0, 128, 0, 64u << 20, 0};
+    zf_kcfg kcfg{0, 0, 0, 64u << 20, 0};
+    // Geometry found by zf_tune per (scheme, dtype, bit-width bucket), used
+    // by launches of that class while the context's tile_rows / threads are 0.
+    struct Tuned {
+        uint32_t tile_rows = 0, threads = 0;
+    } tuned[ZF_NSCHEMES][4][4];
+    uint64_t tuned_gen = 0;
     uint64_t slots_gen = 0;        // bumped whenever the staging slots are reallocated
     // CUDA graph of the last transfer (ZF_KCFG_GRAPH) and what it was built for
     cudaGraph_t graph = nullptr;
@@ -96,24 +102,39 @@ zf_status cuda_fail(zf_ctx* ctx, cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
     } while (0)
 
-// Zero fields take the built-in geometry: 128 threads; warp jobs of two
-// 1024-row tiles for delta launches and four for the others (the fastest, or
-// within 1% of it, for delta and RLE columns of 1M-row chunks in a full
-// search on GB300).  tile_rows stays 0 here and is resolved per launch group.
+// tile_rows and threads stay 0 ("auto") here and are resolved per launch
+// group (group_geometry); a zero stage size takes 64 MiB.
 zf_kcfg effective_kcfg(const zf_ctx* ctx) {
     zf_kcfg k = ctx->kcfg;
-    if (!k.threads) k.threads = 128;
     if (!k.stage_bytes) k.stage_bytes = 64u << 20;
     return k;
 }
 
-uint32_t group_tile_rows(const zf_kcfg& k, int scheme) {
-    return k.tile_rows ? k.tile_rows : (scheme == ZF_DELTA_BP ? 2048u : 4096u);
+uint32_t width_bucket(uint32_t bmax) { return bmax <= 8 ? 0u : bmax <= 16 ? 1u : bmax <= 32 ? 2u : 3u; }
+
+// The geometry of one launch: the context's tile_rows / threads where set,
+// else the tuned entry of the launch's (scheme, dtype, widest bit width)
+// class, else the built-in values: 128 threads, warp jobs of two 1024-row
+// tiles for delta and four for the others (the fastest, or within 1% of it,
+// for delta and RLE columns of 1M-row chunks in a full search on GB300).
+struct Geometry {
+    uint32_t tile_rows, threads;
+};
+Geometry group_geometry(const zf_ctx* ctx, const zf_kcfg& k, int scheme, int dtype, uint32_t bmax) {
+    Geometry g{k.tile_rows, k.threads};
+    if (scheme >= 0 && scheme < ZF_NSCHEMES && dtype >= 0 && dtype < 4) {
+        const auto& t = ctx->tuned[scheme][dtype][width_bucket(bmax)];
+        if (!g.tile_rows) g.tile_rows = t.tile_rows;
+        if (!g.threads) g.threads = t.threads;
+    }
+    if (!g.tile_rows) g.tile_rows = scheme == ZF_DELTA_BP ? 2048u : 4096u;
+    if (!g.threads) g.threads = 128;
+    return g;
 }
 
 bool kcfg_valid(const zf_kcfg& k) {
     return (k.tile_rows == 0 || (k.tile_rows % 1024 == 0 && k.tile_rows >= 1024 && k.tile_rows <= zf::kMaxTileRows)) &&
-           (k.threads == 128 || k.threads == 256 || k.threads == 512) && k.ctas_per_sm <= 64;
+           (k.threads == 0 || k.threads == 128 || k.threads == 256 || k.threads == 512) && k.ctas_per_sm <= 64;
 }
 
 // One decode unit of a call: a chunk with its host source, device output and part.
@@ -209,11 +230,12 @@ struct Group {
     uint32_t first, count, ntiles;
     uint32_t warp_smem;  // widest per-warp shared memory of the group's chunks
     uint32_t tile_rows;  // rows of a warp job in this launch
+    uint32_t threads;    // threads per CTA of this launch
 };
 
 // Append descriptors of works[b, e) to `desc`, grouped for launching.
-void build_groups(const std::vector<Work>& w, size_t b, size_t e, const zf_kcfg& k, std::vector<ZfDevChunk>& desc,
-                  std::vector<Group>& groups) {
+void build_groups(const zf_ctx* ctx, const std::vector<Work>& w, size_t b, size_t e, const zf_kcfg& k,
+                  std::vector<ZfDevChunk>& desc, std::vector<Group>& groups) {
     const bool batched = k.flags & ZF_KCFG_BATCHED;
     std::vector<std::pair<int, int>> keys;
     for (size_t i = b; i < e; i++) {
@@ -227,7 +249,11 @@ void build_groups(const std::vector<Work>& w, size_t b, size_t e, const zf_kcfg&
         if (std::find(keys.begin(), keys.end(), std::make_pair(s, d)) == keys.end()) keys.push_back({s, d});
     }
     for (auto& key : keys) {
-        Group g{key.first, key.second, (uint32_t)desc.size(), 0, 0, 16, group_tile_rows(k, key.first)};
+        uint32_t bmax = 0;   // widest bit width of the group: its geometry class
+        for (size_t i = b; i < e; i++)
+            if (w[i].ch->scheme == key.first && w[i].ch->dtype == key.second) bmax = std::max<uint32_t>(bmax, w[i].ch->bmax);
+        const Geometry geo = group_geometry(ctx, k, key.first, key.second, bmax);
+        Group g{key.first, key.second, (uint32_t)desc.size(), 0, 0, 16, geo.tile_rows, geo.threads};
         for (size_t i = b; i < e; i++) {
             int s = w[i].ch->scheme, d = w[i].ch->dtype;
             bool lz = s == ZF_LZ77;
@@ -262,8 +288,8 @@ zf_status launch_groups(zf_ctx* ctx, const std::vector<Group>& groups, const ZfD
         if (g.scheme == ZF_LZ77) {
             e = zf::launch_lz(dchunks, g.count, ctx->d_errw, ctx->num_sms, stream);
         } else {
-            uint32_t smem = ((g.warp_smem + 15) & ~15u) * (k.threads / 32);
-            zf::TileLaunch L{dchunks, g.count, g.ntiles, g.scheme, g.dtype, g.tile_rows, k.threads,
+            uint32_t smem = ((g.warp_smem + 15) & ~15u) * (g.threads / 32);
+            zf::TileLaunch L{dchunks, g.count, g.ntiles, g.scheme, g.dtype, g.tile_rows, g.threads,
                              k.ctas_per_sm, smem, ctx->num_sms, ctx->d_errw, queue};
             e = zf::launch_tiles(L, stream);
         }
@@ -419,7 +445,6 @@ const char* zf_last_error(const zf_ctx* ctx) { return ctx ? ctx->last_error.c_st
 zf_status zf_ctx_set_kcfg(zf_ctx* ctx, const zf_kcfg* k) {
     if (!ctx || !k) return ZF_EINVAL;
     zf_kcfg n = *k;
-    if (!n.threads) n.threads = 128;
     if (!n.stage_bytes) n.stage_bytes = 64u << 20;
     if (!kcfg_valid(n)) {
         ctx->last_error = "invalid kernel geometry";
@@ -528,7 +553,7 @@ zf_status zf_transfer_decompress(zf_ctx* ctx, const zf_compressed* const* cols, 
             key.push_back((uint64_t)(uintptr_t)d_out[o]);
             key.push_back(d_out_bytes[o]);
         }
-        key.insert(key.end(), {k.tile_rows, k.threads, k.ctas_per_sm, k.stage_bytes, k.flags, ctx->nslots,
+        key.insert(key.end(), {k.tile_rows, k.threads, k.ctas_per_sm, k.stage_bytes, k.flags, ctx->tuned_gen, ctx->nslots,
                                ctx->slot_req, ctx->slots_gen});
         if (ctx->graph_exec && key == ctx->graph_key) {
             ZF_CU(ctx, cudaEventRecord(ctx->ev_t0, ctx->copy));
@@ -592,7 +617,7 @@ zf_status zf_transfer_decompress(zf_ctx* ctx, const zf_compressed* const* cols, 
         for (size_t q = stages[s].first; q < stages[s].second; q++) work[q].dev = ctx->slots[s % ctx->nslots] + dev_off[q];
     std::vector<ZfDevChunk> desc;
     std::vector<std::vector<Group>> groups(stages.size());
-    for (size_t s = 0; s < stages.size(); s++) build_groups(work, stages[s].first, stages[s].second, k, desc, groups[s]);
+    for (size_t s = 0; s < stages.size(); s++) build_groups(ctx, work, stages[s].first, stages[s].second, k, desc, groups[s]);
     const size_t nd = std::max<size_t>(desc.size(), 1);
     ZfDevChunk* d_desc;
     ZfDevChunk* h_desc;
@@ -787,7 +812,7 @@ zf_status zf_decompress_resident(zf_ctx* ctx, const zf_resident* const* cols, ui
     if (st) return st;
     std::vector<ZfDevChunk> desc;
     std::vector<Group> groups;
-    build_groups(work, 0, work.size(), k, desc, groups);
+    build_groups(ctx, work, 0, work.size(), k, desc, groups);
     ZF_CU(ctx, cudaEventRecord(ctx->ev_t0, ctx->compute));
     bool same = desc.size() == ctx->resident_cache.size() &&
                 (desc.empty() || memcmp(desc.data(), ctx->resident_cache.data(), desc.size() * sizeof(ZfDevChunk)) == 0);
@@ -942,7 +967,7 @@ extern "C" zf_status zf_plan(zf_ctx* ctx, const zf_column* col, const zf_plan_op
         if (ctx) ctx->last_error = "chunk_rows must be a multiple of 1024 and at most 2^30";
         return ZF_EINVAL;
     }
-    p.kcfg = ctx ? ctx->kcfg : zf_kcfg{0, 128, 0, 64u << 20, 0};
+    p.kcfg = ctx ? ctx->kcfg : zf_kcfg{0, 0, 0, 64u << 20, 0};
     if (o.scheme >= 0) {
         if (o.scheme >= ZF_NSCHEMES) return ZF_EINVAL;
         p.scheme = o.scheme;
@@ -1047,8 +1072,44 @@ extern "C" zf_status zf_tune(zf_ctx* ctx, const zf_compressed* const* cols, uint
                 }
             }
     best_k.flags = saved.flags;
-    ctx->kcfg = best_k;
+    // Columns of one (scheme, dtype, bit-width bucket) class: the result is
+    // kept for that class and the context's geometry stays automatic, so
+    // later calls give every class its own; otherwise the context takes it.
+    int cs = -1, cd = -1, cb = -1;
+    bool one = true;
+    for (uint32_t c = 0; c < ncols && one; c++)
+        for (const zf::ChunkInfo& ch : cols[c]->chunks) {
+            const int b = (int)width_bucket(ch.bmax);
+            if (ch.scheme == ZF_LZ77 || (cs >= 0 && (ch.scheme != cs || ch.dtype != cd || b != cb))) {
+                one = false;
+                break;
+            }
+            cs = ch.scheme;
+            cd = ch.dtype;
+            cb = b;
+        }
+    if (one && cs >= 0) {
+        ctx->tuned[cs][cd][cb].tile_rows = best_k.tile_rows;
+        ctx->tuned[cs][cd][cb].threads = best_k.threads;
+        ctx->tuned_gen++;
+        ctx->kcfg = saved;
+        if (transfer) ctx->kcfg.stage_bytes = best_k.stage_bytes;
+    } else {
+        ctx->kcfg = best_k;
+    }
     *n_points = n;
     if (best) *best = best_k;
     return cleanup(ZF_OK);
+}
+
+extern "C" zf_status zf_ctx_tuned_geometry(const zf_ctx* ctx, int32_t scheme, int32_t dtype, uint32_t bmax,
+                                           zf_kcfg* out) {
+    if (!ctx || !out || scheme < 0 || scheme >= ZF_NSCHEMES || dtype < 0 || dtype > ZF_F64 || bmax > 64)
+        return ZF_EINVAL;
+    const zf_kcfg k = effective_kcfg(ctx);
+    const Geometry g = group_geometry(ctx, k, scheme, dtype, bmax);
+    *out = k;
+    out->tile_rows = g.tile_rows;
+    out->threads = g.threads;
+    return ZF_OK;
 }

@@ -76,3 +76,31 @@ def test_tune_visits_every_point_and_keeps_the_fastest(columns, transfer, npts):
             assert np.array_equal(b[: x.nbytes].cpu().numpy().view(x.dtype), x)
     finally:
         g.close()
+
+
+def test_tune_of_one_class_is_kept_for_that_class(columns):
+    """Tuning columns of one (scheme, dtype, bit-width bucket) class records
+    the fastest geometry for that class and leaves the context automatic:
+    other classes keep the built-in geometry, and decodes stay bit-exact."""
+    cols, hs = columns
+    g = Gpu()
+    try:
+        (x, s, cr), h = cols[0], hs[0]                 # the delta keys
+        assert s == zf.ZF_DELTA_BP
+        before = zf.zf_ctx_tuned_geometry(g.ctx, zf.ZF_DELTA_BP, zf.ZF_I64, 8)
+        buf = g.alloc(out_specs(x))[0]
+        pts, best = zf.zf_tune(g.ctx, [h], [buf.data_ptr()], [buf.numel()], transfer=False, reps=2)
+        assert len(pts) == 15
+        # the class of these chunks (bucket of the column's widest delta width) has the tuned geometry
+        geo = [zf.zf_ctx_tuned_geometry(g.ctx, zf.ZF_DELTA_BP, zf.ZF_I64, w) for w in (8, 16, 32, 64)]
+        assert any((k.tile_rows, k.threads) == (best.tile_rows, best.threads) for k in geo)
+        # RLE int32 is another class: still the built-in geometry
+        rle = zf.zf_ctx_tuned_geometry(g.ctx, zf.ZF_RLE, zf.ZF_I32, 0)
+        assert (rle.tile_rows, rle.threads) == (4096, 128)
+        assert (before.tile_rows, before.threads) == (2048, 128)
+        # decoding every column afterwards is exact
+        for (x2, s2, cr2), h2 in zip(cols, hs):
+            got, = g.decode([h2], out_specs(x2))
+            assert np.array_equal(got, x2)
+    finally:
+        g.close()
