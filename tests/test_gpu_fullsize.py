@@ -77,3 +77,27 @@ def test_non_parallel_256mb_text():
     finally:
         g.close()
         zf.zf_compressed_free(h)
+
+
+def test_single_64m_row_chunks():
+    """Chunks far above the default size: one 64M-row chunk per column
+    (512 MiB of int64 keys, 256 MiB of int32 dates and FOR values), so row
+    and byte offsets inside a chunk run into the hundreds of millions."""
+    n = 1 << 26
+    cols = [(W.sorted_keys(7, n), zf.ZF_DELTA_BP),
+            (W.dates_rle(7, n), zf.ZF_RLE),
+            (W.uniform_int(7, 0, 0, n, 0, 4096).astype(np.int32), zf.ZF_FOR_BP)]
+    g = Gpu()
+    try:
+        for x, s in cols:
+            h = compress(x, s, n)
+            try:
+                assert zf.zf_compressed_info(h)[2] == 1
+                for resident in (False, True):
+                    got, = g.decode([h], out_specs(x), resident=resident)
+                    assert np.array_equal(got, x), (s, resident)
+                _sampled_oracle_check(h, got, x.dtype, samples=(0,))
+            finally:
+                zf.zf_compressed_free(h)
+    finally:
+        g.close()
