@@ -311,7 +311,7 @@ zf_status zf_ctx_set_selector(zf_ctx* ctx, zf_mlp* net, const float* mean, const
 /* ---- decode without allocation ------------------------------------------ */
 
 /* Decode one compressed I32/I64 column (scheme RAW, FOR_BP, DICT_BP,
- * DELTA_BP or RLE) whose serialized bytes (the format above, for example
+ * DELTA_BP or RLE) or F64 column (RAW or FLOAT2INT) whose serialized bytes (the format above, for example
  * zf_compressed_bytes copied to the GPU) already sit in device memory at
  * `d_column`, into the device buffer `d_out`, on `stream` (a cudaStream_t,
  * or NULL for the default stream).  The paper has no counterpart: this entry
@@ -332,7 +332,9 @@ zf_status zf_ctx_set_selector(zf_ctx* ctx, zf_mlp* net, const float* mean, const
  * array (each call rewrites what it uses); calls that overlap on the GPU,
  * from several host threads or streams at once, race -- serialize them.
  * Both pointers must be 16-byte aligned; `out_bytes` must hold all rows.
- * Returns ZF_EUNSUPPORTED for BYTES columns. */
+ * Returns ZF_EUNSUPPORTED for BYTES columns.  Besides the checks of the
+ * other entry points' kernels, the device checks that each Float2Int chunk's
+ * exception rows are strictly increasing and inside the chunk. */
 zf_status zf_decompress_device_noalloc(const void* d_column, uint64_t column_bytes, void* d_out,
                                        uint64_t out_bytes, void* stream);
 

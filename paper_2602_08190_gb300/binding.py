@@ -237,8 +237,8 @@ def zf_decompress_resident(ctx: int, cols: list[int], outs: list[int], caps: lis
 
 def zf_decompress_device_noalloc(d_column: int, column_bytes: int, d_out: int, out_bytes: int,
                                  stream: int | None = None) -> int:
-    """Decode a serialized integer column already in device memory without
-    allocating; returns the zf_status (0 = ok) instead of raising."""
+    """Decode a serialized integer or float64 column already in device memory
+    without allocating; returns the zf_status (0 = ok) instead of raising."""
     return int(_L.zf_decompress_device_noalloc(d_column, column_bytes, d_out, out_bytes, stream or None))
 
 

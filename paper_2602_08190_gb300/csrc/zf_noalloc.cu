@@ -1,5 +1,6 @@
 // zf_noalloc.cu -- zf_decompress_device_noalloc: decode a compressed integer
-// column that is already in device memory without allocating anything.
+// or float64 column that is already in device memory without allocating
+// anything.
 //
 // Who needs it: code that must not call cudaMalloc (or any allocator) after
 // start-up -- for example a query engine that reserved all device memory up
@@ -47,10 +48,11 @@ __device__ bool chunk_ok(const uint8_t* c, uint64_t len, int scheme, int dtype, 
     const uint32_t b = c[6], n_aux = w[3];
     const uint32_t* off = w + 6;
     const uint32_t* ln = w + 9;
-    const int nsec = scheme == ZF_RLE ? 3 : (scheme == ZF_DICT_BP || scheme == ZF_DELTA_BP) ? 2 : 1;
+    const int nsec = (scheme == ZF_RLE || scheme == ZF_FLOAT2INT) ? 3
+                     : (scheme == ZF_DICT_BP || scheme == ZF_DELTA_BP) ? 2 : 1;
     for (int s = 0; s < nsec; s++)
         if (off[s] < 64 || (off[s] & 15) || (uint64_t)off[s] + ln[s] > len) return false;
-    const uint32_t sz = dtype == ZF_I64 ? 8 : 4, wd = 8 * sz;
+    const uint32_t sz = dtype == ZF_I32 ? 4 : 8, wd = 8 * sz;
     switch (scheme) {
     case ZF_RAW: return ln[0] == (uint64_t)rows * sz;
     case ZF_FOR_BP: return b <= wd && ln[0] == ((uint64_t)rows * b + 7) / 8;
@@ -75,6 +77,12 @@ __device__ bool chunk_ok(const uint8_t* c, uint64_t len, int scheme, int dtype, 
     case ZF_RLE:
         return n_aux <= rows && (!rows || n_aux) && ln[0] == (uint64_t)n_aux * sz && ln[1] == 4ull * n_aux &&
                ln[2] == 8ull * ((rows + zf::kRleDirRows - 1) / zf::kRleDirRows);
+    case ZF_FLOAT2INT: {
+        if (b > 64 || c[48] > zf::kF2IMaxExp || n_aux > rows || ln[0] != ((uint64_t)rows * b + 7) / 8 ||
+            ln[1] != 4ull * n_aux || ln[2] != 8ull * n_aux)
+            return false;
+        return true;   // the order of the exception rows is checked by the whole CTA
+    }
     }
     return false;
 }
@@ -88,7 +96,7 @@ __global__ void noalloc_setup(const uint8_t* col, uint64_t col_bytes, uint8_t* o
     __shared__ uint32_t s_bad;
     if (threadIdx.x == 0) s_bad = 0;
     __syncthreads();
-    const uint32_t sz = dtype == ZF_I64 ? 8 : 4;
+    const uint32_t sz = dtype == ZF_I32 ? 4 : 8;
     uint64_t expect_end = 64 + 32ull * nch;
     for (uint32_t k = threadIdx.x; k < nch; k += blockDim.x) {
         const uint8_t* d = col + 64 + 32ull * k;
@@ -113,6 +121,22 @@ __global__ void noalloc_setup(const uint8_t* col, uint64_t col_bytes, uint8_t* o
         if (!ok) atomicOr(&s_bad, 1u);
     }
     __syncthreads();
+    if (scheme == ZF_FLOAT2INT && !s_bad) {
+        // Float2Int exception rows strictly increasing and inside the chunk
+        // (the decoder's search over them relies on the order); the CTA's
+        // threads share each chunk's rows
+        bool bad = false;
+        for (uint32_t k = 0; k < nch; k++) {
+            const uint8_t* cb = col + *reinterpret_cast<const uint64_t*>(col + 64 + 32ull * k);
+            const uint32_t* w = reinterpret_cast<const uint32_t*>(cb);
+            const uint32_t rows = w[2], n_aux = w[3];
+            const uint32_t* er = reinterpret_cast<const uint32_t*>(cb + w[7]);   // section 1
+            for (uint32_t j = threadIdx.x; j < n_aux; j += blockDim.x)
+                bad |= er[j] >= rows || (j && er[j] <= er[j - 1]);
+        }
+        if (bad) atomicOr(&s_bad, 1u);
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
         // chunks must follow each other: each starts where the previous ends
         uint32_t tiles = 0;
@@ -148,6 +172,9 @@ __device__ __noinline__ void noalloc_tile(const ZfDevChunk& c, const zfd::Hdr& h
     case ZF_DELTA_BP * 4 + ZF_I64: zfd::delta_warp<int64_t>(c, h, r0, nr, wsm, err); break;
     case ZF_RLE * 4 + ZF_I32: zfd::rle_warp<int32_t>(c, h, r0, nr, wsm, err); break;
     case ZF_RLE * 4 + ZF_I64: zfd::rle_warp<int64_t>(c, h, r0, nr, wsm, err); break;
+    // doubles travel as their 64-bit patterns
+    case ZF_RAW * 4 + ZF_F64: zfd::fp_warp<int64_t, ZF_RAW>(c, h, r0, nr, wsm, err); break;
+    case ZF_FLOAT2INT * 4 + ZF_F64: zfd::fp_warp<int64_t, ZF_FLOAT2INT>(c, h, r0, nr, wsm, err); break;
     default:
         if ((threadIdx.x & 31) == 0) zfd::report(err, ZF_EINVAL, c.chunk_id);
     }
@@ -180,7 +207,7 @@ __global__ void __launch_bounds__(kThreads, 2) noalloc_decode(uint32_t warp_smem
         zfd::Hdr h;
         zfd::load_hdr(c.blob, h);
         const uint32_t rc = (tile - c.tile0) * kTileRows;
-        const uint32_t sz = c.dtype == ZF_I64 ? 8 : 4;
+        const uint32_t sz = c.dtype == ZF_I32 ? 4 : 8;
         if (h.rows != c.rows || rc >= c.rows || (uint64_t)c.rows * sz > c.dst_cap) {
             if (threadIdx.x == 0) zfd::report(err, ZF_ECORRUPT, c.chunk_id);
             continue;
@@ -238,13 +265,15 @@ extern "C" zf_status zf_decompress_device_noalloc(const void* d_column, uint64_t
     memcpy(&n_rows, hdr + 16, 8);
     memcpy(&total, hdr + 32, 8);
     if (magic != zf::kColMagic || ver != 1) return ZF_ECORRUPT;
-    if (dtype != ZF_I32 && dtype != ZF_I64) return ZF_EUNSUPPORTED;
-    if (scheme < ZF_RAW || scheme > ZF_RLE || chunk_rows == 0 || chunk_rows % 1024) return ZF_ECORRUPT;
+    if (dtype != ZF_I32 && dtype != ZF_I64 && dtype != ZF_F64) return ZF_EUNSUPPORTED;
+    const bool scheme_ok = dtype == ZF_F64 ? (scheme == ZF_RAW || scheme == ZF_FLOAT2INT)
+                                           : (scheme >= ZF_RAW && scheme <= ZF_RLE);
+    if (!scheme_ok || chunk_rows == 0 || chunk_rows % 1024) return ZF_ECORRUPT;
     if (nch > kNoallocMaxChunks) return ZF_EINVAL;  // above the fixed scratch size
     if ((uint64_t)nch != (n_rows + chunk_rows - 1) / chunk_rows || total > column_bytes ||
         64 + 32ull * nch > total)
         return ZF_ECORRUPT;
-    const uint32_t sz = dtype == ZF_I64 ? 8 : 4;
+    const uint32_t sz = dtype == ZF_I32 ? 4 : 8;
     if (n_rows * sz > out_bytes) return ZF_EINVAL;
     if (n_rows == 0) return ZF_OK;
     noalloc_setup<<<1, 256, 0, s>>>((const uint8_t*)d_column, total, (uint8_t*)d_out, out_bytes, nch, scheme,
