@@ -140,6 +140,17 @@ __device__ __forceinline__ S warp_incl_sum(S x, uint32_t lane) {
     return x;
 }
 
+// Inclusive sum over the lanes of values <= cap, saturating at cap (cap <
+// 2^31, so no partial sum wraps).
+__device__ __forceinline__ uint32_t warp_incl_sum_sat(uint32_t x, uint32_t cap, uint32_t lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+        if (lane >= (uint32_t)d) x = min(x + y, cap);
+    }
+    return x;
+}
+
 // ---------------------------------------------------------------- async staging
 // Copy `nbytes` (rounded up to 16) from a 16-byte aligned global address into
 // a warp's shared-memory buffer with cp.async, 16 bytes per lane per step.
@@ -566,8 +577,10 @@ __device__ __forceinline__ void rle_rows(const ZfDevChunk& c, const Hdr& h, T* d
     // one 16-byte load (entry sft is the tile's first run), one warp scan of
     // the lanes' sums gives each run its start row relative to the first
     // run's start, and every run but the first sets the bit of its start row.
-    // Lengths are at most the chunk's rows (< 2^30), and only the first and
-    // last run of a tile can be longer than the tile, so 32-bit sums hold.
+    // The tile's runs lie inside the chunk, so their lengths add up to at most
+    // its rows (<= 2^30); sums saturate at kCap = 2^30 + 1, which no valid
+    // tile reaches, so a stream whose lengths would wrap 32 bits is caught.
+    constexpr uint32_t kCap = (1u << 30) + 1u;
     bool bad = false;
     uint32_t end = 0;                 // rows covered so far, counted from the first run's start
     uint32_t first_len = 0, my_last = 0;
@@ -583,8 +596,8 @@ __device__ __forceinline__ void rle_rows(const ZfDevChunk& c, const Hdr& h, T* d
             if (!valid) L[e] = 0;
             bad |= valid && (L[e] == 0 || L[e] > h.rows);
         }
-        const uint32_t s4 = L[0] + L[1] + L[2] + L[3];
-        const uint32_t incl = warp_incl_sum<uint32_t>(s4, lane);
+        const uint32_t s4 = min(min(L[0] + L[1], kCap) + min(L[2] + L[3], kCap), kCap);
+        const uint32_t incl = warp_incl_sum_sat(s4, kCap, lane);
         uint32_t st = end + incl - s4;  // start of entry k0
 #pragma unroll
         for (int e = 0; e < 4; e++) {
@@ -600,8 +613,8 @@ __device__ __forceinline__ void rle_rows(const ZfDevChunk& c, const Hdr& h, T* d
             const uint32_t f0 = sft == 0 ? L[0] : sft == 1 ? L[1] : sft == 2 ? L[2] : L[3];
             first_len = __shfl_sync(0xFFFFFFFFu, f0, 0);   // run 0: entry sft of lane 0
         }
-        end += __shfl_sync(0xFFFFFFFFu, incl, 31);
-        if (end > 2u * (1u << 30) + 2048u) bad = true;
+        end = min(end + __shfl_sync(0xFFFFFFFFu, incl, 31), kCap);
+        if (end > h.rows) bad = true;
     }
     const uint32_t last_start = __shfl_sync(0xFFFFFFFFu, my_last, ((n - 1) & 127) >> 2);
     // The runs cover exactly [0, nr): the first starts at or before row 0, the
@@ -667,6 +680,10 @@ template <class T, bool WS>
 __device__ void rle_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t nrows, uint32_t* wsm,
                         uint32_t* err) {
     const uint32_t lane = threadIdx.x & 31;
+    if (h.rows > (1u << 30)) {   // chunks hold at most 2^30 rows (the presum relies on it)
+        if (lane == 0) report(err, ZF_ECORRUPT, c.chunk_id);
+        return;
+    }
     const T* vals = reinterpret_cast<const T*>(c.blob + h.off[0]);
     const uint32_t* lens = reinterpret_cast<const uint32_t*>(c.blob + h.off[1]);
     const uint2* dir = reinterpret_cast<const uint2*>(c.blob + h.off[2]);

@@ -708,8 +708,12 @@ zf_status parse_serialized(zf_compressed* c, std::string* why) {
             fail(why, "inconsistent column header");
             return ZF_ECORRUPT;
         }
-        if (pi.dtype != ZF_BYTES && pi.chunk_rows % 1024) {
-            fail(why, "chunk_rows must be a multiple of 1024");
+        if (pi.dtype != ZF_BYTES && (pi.chunk_rows % 1024 || pi.chunk_rows > (1u << 30))) {
+            fail(why, "chunk_rows must be a multiple of 1024 and at most 2^30");
+            return ZF_ECORRUPT;
+        }
+        if (pi.n_rows > (1ull << 48)) {
+            fail(why, "column above 2^48 rows");
             return ZF_ECORRUPT;
         }
         if (pi.dtype == ZF_BYTES && pi.chunk_rows != kLzBlock) {

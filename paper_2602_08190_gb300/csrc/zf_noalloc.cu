@@ -268,7 +268,8 @@ extern "C" zf_status zf_decompress_device_noalloc(const void* d_column, uint64_t
     if (dtype != ZF_I32 && dtype != ZF_I64 && dtype != ZF_F64) return ZF_EUNSUPPORTED;
     const bool scheme_ok = dtype == ZF_F64 ? (scheme == ZF_RAW || scheme == ZF_FLOAT2INT)
                                            : (scheme >= ZF_RAW && scheme <= ZF_RLE);
-    if (!scheme_ok || chunk_rows == 0 || chunk_rows % 1024) return ZF_ECORRUPT;
+    if (!scheme_ok || chunk_rows == 0 || chunk_rows % 1024 || chunk_rows > (1u << 30) || n_rows > (1ull << 48))
+        return ZF_ECORRUPT;
     if (nch > kNoallocMaxChunks) return ZF_EINVAL;  // above the fixed scratch size
     if ((uint64_t)nch != (n_rows + chunk_rows - 1) / chunk_rows || total > column_bytes ||
         64 + 32ull * nch > total)

@@ -183,6 +183,28 @@ def _corrupt(b: bytes, fn) -> bytes:
     return bytes(bb)
 
 
+def test_device_detects_rle_lengths_that_wrap_32_bits(gpu):
+    """A 64M-row RLE chunk whose first tile's 1,024 run lengths each pass the
+    per-run check (1 <= length <= rows) but add up to 2^32 + 1,024: a 32-bit
+    sum would wrap to the tile's 1,024 rows.  The device reports ZF_ECORRUPT."""
+    import struct
+    from oracle_pins import chunks_of
+    n = 1 << 26
+    x = np.full(n, 5000, np.int32)
+    x[:1024] = np.arange(1024)                       # runs 0..1023 of length 1, then one long run
+    b = oracle.encode(x, oracle.RLE, n)
+    off, ln, r0, rows, ch = chunks_of(oracle.default(), b)[0]
+    lo = off + ch["offs"][1]                          # run lengths
+    lens = [(1 << 25) + 1, (1 << 25) - 1] + [1 << 25] * 126 + [1] * 895 + [129]
+    assert len(lens) == 1024 and sum(lens) == (1 << 32) + 1024
+    bad = _corrupt(b, lambda bb: struct.pack_into("<1024I", bb, lo, *lens))
+    h = zf.zf_compressed_from_bytes(bad)
+    try:
+        gpu.decode([h], out_specs(x), expect=zf.ZF_ECORRUPT)
+    finally:
+        zf.zf_compressed_free(h)
+
+
 def test_device_detects_corrupt_streams(gpu):
     """Streams that pass the host's structural checks but whose data is
     inconsistent make the decoder report ZF_ECORRUPT, without a fault."""

@@ -115,6 +115,8 @@ def test_from_bytes_round_trip_and_rejects_corruption():
     bb = bytearray(b); bb[off] ^= 1; bad_cases.append(bb)                    # chunk magic
     bb = bytearray(b); struct.pack_into("<I", bb, off + 36, 1 << 30); bad_cases.append(bb)  # section length
     bad_cases.append(bytearray(b[:-16]))                                     # truncated
+    one = oracle.encode(x[:10000], oracle.RLE, 16384)                        # one chunk: only the bound fails
+    bb = bytearray(one); struct.pack_into("<I", bb, 12, 1 << 31); bad_cases.append(bb)  # chunk_rows above 2^30
     for bb in bad_cases:
         with pytest.raises(zf.ZfError) as e:
             zf.zf_compressed_from_bytes(bytes(bb))
