@@ -163,7 +163,9 @@ typedef struct {
 /* Create a context on `device`.  `copy_stream` / `compute_stream` are
  * cudaStream_t handles (for example torch.cuda.Stream.cuda_stream) or NULL
  * to let the context create its own non-blocking streams.  The context owns
- * the staging ring, events, descriptor buffers and the device error word. */
+ * the staging ring, events, descriptor buffers and the device error word.
+ * Calls on a context (and on a zf_mlp) work on its device and put the
+ * calling thread's current device back before they return. */
 zf_status zf_ctx_create(int device, void* copy_stream, void* compute_stream, zf_ctx** out);
 zf_status zf_ctx_destroy(zf_ctx* ctx);
 const char* zf_last_error(const zf_ctx* ctx);

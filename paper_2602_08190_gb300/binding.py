@@ -130,11 +130,16 @@ class Column:
     def __init__(self, data: np.ndarray, offsets: np.ndarray | None = None):
         self.data = np.ascontiguousarray(data)
         if offsets is None:
-            dt = {np.dtype(np.int32): ZF_I32, np.dtype(np.int64): ZF_I64, np.dtype(np.float64): ZF_F64}[self.data.dtype]
+            kinds = {np.dtype(np.int32): ZF_I32, np.dtype(np.int64): ZF_I64, np.dtype(np.float64): ZF_F64}
+            if self.data.dtype not in kinds:
+                raise TypeError(f"columns are int32, int64 or float64 (or uint8 bytes with offsets), "
+                                f"not {self.data.dtype}")
+            dt = kinds[self.data.dtype]
             self.offsets = None
             n = len(self.data)
         else:
-            assert self.data.dtype == np.uint8
+            if self.data.dtype != np.uint8:
+                raise TypeError(f"a string column's bytes are uint8, not {self.data.dtype}")
             self.offsets = np.ascontiguousarray(offsets, dtype=np.int32)
             dt = ZF_BYTES
             n = len(self.offsets) - 1

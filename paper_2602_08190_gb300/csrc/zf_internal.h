@@ -7,7 +7,27 @@
 
 #include "../../include/zf.h"
 
+#include <cuda_runtime_api.h>
+
 namespace zf {
+
+// Entry points make their context's device current; this puts the caller's
+// current device back when the entry point returns.
+struct KeepDevice {
+    int dev = -1;
+    KeepDevice() {
+        if (cudaGetDevice(&dev) != cudaSuccess) {
+            cudaGetLastError();
+            dev = -1;
+        }
+    }
+    ~KeepDevice() {
+        int cur = -1;
+        if (dev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != dev) cudaSetDevice(dev);
+    }
+    KeepDevice(const KeepDevice&) = delete;
+    KeepDevice& operator=(const KeepDevice&) = delete;
+};
 
 constexpr uint32_t kColMagic = 0x4C4F435Au;    // 'ZCOL'
 constexpr uint32_t kChunkMagic = 0x4B48435Au;  // 'ZCHK'

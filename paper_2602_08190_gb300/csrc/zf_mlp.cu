@@ -183,6 +183,7 @@ zf_status ensure_batch(zf_mlp* n, uint32_t B) {
 extern "C" {
 
 zf_status zf_mlp_create(int device, uint64_t seed, zf_mlp** out) {
+    zf::KeepDevice keep_device;
     if (!out) return ZF_EINVAL;
     *out = nullptr;
     if (cudaSetDevice(device) != cudaSuccess) return ZF_ECUDA;
@@ -217,6 +218,7 @@ zf_status zf_mlp_create(int device, uint64_t seed, zf_mlp** out) {
 }
 
 zf_status zf_mlp_destroy(zf_mlp* n) {
+    zf::KeepDevice keep_device;
     if (!n) return ZF_OK;
     cudaSetDevice(n->device);
     for (float* q : {n->p, n->m, n->v, n->grad, n->loss, n->gs, n->ls})
@@ -226,12 +228,14 @@ zf_status zf_mlp_destroy(zf_mlp* n) {
 }
 
 zf_status zf_mlp_get_params(const zf_mlp* n, float* host) {
+    zf::KeepDevice keep_device;
     if (!n || !host) return ZF_EINVAL;
     cudaSetDevice(n->device);
     return cudaMemcpy(host, n->p, NP * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess ? ZF_OK : ZF_ECUDA;
 }
 
 zf_status zf_mlp_set_params(zf_mlp* n, const float* host) {
+    zf::KeepDevice keep_device;
     if (!n || !host) return ZF_EINVAL;
     cudaSetDevice(n->device);
     if (cudaMemcpy(n->p, host, NP * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -272,6 +276,7 @@ zf_status zf_mlp_adam(zf_mlp* n, const float* d_grad, float lr, void* stream) {
 // seeded shuffle; each batch runs the gradient and Adam kernels.
 zf_status zf_mlp_train(zf_mlp* n, const float* h_x, const int32_t* h_y, const uint8_t* h_mask, uint32_t count,
                        uint32_t epochs, uint32_t batch, float lr, uint64_t seed, float* h_losses) {
+    zf::KeepDevice keep_device;
     if (!n || !h_x || !h_y || !h_mask || !count || !batch) return ZF_EINVAL;
     cudaSetDevice(n->device);
     float *dx = nullptr, *dl = nullptr;
@@ -331,6 +336,7 @@ zf_status zf_mlp_train(zf_mlp* n, const float* h_x, const int32_t* h_y, const ui
 // Class of each row of h_x (count x 32): the argmax of the logits over the
 // classes h_mask allows (-1 if none), computed on the GPU.
 zf_status zf_mlp_predict(zf_mlp* n, const float* h_x, const uint8_t* h_mask, uint32_t count, int32_t* h_class) {
+    zf::KeepDevice keep_device;
     if (!n || !h_x || !h_mask || !h_class) return ZF_EINVAL;
     if (!count) return ZF_OK;
     cudaSetDevice(n->device);

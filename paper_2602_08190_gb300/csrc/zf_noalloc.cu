@@ -38,6 +38,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratch
 
 std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices];   // device address of g_noalloc_scratch per device (set once)
+bool g_attr_set[kMaxDevices];        // shared-memory attribute of noalloc_decode set on the device
 
 // Structural checks of one chunk blob on the device (the host path makes the
 // same checks before a column is accepted).
@@ -281,16 +282,24 @@ extern "C" zf_status zf_decompress_device_noalloc(const void* d_column, uint64_t
                                     dtype, n_rows, chunk_rows);
     if (cudaGetLastError() != cudaSuccess) return ZF_ECUDA;
     // widest per-warp slice any chunk of this dtype may need (bit widths are not read on the host)
-    uint32_t ws = zfd::warp_smem(ZF_FOR_BP, sz, 8 * sz);
-    ws = ws > zfd::warp_smem(ZF_RLE, sz, 0) ? ws : zfd::warp_smem(ZF_RLE, sz, 0);
-    ws = (ws + 15) & ~15u;
+    auto slice = [](uint32_t vb) {
+        uint32_t w = zfd::warp_smem(ZF_FOR_BP, vb, 8 * vb);
+        w = w > zfd::warp_smem(ZF_RLE, vb, 0) ? w : zfd::warp_smem(ZF_RLE, vb, 0);
+        return (w + 15) & ~15u;
+    };
+    const uint32_t ws = slice(sz);
     const uint32_t smem = ws * (kThreads / 32);
-    static bool attr_set[kMaxDevices];
-    if (!attr_set[dev]) {
-        if (cudaFuncSetAttribute(noalloc_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-            return ZF_ECUDA;
-        attr_set[dev] = true;
+    {
+        // once per device, allow the largest launch of any value size (8-byte values need the most)
+        std::lock_guard<std::mutex> g(g_mu);
+        if (!g_attr_set[dev]) {
+            if (cudaFuncSetAttribute(noalloc_decode, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(slice(8) * (kThreads / 32))) != cudaSuccess) {
+                cudaGetLastError();
+                return ZF_ECUDA;
+            }
+            g_attr_set[dev] = true;
+        }
     }
     int per_sm = 0, sms = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, noalloc_decode, kThreads, smem) != cudaSuccess ||

@@ -368,6 +368,7 @@ zf_status finish_enqueue(zf_ctx* ctx) {
 extern "C" {
 
 zf_status zf_ctx_create(int device, void* copy_stream, void* compute_stream, zf_ctx** out) {
+    zf::KeepDevice keep_device;
     if (!out) return ZF_EINVAL;
     *out = nullptr;
     int ndev = 0;
@@ -410,6 +411,7 @@ zf_status zf_ctx_create(int device, void* copy_stream, void* compute_stream, zf_
 }
 
 zf_status zf_ctx_destroy(zf_ctx* ctx) {
+    zf::KeepDevice keep_device;
     if (!ctx) return ZF_OK;
     cudaSetDevice(ctx->device);
     if (ctx->compute) cudaStreamSynchronize(ctx->compute);
@@ -455,6 +457,7 @@ zf_status zf_ctx_set_kcfg(zf_ctx* ctx, const zf_kcfg* k) {
 }
 
 zf_status zf_ctx_set_ring(zf_ctx* ctx, uint32_t slots, uint64_t slot_bytes) {
+    zf::KeepDevice keep_device;
     if (!ctx || slots < 2 || slots > kMaxSlots) return ZF_EINVAL;
     if (ctx->busy) return ZF_EBUSY;
     cudaSetDevice(ctx->device);
@@ -533,6 +536,7 @@ zf_status zf_compressed_from_bytes(const uint8_t* data, uint64_t len, zf_compres
 
 zf_status zf_transfer_decompress(zf_ctx* ctx, const zf_compressed* const* cols, uint32_t ncols,
                                  void* const* d_out, const uint64_t* d_out_bytes) {
+    zf::KeepDevice keep_device;
     if (!ctx || (ncols && (!cols || !d_out || !d_out_bytes))) return ZF_EINVAL;
     zf_status st = begin_call(ctx);
     if (st) return st;
@@ -737,6 +741,7 @@ zf_status zf_transfer_decompress(zf_ctx* ctx, const zf_compressed* const* cols, 
 }
 
 zf_status zf_sync(zf_ctx* ctx, zf_stats* stats) {
+    zf::KeepDevice keep_device;
     if (!ctx) return ZF_EINVAL;
     if (!ctx->busy) {
         if (stats) *stats = ctx->st;
@@ -763,6 +768,7 @@ zf_status zf_sync(zf_ctx* ctx, zf_stats* stats) {
 }
 
 zf_status zf_upload(zf_ctx* ctx, const zf_compressed* c, zf_resident** out) {
+    zf::KeepDevice keep_device;
     if (!ctx || !c || !out) return ZF_EINVAL;
     *out = nullptr;
     if (ctx->busy) return ZF_EBUSY;
@@ -793,6 +799,7 @@ zf_status zf_upload(zf_ctx* ctx, const zf_compressed* c, zf_resident** out) {
 }
 
 zf_status zf_resident_free(zf_resident* r) {
+    zf::KeepDevice keep_device;
     if (!r) return ZF_OK;
     cudaSetDevice(r->device);
     if (r->d) cudaFree(r->d);
@@ -802,6 +809,7 @@ zf_status zf_resident_free(zf_resident* r) {
 
 zf_status zf_decompress_resident(zf_ctx* ctx, const zf_resident* const* cols, uint32_t ncols,
                                  void* const* d_out, const uint64_t* d_out_bytes) {
+    zf::KeepDevice keep_device;
     if (!ctx || (ncols && (!cols || !d_out || !d_out_bytes))) return ZF_EINVAL;
     zf_status st = begin_call(ctx);
     if (st) return st;
@@ -883,6 +891,7 @@ void class_mask(const zf_column& col, uint8_t* mask) {
 // Median end-to-end time (transfer + decode, zf_sync's total_ms) of every
 // selector class on this column; classes that do not apply get -1.
 extern "C" zf_status zf_measure_classes(zf_ctx* ctx, const zf_column* col, uint32_t reps, float* ms) {
+    zf::KeepDevice keep_device;
     if (!ctx || !col || !ms) return ZF_EINVAL;
     if (ctx->busy) return ZF_EBUSY;
     if (!reps) reps = 3;
@@ -1021,6 +1030,7 @@ const uint32_t kTuneStageMiB[] = {4, 8, 16, 32, 64};
 extern "C" zf_status zf_tune(zf_ctx* ctx, const zf_compressed* const* cols, uint32_t ncols, void* const* d_out,
                              const uint64_t* d_out_bytes, int32_t transfer, uint32_t reps, zf_tune_point* points,
                              uint32_t max_points, uint32_t* n_points, zf_kcfg* best) {
+    zf::KeepDevice keep_device;
     if (!ctx || !cols || !ncols || !d_out || !d_out_bytes || !n_points) return ZF_EINVAL;
     if (ctx->busy) return ZF_EBUSY;
     if (reps == 0) reps = 3;

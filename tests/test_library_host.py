@@ -184,3 +184,11 @@ def test_float2int_plan_and_validation():
     with pytest.raises(zf.ZfError) as e:
         zf.zf_compressed_from_bytes(bytes(bad))
     assert e.value.status == zf.ZF_ECORRUPT
+
+
+def test_column_rejects_unsupported_dtypes():
+    with pytest.raises(TypeError):
+        zf.Column(np.zeros(8, np.int16))
+    with pytest.raises(TypeError):
+        zf.Column(np.zeros(8, np.int32), np.array([0, 8], np.int32))   # string bytes must be uint8
+    assert zf.Column(np.zeros(8, np.float64)).c.dtype == zf.ZF_F64

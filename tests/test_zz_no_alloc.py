@@ -29,10 +29,12 @@ def _prices_with_exceptions():
 
 def test_noalloc_matches_transfer_decompress_twice():
     import torch
+    # int32 first: the first call on a device must already allow the larger
+    # shared-memory slices of the 8-byte columns after it
     cols = [
+        (W.uniform_int(11, 0, 0, (1 << 20) + 777, 0, 4096).astype(np.int32), zf.ZF_FOR_BP, 65536),
         (W.sorted_keys(11, 3 << 20), zf.ZF_DELTA_BP, 1 << 18),
         (W.dates_rle(11, 3 << 20), zf.ZF_RLE, 1 << 18),
-        (W.uniform_int(11, 0, 0, (1 << 20) + 777, 0, 4096).astype(np.int32), zf.ZF_FOR_BP, 65536),
         (W.dict_codes(11, 3, 0, 500000), zf.ZF_DICT_BP, 65536),
         (W.decimal_prices(11, 5, 0, (1 << 20) + 333), zf.ZF_FLOAT2INT, 65536),
         (_prices_with_exceptions(), zf.ZF_FLOAT2INT, 16384),
