@@ -231,7 +231,8 @@ def run_reference(args, rank: int):
     tot_b, tot_s = 0, 0.0
     desc = ""
     for _ in range(args.steps):
-        b, s, desc = oracle_sample([hk, hd], [np.int64, np.int32], args.ref_step_s, nt)
+        step_s = args.ref_step_s if args.ref_step_s is not None else min(2.0, max(0.3, 60.0 / args.steps))
+        b, s, desc = oracle_sample([hk, hd], [np.int64, np.int32], step_s, nt)
         tot_b += b
         tot_s += s
     v = tot_b / tot_s / 1e9
@@ -566,10 +567,12 @@ def run_profile(args, zf, torch):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="zipflow", choices=["zipflow", "reference"])
-    ap.add_argument("--ref-step-s", type=float, default=2.0, help="CPU seconds per reference step")
+    ap.add_argument("--ref-step-s", type=float, default=None,
+                    help="CPU seconds per reference step (default: 2 s, less for long runs so that "
+                         "all steps take about a minute)")
     ap.add_argument("--cpu-budget-s", type=float, default=12.0, help="CPU seconds for the cpu_baseline sample")
     ap.add_argument("--tile-rows", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
