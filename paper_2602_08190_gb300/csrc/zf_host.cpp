@@ -584,8 +584,10 @@ zf_status encode_column(const zf_plan_t& plan, const zf_column& col, zf_compress
     return ZF_OK;
 }
 
+// Warp jobs of a chunk: one per LZ77 block (its own kernel), else one per
+// tile_rows rows (bytes for a raw byte chunk).
 uint32_t tiles_of(const ChunkInfo& ch, uint32_t tile_rows) {
-    if (ch.scheme == ZF_LZ77 || ch.dtype == ZF_BYTES) return 1;
+    if (ch.scheme == ZF_LZ77) return 1;
     return (ch.rows + tile_rows - 1) / tile_rows;
 }
 

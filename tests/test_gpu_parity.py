@@ -82,6 +82,29 @@ def test_lz77_strings(gpu):
         assert np.array_equal(got_o, o), enc
 
 
+def test_raw_string_columns(gpu):
+    """A string column stored raw (the selector's other class for bytes):
+    every byte of each 64 KiB chunk comes back, through the transfer, the
+    resident and the batched paths."""
+    t, o = W.text_column(8, 300001)                  # ragged last chunk
+    h = compress(t, zf.ZF_RAW, offsets=o)
+    try:
+        for resident in (False, True):
+            got_t, got_o = gpu.decode([h], out_specs(t, o), resident=resident)
+            assert np.array_equal(got_t, t), resident
+            assert np.array_equal(got_o, o), resident
+    finally:
+        zf.zf_compressed_free(h)
+    g = Gpu(flags=zf.ZF_KCFG_BATCHED)
+    h = compress(t, zf.ZF_RAW, offsets=o)
+    try:
+        got_t, got_o = g.decode([h], out_specs(t, o))
+        assert np.array_equal(got_t, t) and np.array_equal(got_o, o)
+    finally:
+        zf.zf_compressed_free(h)
+        g.close()
+
+
 def test_lz77_edge_blocks(gpu):
     cases = [
         np.frombuffer(b"a" * 70000, np.uint8),                            # one long overlapping run
