@@ -20,11 +20,11 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-RAW, FOR_BP, DICT_BP, DELTA_BP, RLE, LZ77, FLOAT2INT = range(7)
+RAW, FOR_BP, DICT_BP, DELTA_BP, RLE, LZ77, FLOAT2INT, STRDICT = range(8)
 I32, I64, BYTES, F64 = range(4)
 OK, EINVAL, ENOMEM, ECUDA, ECORRUPT = 0, 1, 2, 3, 4
 SCHEMES = {"raw": RAW, "for_bp": FOR_BP, "dict_bp": DICT_BP, "delta_bp": DELTA_BP, "rle": RLE, "lz77": LZ77,
-           "float2int": FLOAT2INT}
+           "float2int": FLOAT2INT, "strdict": STRDICT}
 _DT = {np.dtype(np.int32): I32, np.dtype(np.int64): I64, np.dtype(np.uint8): BYTES, np.dtype(np.float64): F64}
 _NP = {I32: np.int32, I64: np.int64, BYTES: np.uint8, F64: np.float64}
 
@@ -68,6 +68,9 @@ class Oracle:
         L.orc_encode.restype = ctypes.c_int
         L.orc_encode.argtypes = [ctypes.c_int, ctypes.c_int, u8p, ctypes.c_uint64, ctypes.c_uint32, u8p,
                                  ctypes.c_uint64, u64p]
+        L.orc_encode_strdict.restype = ctypes.c_int
+        L.orc_encode_strdict.argtypes = [u8p, ctypes.c_uint64, u8p, ctypes.c_uint64, ctypes.c_uint32, u8p,
+                                         ctypes.c_uint64, u64p]
         L.orc_decode.restype = ctypes.c_int
         L.orc_decode.argtypes = [u8p, ctypes.c_uint64, u8p, ctypes.c_uint64]
         L.orc_decode_chunk.restype = ctypes.c_int
@@ -149,10 +152,30 @@ class Oracle:
             raise OracleError(st, "decode_chunk")
         return out[:rows]
 
-    # ---- string columns: LZ77 byte part followed by an int32 offsets part ----
+    def encode_strdict(self, data: np.ndarray, offsets: np.ndarray, chunk_bytes: int) -> bytes:
+        """Serialize a byte column (rows at ``offsets``) in string-dictionary chunks."""
+        data = np.ascontiguousarray(data, dtype=np.uint8)
+        offsets = np.ascontiguousarray(offsets, dtype=np.int32)
+        cap = int(self.L.orc_encode_bound(STRDICT, BYTES, len(data), chunk_bytes))
+        if cap == 0:
+            raise OracleError(EINVAL, "encode bound")
+        out = np.empty(cap, np.uint8)
+        n = ctypes.c_uint64(0)
+        dd = data if len(data) else np.zeros(1, np.uint8)
+        st = self.L.orc_encode_strdict(_ptr(dd), len(data), _ptr(offsets), len(offsets) - 1, chunk_bytes,
+                                       _ptr(out), cap, ctypes.byref(n))
+        if st:
+            raise OracleError(st, "encode_strdict")
+        return bytes(out[: n.value])
+
+    # ---- string columns: a byte part (LZ77 or string dictionary) followed by an int32 offsets part ----
     def encode_strings(self, data: np.ndarray, offsets: np.ndarray, block: int = 65536,
-                       offsets_scheme: int = DELTA_BP, offsets_chunk_rows: int = 65536) -> bytes:
-        a = bytearray(self.encode(np.ascontiguousarray(data, dtype=np.uint8), LZ77, block))
+                       offsets_scheme: int = DELTA_BP, offsets_chunk_rows: int = 65536,
+                       scheme: int = LZ77) -> bytes:
+        if scheme == STRDICT:
+            a = bytearray(self.encode_strdict(data, offsets, block))
+        else:
+            a = bytearray(self.encode(np.ascontiguousarray(data, dtype=np.uint8), scheme, block))
         a[40] |= 1  # flag: an offsets part follows
         b = self.encode(np.ascontiguousarray(offsets, dtype=np.int32), offsets_scheme, offsets_chunk_rows)
         return bytes(a) + b
@@ -179,5 +202,5 @@ def _delegate(name):
 
 
 for _n in ("bits", "pack", "unpack", "encode", "column_info", "decode", "chunk_span", "decode_chunk",
-           "encode_strings", "decode_strings"):
+           "encode_strdict", "encode_strings", "decode_strings"):
     globals()[_n] = _delegate(_n)

@@ -13,6 +13,8 @@
  *   Run-length encoding, presum        Section 2.1 ("RLE"); Section 3.2
  *   LZ77 back-references               Section 2.1 (LZ77-based algorithms)
  *   Float2Int (+ bit-packing)          Section 2.1 ("Float2Int"); Table 2
+ *   String dictionary (+ bit-packing)  Section 2.1 (dictionary encoding); Section 5.3.1
+ *                                      (the comment column's words as dictionary codes)
  *   Independent chunks                 Section 3.1 (Non-Parallel "file chunking")
  *
  * Decoders are the definitions written out: values are read bit by bit,
@@ -36,7 +38,8 @@
 /* ---- status codes (values of the library's zf_status) ---- */
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_ECORRUPT = 4 };
 /* ---- schemes and dtypes ---- */
-enum { ORC_RAW = 0, ORC_FOR_BP = 1, ORC_DICT_BP = 2, ORC_DELTA_BP = 3, ORC_RLE = 4, ORC_LZ77 = 5, ORC_F2I = 6 };
+enum { ORC_RAW = 0, ORC_FOR_BP = 1, ORC_DICT_BP = 2, ORC_DELTA_BP = 3, ORC_RLE = 4, ORC_LZ77 = 5, ORC_F2I = 6,
+       ORC_STRDICT = 7 };
 enum { ORC_I32 = 0, ORC_I64 = 1, ORC_BYTES = 2, ORC_F64 = 3 };
 
 #define COL_MAGIC 0x4C4F435Au   /* "ZCOL" */
@@ -46,6 +49,9 @@ enum { ORC_I32 = 0, ORC_I64 = 1, ORC_BYTES = 2, ORC_F64 = 3 };
 #define LZ_HASH_BITS 14
 #define LZ_MIN_MATCH 4u
 #define LZ_MAX_OFFSET 65535u
+#define STR_TOKEN_MAX 64u     /* bytes in one string-dictionary token at most */
+#define STR_DICT_MAX 65536u   /* dictionary entries at most */
+#define STR_TILE 1024u        /* tokens per tile-start entry */
 
 /* ------------------------------------------------------------------------- */
 /* little-endian byte helpers                                                */
@@ -155,6 +161,7 @@ static uint64_t chunk_bound(int scheme, int dtype, uint64_t rows) {
     case ORC_RLE: return b + rows * (sz + 4) + (rows / RLE_DIR_ROWS + 1) * 8;
     case ORC_LZ77: return b + rows + rows / 2 + 64;
     case ORC_F2I: return b + rows * (8 + 4 + 8) + 32;
+    case ORC_STRDICT: return b + 4 * (rows + 2 + rows / STR_TILE + 1) + rows + 2 * rows + 32;
     }
     return 0;
 }
@@ -440,6 +447,91 @@ static uint64_t enc_f2i(uint8_t* p, const void* x, uint32_t m) {
     return align16(w.end);
 }
 
+
+/* ---- string dictionary + bit-packing (bytes) ----
+ * The chunk's bytes are cut into tokens: a token ends after a space byte,
+ * before the first byte of a row, after STR_TOKEN_MAX bytes, or at the end of
+ * the chunk.  The dictionary is the distinct tokens in byte order (a prefix
+ * first); each token is stored as its rank, bit-packed at bits(ndict - 1).
+ * With more than STR_DICT_MAX distinct tokens every byte is a token instead.
+ * Sections: s0 = dictionary offsets [ndict + 1] then the output offset of
+ * every STR_TILE-th token; s1 = the dictionary's bytes; s2 = the codes. */
+typedef struct { const uint8_t* s; uint32_t len; } str_tok;
+
+static int cmp_tok(const void* a, const void* b) {
+    const str_tok* x = (const str_tok*)a;
+    const str_tok* y = (const str_tok*)b;
+    uint32_t n = x->len < y->len ? x->len : y->len;
+    int c = n ? memcmp(x->s, y->s, n) : 0;
+    if (c) return c;
+    return (x->len > y->len) - (x->len < y->len);
+}
+
+static uint32_t str_tokens(const uint8_t* x, uint32_t m, const uint8_t* row_start, int bytes_only, str_tok* t) {
+    uint32_t n = 0, i = 0;
+    while (i < m) {
+        uint32_t j = i + 1;
+        if (!bytes_only)
+            while (j < m && x[j - 1] != ' ' && !row_start[j] && j - i < STR_TOKEN_MAX) j++;
+        t[n].s = x + i;
+        t[n].len = j - i;
+        n++;
+        i = j;
+    }
+    return n;
+}
+
+/* sorted distinct tokens of t[0..n) into d; returns their number */
+static uint32_t str_dict(const str_tok* t, uint32_t n, str_tok* d) {
+    memcpy(d, t, sizeof(str_tok) * n);
+    qsort(d, n, sizeof(str_tok), cmp_tok);
+    uint32_t nd = 0;
+    for (uint32_t i = 0; i < n; i++)
+        if (nd == 0 || cmp_tok(&d[nd - 1], &d[i]) != 0) d[nd++] = d[i];
+    return nd;
+}
+
+static uint64_t enc_strdict(uint8_t* p, const uint8_t* x, uint32_t m, const uint8_t* row_start, int* err) {
+    str_tok* t = (str_tok*)malloc(sizeof(str_tok) * (m ? m : 1));
+    str_tok* d = (str_tok*)malloc(sizeof(str_tok) * (m ? m : 1));
+    if (!t || !d) { free(t); free(d); *err = ORC_ENOMEM; return 0; }
+    uint32_t T = str_tokens(x, m, row_start, 0, t);
+    uint32_t nd = str_dict(t, T, d);
+    if (nd > STR_DICT_MAX) {
+        T = str_tokens(x, m, row_start, 1, t);
+        nd = str_dict(t, T, d);
+    }
+    uint32_t b = orc_bits(nd ? nd - 1 : 0), ntiles = (T + STR_TILE - 1) / STR_TILE;
+    uint64_t dbytes = 0;
+    for (uint32_t k = 0; k < nd; k++) dbytes += d[k].len;
+    chunk_w w = {p, 64};
+    chunk_header(p, ORC_STRDICT, ORC_BYTES, b, 0, m, nd, T);
+    uint64_t o0 = sec_begin(&w, 0, 4ull * (nd + 1 + ntiles));
+    uint64_t o1 = sec_begin(&w, 1, dbytes);
+    uint64_t pos = 0;
+    for (uint32_t k = 0; k < nd; k++) {
+        put_u32(p + o0 + 4ull * k, (uint32_t)pos);
+        memcpy(p + o1 + pos, d[k].s, d[k].len);
+        pos += d[k].len;
+    }
+    put_u32(p + o0 + 4ull * nd, (uint32_t)pos);
+    uint64_t* code = (uint64_t*)malloc(sizeof(uint64_t) * (T ? T : 1));
+    if (!code) { free(t); free(d); *err = ORC_ENOMEM; return 0; }
+    uint64_t out_pos = 0;
+    for (uint32_t i = 0; i < T; i++) {
+        const str_tok* hit = (const str_tok*)bsearch(&t[i], d, nd, sizeof(str_tok), cmp_tok);
+        code[i] = (uint64_t)(hit - d);
+        if (i % STR_TILE == 0) put_u32(p + o0 + 4ull * (nd + 1 + i / STR_TILE), (uint32_t)out_pos);
+        out_pos += t[i].len;
+    }
+    uint64_t o2 = sec_begin(&w, 2, orc_packed_bytes(T, b));
+    orc_pack(code, T, b, p + o2);
+    free(code);
+    free(t);
+    free(d);
+    return align16(w.end);
+}
+
 /* ------------------------------------------------------------------------- */
 /* column encoder                                                            */
 /* ------------------------------------------------------------------------- */
@@ -450,7 +542,7 @@ uint64_t orc_encode_bound(int scheme, int dtype, uint64_t n, uint32_t chunk_rows
 }
 
 static int scheme_ok(int scheme, int dtype) {
-    if (dtype == ORC_BYTES) return scheme == ORC_RAW || scheme == ORC_LZ77;
+    if (dtype == ORC_BYTES) return scheme == ORC_RAW || scheme == ORC_LZ77 || scheme == ORC_STRDICT;
     if (dtype == ORC_F64) return scheme == ORC_RAW || scheme == ORC_F2I;
     if (dtype != ORC_I32 && dtype != ORC_I64) return 0;
     return scheme >= ORC_RAW && scheme <= ORC_RLE;
@@ -481,6 +573,7 @@ int orc_encode(int scheme, int dtype, const void* data, uint64_t n, uint32_t chu
         case ORC_RLE: len = enc_rle(p, dtype, x, m); break;
         case ORC_LZ77: len = enc_lz(p, x, m); break;
         case ORC_F2I: len = enc_f2i(p, x, m); break;
+        case ORC_STRDICT: return ORC_EINVAL;   /* needs the row offsets: orc_encode_strdict */
         }
         if (err) return err;
         uint8_t* d = out + 64 + 32 * c;
@@ -499,6 +592,53 @@ int orc_encode(int scheme, int dtype, const void* data, uint64_t n, uint32_t chu
     put_u32(out + 12, chunk_rows);
     put_u64(out + 16, n);
     put_u64(out + 24, n * sz);
+    put_u64(out + 32, pos);
+    *out_len = pos;
+    return ORC_OK;
+}
+
+
+/* A byte column of n bytes whose rows start at offsets[0..nrows] (offsets[0]
+ * = 0, offsets[nrows] = n, nondecreasing) in string-dictionary chunks of
+ * chunk_bytes bytes.  `out` must hold orc_encode_bound(ORC_STRDICT,
+ * ORC_BYTES, n, chunk_bytes) bytes. */
+int orc_encode_strdict(const uint8_t* data, uint64_t n, const int32_t* offsets, uint64_t nrows,
+                       uint32_t chunk_bytes, uint8_t* out, uint64_t cap, uint64_t* out_len) {
+    if (chunk_bytes == 0 || cap < orc_encode_bound(ORC_STRDICT, ORC_BYTES, n, chunk_bytes)) return ORC_EINVAL;
+    if (offsets[0] != 0 || (uint64_t)offsets[nrows] != n) return ORC_EINVAL;
+    for (uint64_t r = 0; r < nrows; r++)
+        if (offsets[r + 1] < offsets[r]) return ORC_EINVAL;
+    uint64_t nch = (n + chunk_bytes - 1) / chunk_bytes;
+    memset(out, 0, cap);
+    uint8_t* row_start = (uint8_t*)malloc(chunk_bytes + 1);
+    if (!row_start) return ORC_ENOMEM;
+    uint64_t pos = 64 + 32 * nch, r = 0;
+    for (uint64_t c = 0; c < nch; c++) {
+        uint64_t c0 = c * chunk_bytes;
+        uint32_t m = (uint32_t)(n - c0 < chunk_bytes ? n - c0 : chunk_bytes);
+        memset(row_start, 0, (size_t)m + 1);
+        while (r <= nrows && (uint64_t)offsets[r] < c0) r++;
+        for (uint64_t q = r; q <= nrows && (uint64_t)offsets[q] < c0 + m; q++) row_start[offsets[q] - c0] = 1;
+        int err = ORC_OK;
+        uint64_t len = enc_strdict(out + pos, data + c0, m, row_start, &err);
+        if (err) { free(row_start); return err; }
+        uint8_t* d = out + 64 + 32 * c;
+        put_u64(d + 0, pos);
+        put_u64(d + 8, len);
+        put_u64(d + 16, c0);
+        put_u32(d + 24, m);
+        put_u32(d + 28, 0);
+        pos += len;
+    }
+    free(row_start);
+    put_u32(out + 0, COL_MAGIC);
+    put_u16(out + 4, 1);
+    out[6] = (uint8_t)ORC_STRDICT;
+    out[7] = (uint8_t)ORC_BYTES;
+    put_u32(out + 8, (uint32_t)nch);
+    put_u32(out + 12, chunk_bytes);
+    put_u64(out + 16, n);
+    put_u64(out + 24, n);
     put_u64(out + 32, pos);
     *out_len = pos;
     return ORC_OK;
@@ -600,6 +740,33 @@ int orc_decode_chunk(const uint8_t* c, uint64_t len, void* out, uint64_t out_cap
             uint64_t bits = get_u64(s2 + 8ull * k);
             memcpy(&o[pos], &bits, 8);
         }
+        return ORC_OK;
+    }
+    case ORC_STRDICT: {
+        /* the output is the dictionary entries of the codes, one after another */
+        uint8_t* o = (uint8_t*)out;
+        uint32_t nd = n_aux;
+        uint64_t T = ref, ntiles = (T + STR_TILE - 1) / STR_TILE;
+        if (!sec_ok(c, len, 0) || !sec_ok(c, len, 1) || !sec_ok(c, len, 2) || nd == 0 || nd > STR_DICT_MAX ||
+            b != orc_bits(nd - 1) || T > m || (m > 0 && T == 0) || l0 != 4ull * (nd + 1 + ntiles) ||
+            l2 != orc_packed_bytes(T, b))
+            return ORC_ECORRUPT;
+        if (get_u32(s0) != 0 || get_u32(s0 + 4ull * nd) != l1) return ORC_ECORRUPT;
+        for (uint32_t k = 0; k < nd; k++) {
+            uint32_t a0 = get_u32(s0 + 4ull * k), a1 = get_u32(s0 + 4ull * (k + 1));
+            if (a1 <= a0 || a1 - a0 > STR_TOKEN_MAX) return ORC_ECORRUPT;
+        }
+        uint64_t op = 0;
+        for (uint64_t t = 0; t < T; t++) {
+            if (t % STR_TILE == 0 && get_u32(s0 + 4ull * (nd + 1 + t / STR_TILE)) != op) return ORC_ECORRUPT;
+            uint64_t k = orc_unpack_one(s2, t, b);
+            if (k >= nd) return ORC_ECORRUPT;
+            uint32_t a0 = get_u32(s0 + 4 * k), a1 = get_u32(s0 + 4 * (k + 1));
+            if (op + (a1 - a0) > m) return ORC_ECORRUPT;
+            for (uint32_t q = a0; q < a1; q++) o[op++] = s1[q];
+        }
+        if (op != m) return ORC_ECORRUPT;
+        (void)flags;
         return ORC_OK;
     }
     case ORC_LZ77: {

@@ -489,4 +489,114 @@ def pin_f2i_exceptions(orc):
         else:
             raise AssertionError("malformed Float2Int chunk accepted")
 
+
+# ---- string dictionary + bit-packing (Section 2.1 dictionary encoding over the
+# ---- words of a text column, as Section 5.3.1 does for the comment column) ----
+
+def _plain_tokens(chunk: bytes, starts: set) -> list:
+    """Tokens of one chunk by the format's rule, written with Python slicing:
+    cut after every space, before every row start, every 64 bytes."""
+    toks, cur = [], b""
+    for i, c in enumerate(chunk):
+        if cur and (i in starts or len(cur) == 64):
+            toks.append(cur)
+            cur = b""
+        cur += bytes([c])
+        if c == 0x20:
+            toks.append(cur)
+            cur = b""
+    if cur:
+        toks.append(cur)
+    return toks
+
+
+def _plain_strdict_chunk(chunk: bytes, starts: set):
+    toks = _plain_tokens(chunk, starts)
+    d = sorted(set(toks))
+    if len(d) > 65536:
+        toks = [bytes([c]) for c in chunk]
+        d = sorted(set(toks))
+    rank = {t: k for k, t in enumerate(d)}
+    offs = np.cumsum([0] + [len(t) for t in d]).tolist()
+    tiles, pos = [], 0
+    for i, t in enumerate(toks):
+        if i % 1024 == 0:
+            tiles.append(pos)
+        pos += len(t)
+    b = (len(d) - 1).bit_length()
+    return d, [rank[t] for t in toks], offs, tiles, b
+
+
+def pin_strdict_hand_example(orc):
+    # rows "ab cd" and "ab": tokens "ab ", "cd" | "ab"; sorted dictionary
+    # "ab" < "ab " < "cd"; codes 1, 2, 0 at 2 bits = 0b00_10_01
+    t = np.frombuffer(b"ab cdab", np.uint8).copy()
+    buf = orc.encode_strdict(t, np.array([0, 5, 7], np.int32), 65536)
+    (off, ln, r0, rows, ch), = chunks_of(orc, buf)
+    assert (ch["scheme"], ch["dtype"], ch["bw"], ch["rows"], ch["n_aux"], ch["ref"]) == (7, 2, 2, 7, 3, 3)
+    assert ch["secs"][0] == struct.pack("<5I", 0, 2, 5, 7, 0)
+    assert ch["secs"][1] == b"abab cd"
+    assert ch["secs"][2] == bytes([0x09])
+    assert orc.decode(buf).tobytes() == b"ab cdab"
+
+
+def pin_strdict_matches_the_plain_tokenizer(orc):
+    rng = np.random.default_rng(17)
+    words = [b"a", b"bb", b"ccc", b"the", b"x" * 70, b"", b"  ", b"q r"]
+    for trial in range(6):
+        rows = [b" ".join(words[k] for k in rng.integers(0, len(words), rng.integers(0, 6)))
+                for _ in range(rng.integers(1, 400))]
+        t = np.frombuffer(b"".join(rows) or b"", np.uint8).copy()
+        o = np.cumsum([0] + [len(r) for r in rows]).astype(np.int32)
+        if len(t) == 0:
+            continue
+        chunk = 65536 if trial % 2 else 1 << 16
+        buf = orc.encode_strdict(t, o, chunk)
+        data = t.tobytes()
+        for off, ln, r0, rows_c, ch in chunks_of(orc, buf):
+            piece = data[r0:r0 + rows_c]
+            starts = {int(x) - r0 for x in o if r0 < x < r0 + rows_c}
+            d, codes, offs, tiles, b = _plain_strdict_chunk(piece, starts)
+            assert ch["n_aux"] == len(d) and ch["ref"] == len(codes) and ch["bw"] == b
+            assert ch["secs"][1] == b"".join(d)
+            assert ch["secs"][0] == struct.pack(f"<{len(offs) + len(tiles)}I", *offs, *tiles)
+            assert ch["secs"][2] == bigint_pack(codes, b)
+        assert orc.decode(buf).tobytes() == data
+
+
+def pin_strdict_round_trip_and_byte_tokens(orc):
+    t, o = W.text_column(9, 300000)
+    buf = orc.encode_strings(t, o, 131072, scheme=O.STRDICT)
+    t2, o2 = orc.decode_strings(buf)
+    assert np.array_equal(t2, t) and np.array_equal(o2, o)
+    # 70,000 distinct five-byte tokens in one chunk: above 65,536, so every byte is a token
+    k = np.arange(70000)
+    words = np.stack([97 + k % 26, 97 + k // 26 % 26, 97 + k // 676 % 26, 97 + k // 17576 % 26,
+                      np.full_like(k, 32)], 1).astype(np.uint8)
+    data = words.reshape(-1)
+    buf = orc.encode_strdict(data, np.array([0, len(data)], np.int32), 1 << 19)
+    (off, ln, r0, rows, ch), = chunks_of(orc, buf)
+    assert ch["ref"] == len(data) and ch["n_aux"] == len(np.unique(data)) and ch["bw"] == 5
+    assert np.array_equal(orc.decode(buf), data)
+
+
+def pin_strdict_rejects_corrupt(orc):
+    t = np.frombuffer(b"ab cdab", np.uint8).copy()
+    buf = orc.encode_strdict(t, np.array([0, 5, 7], np.int32), 65536)
+    (off, ln, r0, rows, ch), = chunks_of(orc, buf)
+    blob = bytearray(buf[off:off + ln])
+    o0, o1, o2 = ch["offs"]
+    bad = []
+    b1 = bytearray(blob); b1[o2] = 0x0D; bad.append(b1)                             # code 3 >= 3 entries
+    b2 = bytearray(blob); struct.pack_into("<I", b2, o0 + 16, 1); bad.append(b2)    # first tile starts at 1
+    b3 = bytearray(blob); struct.pack_into("<I", b3, o0 + 4, 5); bad.append(b3)     # entries not increasing
+    b4 = bytearray(blob); b4[6] = 3; bad.append(b4)                                 # width is not bits(ndict - 1)
+    for bb in bad:
+        try:
+            orc.decode_chunk(bytes(bb), np.uint8)
+        except O.OracleError as err:
+            assert err.code == O.ECORRUPT
+        else:
+            raise AssertionError("malformed string-dictionary chunk accepted")
+
 PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

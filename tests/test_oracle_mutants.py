@@ -52,6 +52,13 @@ MUTANTS = {
     "f2i_reference_is_max": ("if (ok[i] && (!have || d[i] < mn)) { mn = d[i]; have = 1; }",
                              "if (ok[i] && (!have || d[i] > mn)) { mn = d[i]; have = 1; }"),
     "lz_no_raw_fallback": ("if ((uint64_t)nl + no + nlit >= m) {", "if (0) {"),
+    "strdict_tokens_cross_rows": ("while (j < m && x[j - 1] != ' ' && !row_start[j] && j - i < STR_TOKEN_MAX) j++;",
+                                  "while (j < m && x[j - 1] != ' ' && j - i < STR_TOKEN_MAX) j++;"),
+    "strdict_token_cap_65": ("while (j < m && x[j - 1] != ' ' && !row_start[j] && j - i < STR_TOKEN_MAX) j++;",
+                             "while (j < m && x[j - 1] != ' ' && !row_start[j] && j - i <= STR_TOKEN_MAX) j++;"),
+    "strdict_first_seen_order": ("    qsort(d, n, sizeof(str_tok), cmp_tok);\n", ""),
+    "strdict_no_tile_check": (
+        "if (t % STR_TILE == 0 && get_u32(s0 + 4ull * (nd + 1 + t / STR_TILE)) != op) return ORC_ECORRUPT;", ""),
     "lz_offset_of_next_token": ("uint32_t off = get_u16(s1 + 2ull * t);", "uint32_t off = get_u16(s1 + 2ull * (t + 1 < n_aux - 1 ? t + 1 : t));"),
 }
 
