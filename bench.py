@@ -344,14 +344,22 @@ def run_batched(args, zf, torch):
 TEXT_WORKLOAD = ("non_parallel: {:,}-byte string column, Zipf(1.1) words from a 5,000-word vocabulary "
                  "(3-12 letters), 1-8 words per row; LZ77 in 64 KiB blocks (one warp per block), int32 offsets "
                  "delta-packed in 65,536-row chunks")
+TEXT_STRDICT_WORKLOAD = ("group_parallel string dictionary: {:,}-byte string column, Zipf(1.1) words from a "
+                         "5,000-word vocabulary (3-12 letters), 1-8 words per row; tokens (words with their space) "
+                         "as bit-packed dictionary codes in {:,}-byte chunks, int32 offsets delta-packed in "
+                         "65,536-row chunks")
 
 
 def run_text(args, zf, torch):
-    """The Non-Parallel workload: decode of a 256 MB LZ77 string column."""
+    """The Non-Parallel workload: decode of a 256 MB LZ77 string column (or,
+    with --text-scheme strdict, the same column as a string dictionary)."""
     import zf_workloads as W
     t, o = W.text_column(1, int(args.text_mb * (1 << 20)))
     col = zf.Column(t, o)
-    h = zf.zf_compress_host(zf.zf_plan(None, col, scheme=zf.ZF_LZ77), col)
+    strdict = args.text_scheme == "strdict"
+    chunk = int(args.text_chunk_mb * (1 << 20))
+    plan = zf.zf_plan(None, col, scheme=zf.ZF_STRDICT if strdict else zf.ZF_LZ77, chunk_rows=chunk if strdict else 0)
+    h = zf.zf_compress_host(plan, col)
     raw, comp, nch = zf.zf_compressed_info(h)
     copy_s, comp_s = torch.cuda.Stream(), torch.cuda.Stream()
     ctx = zf.zf_ctx_create(0, copy_s.cuda_stream, comp_s.cuda_stream)
@@ -386,8 +394,10 @@ def run_text(args, zf, torch):
     line = {"metric": METRIC, "value": round(raw / (td * 1e-3) / 1e9, 2), "unit": "GB/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(td, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8/int32", "data": "synthetic",
-            "config": {"workload": TEXT_WORKLOAD.format(t.nbytes), "raw_bytes_per_step": raw, "comp_bytes_per_step": comp,
-                       "compression_ratio": round(raw / comp, 3), "blocks": nch,
+            "config": {"workload": (TEXT_STRDICT_WORKLOAD.format(t.nbytes, plan.chunk_rows) if strdict
+                                    else TEXT_WORKLOAD.format(t.nbytes)),
+                       "raw_bytes_per_step": raw, "comp_bytes_per_step": comp,
+                       "compression_ratio": round(raw / comp, 3), "chunks": nch,
                        "l2": "flushed (256 MiB write) before every resident step"},
             "e2e": {"value": round(raw / (te * 1e-3) / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": comp,
                     "d2h_bytes_per_step": 8, "ms_per_step": round(te, 4)},
@@ -587,6 +597,9 @@ def main():
                     help="group_parallel: the benchmark line; batched: the 40 GB fact table; "
                          "selector: train and evaluate the learned selector")
     ap.add_argument("--text-mb", type=float, default=256, help="string column size (text workload), MiB")
+    ap.add_argument("--text-scheme", choices=["lz77", "strdict"], default="lz77",
+                    help="byte scheme of the text workload")
+    ap.add_argument("--text-chunk-mb", type=float, default=4, help="string-dictionary chunk size, MiB")
     ap.add_argument("--sel-train", type=int, default=2000)
     ap.add_argument("--sel-test", type=int, default=200)
     ap.add_argument("--sel-cap", type=int, default=2_000_000, help="row cap for label collection")

@@ -63,6 +63,18 @@
  *              of d is q + r * 10^-e with q = d * 10^-e and r = d - q * 10^e
  *              (fused multiply-adds; 10^-e = the double nearest it): the
  *              double nearest d / 10^e.  Exception rows hold u = 0 in s0.
+ *     STRDICT  (BYTES only; chunk_rows = bytes per chunk, a multiple of 65536,
+ *              at most 2^26) rows = bytes of the chunk, n_aux = dictionary
+ *              entries (1..65536), reference = tokens T, b = bits(n_aux - 1).
+ *              s0 = u32 offsets of the n_aux + 1 entries in s1 (0, increasing,
+ *              each entry 1..64 bytes, the last = s1's length), then u32 output
+ *              offset of token 1024*j for j < ceil(T/1024); s1 = the entries'
+ *              bytes; s2 = bit-packed entry numbers of the T tokens.  The chunk
+ *              is the entries of the tokens, one after another.  The encoder
+ *              cuts a token after each space byte, before each row start, after
+ *              64 bytes and at the chunk end, sorts the distinct tokens by
+ *              their bytes (a prefix first), and above 65536 distinct tokens
+ *              makes every byte a token
  *   Bit-packing: value i occupies stream bits [i*b, i*b+b), least
  *   significant bit first; stream bit k is bit k%8 of byte k/8.
  */
@@ -92,7 +104,8 @@ typedef enum { ZF_I32 = 0, ZF_I64 = 1, ZF_BYTES = 2, ZF_F64 = 3 } zf_dtype;
 typedef enum {
     ZF_RAW = 0, ZF_FOR_BP = 1, ZF_DICT_BP = 2, ZF_DELTA_BP = 3, ZF_RLE = 4, ZF_LZ77 = 5,
     ZF_FLOAT2INT = 6,     /* float64 columns (Section 2.1 "Float2Int", with bit-packing as in Table 2) */
-    ZF_NSCHEMES = 7
+    ZF_STRDICT = 7,       /* byte columns: dictionary of tokens + bit-packed codes (Section 2.1; Section 5.3.1) */
+    ZF_NSCHEMES = 8
 } zf_scheme;
 
 typedef struct zf_ctx zf_ctx;

@@ -14,7 +14,9 @@
 #include <cstring>
 #include <functional>
 #include <mutex>
+#include <string_view>
 #include <thread>
+#include <unordered_map>
 
 #include "zf_internal.h"
 
@@ -87,6 +89,76 @@ void enc_raw(const T* x, uint32_t m, Out& o) {
     w.header(ZF_RAW, dtype_code<T>(), 0, 0, m, 0, 0);
     uint64_t off = w.section(0, (uint64_t)m * sizeof(T));
     if (m) memcpy(&o.b[off], x, (uint64_t)m * sizeof(T));
+}
+
+// ------------------------------------------------------------------ string dictionary + BP
+// Tokens of a byte chunk: cut after each space byte, before each row start,
+// after kStrTokenMax bytes and at the chunk end.  The dictionary is the
+// distinct tokens in byte order (a prefix first) and each token is stored as
+// its rank at bits(ndict - 1) bits (Section 2.1 dictionary encoding over the
+// words of a text column, as Section 5.3.1 does for the comment column).
+// Above kStrDictMax distinct tokens every byte is a token.  Sections: s0 =
+// dictionary offsets [ndict + 1], then the output offset of every
+// kStrTile-th token; s1 = the dictionary's bytes; s2 = the codes.
+void enc_strdict(const uint8_t* x, uint32_t m, const std::vector<uint8_t>& row_start, Out& o) {
+    std::vector<std::pair<uint32_t, uint32_t>> tok;   // (first byte, length)
+    std::unordered_map<std::string_view, uint32_t> ids;
+    std::vector<std::string_view> dict;
+    for (int pass = 0; pass < 2; pass++) {
+        tok.clear();
+        for (uint32_t i = 0; i < m;) {
+            uint32_t j = i + 1;
+            if (pass == 0)
+                while (j < m && x[j - 1] != ' ' && !row_start[j] && j - i < kStrTokenMax) j++;
+            tok.push_back({i, j - i});
+            i = j;
+        }
+        ids.clear();
+        dict.clear();
+        bool over = false;
+        for (auto& t : tok) {
+            std::string_view v(reinterpret_cast<const char*>(x) + t.first, t.second);
+            if (ids.emplace(v, 0).second) {
+                dict.push_back(v);
+                if (dict.size() > kStrDictMax) {
+                    over = true;
+                    break;
+                }
+            }
+        }
+        if (!over) break;
+    }
+    std::sort(dict.begin(), dict.end(), [](std::string_view a, std::string_view b) {
+        const size_t n = std::min(a.size(), b.size());
+        const int c = n ? memcmp(a.data(), b.data(), n) : 0;
+        return c ? c < 0 : a.size() < b.size();
+    });
+    for (uint32_t k = 0; k < dict.size(); k++) ids[dict[k]] = k;
+    const uint32_t nd = (uint32_t)dict.size(), T = (uint32_t)tok.size();
+    const uint32_t b = bits_of(nd ? nd - 1 : 0), ntiles = (T + kStrTile - 1) / kStrTile;
+    uint64_t dbytes = 0;
+    for (auto& v : dict) dbytes += v.size();
+    const uint64_t l0 = 4ull * (nd + 1 + ntiles), l2 = packed_bytes(T, b);
+    o.b.assign(align16(align16(align16(kChunkHeader + l0) + dbytes) + l2), 0);
+    ChunkWriter w(o);
+    w.header(ZF_STRDICT, ZF_BYTES, b, 0, m, nd, T);
+    const uint64_t s0 = w.section(0, l0), s1 = w.section(1, dbytes);
+    uint64_t pos = 0;
+    for (uint32_t k = 0; k < nd; k++) {
+        o.put32(s0 + 4ull * k, (uint32_t)pos);
+        memcpy(&o.b[s1 + pos], dict[k].data(), dict[k].size());
+        pos += dict[k].size();
+    }
+    o.put32(s0 + 4ull * nd, (uint32_t)pos);
+    std::vector<uint32_t> code(T);
+    uint64_t out = 0;
+    for (uint32_t i = 0; i < T; i++) {
+        code[i] = ids.find(std::string_view(reinterpret_cast<const char*>(x) + tok[i].first, tok[i].second))->second;
+        if (i % kStrTile == 0) o.put32(s0 + 4ull * (nd + 1 + i / kStrTile), (uint32_t)out);
+        out += tok[i].second;
+    }
+    const uint64_t s2 = w.section(2, l2);
+    pack_stream(T, b, [&](uint64_t i) { return (uint64_t)code[i]; }, o.b.data() + s2);
 }
 
 // ------------------------------------------------------------------ Float2Int + BP
@@ -373,6 +445,8 @@ struct PartSpec {
     const uint8_t* data;
     uint64_t n;
     uint32_t chunk_rows;
+    const int32_t* offsets = nullptr;   // string dictionary: row starts (nrows + 1 entries)
+    uint64_t nrows = 0;
 };
 
 void run_parallel(uint32_t n, const std::function<void(uint32_t)>& f) {
@@ -402,8 +476,16 @@ zf_status encode_part(const PartSpec& p, std::vector<Out>& blobs, std::string* w
         Out& o = blobs[c];
         zf_status st = ZF_OK;
         if (p.dtype == ZF_BYTES) {
-            if (p.scheme == ZF_LZ77) enc_lz(x, m, o);
-            else {  // RAW bytes
+            if (p.scheme == ZF_LZ77) {
+                enc_lz(x, m, o);
+            } else if (p.scheme == ZF_STRDICT) {
+                // rows that start inside the chunk (offsets are nondecreasing)
+                std::vector<uint8_t> row_start((size_t)m + 1, 0);
+                const int32_t* q = std::lower_bound(p.offsets, p.offsets + p.nrows + 1, (int64_t)r0,
+                                                    [](int32_t a, int64_t v) { return (int64_t)a < v; });
+                for (; q < p.offsets + p.nrows + 1 && (uint64_t)*q < r0 + m; q++) row_start[*q - r0] = 1;
+                enc_strdict(x, m, row_start, o);
+            } else {  // RAW bytes
                 o.b.assign(align16(kChunkHeader + m), 0);
                 ChunkWriter w(o);
                 w.header(ZF_RAW, ZF_BYTES, 0, 0, m, 0, 0);
@@ -491,7 +573,7 @@ void write_part(const PartSpec& p, const std::vector<Out>& blobs, uint8_t* dst, 
 }
 
 bool scheme_fits(int scheme, int dtype) {
-    if (dtype == ZF_BYTES) return scheme == ZF_RAW || scheme == ZF_LZ77;
+    if (dtype == ZF_BYTES) return scheme == ZF_RAW || scheme == ZF_LZ77 || scheme == ZF_STRDICT;
     if (dtype == ZF_F64) return scheme == ZF_RAW || scheme == ZF_FLOAT2INT;
     if (dtype != ZF_I32 && dtype != ZF_I64) return false;
     return scheme >= ZF_RAW && scheme <= ZF_RLE;
@@ -541,11 +623,22 @@ zf_status encode_column(const zf_plan_t& plan, const zf_column& col, zf_compress
         if (col.offsets[0] != 0) return ZF_EINVAL;
         for (uint64_t i = 0; i < col.n; i++)
             if (col.offsets[i + 1] < col.offsets[i]) return ZF_EINVAL;
-        int bs = plan.scheme == ZF_RAW ? ZF_RAW : ZF_LZ77;
+        int bs = (plan.scheme == ZF_RAW || plan.scheme == ZF_STRDICT) ? plan.scheme : ZF_LZ77;
         int os = plan.offsets_scheme < 0 ? ZF_DELTA_BP : plan.offsets_scheme;
         if (!scheme_fits(os, ZF_I32)) return ZF_EINVAL;
+        uint32_t cb = kLzBlock;
+        if (bs == ZF_STRDICT) {
+            cb = plan.chunk_rows;
+            if (cb == 0 || cb % kLzBlock || cb > kStrChunkMax) {
+                if (why) *why = "string-dictionary chunks are a multiple of 65536 bytes, at most 2^26";
+                return ZF_EINVAL;
+            }
+        }
         uint64_t nbytes = (uint64_t)(uint32_t)col.offsets[col.n];
-        specs.push_back({bs, ZF_BYTES, (const uint8_t*)col.data, nbytes, kLzBlock});
+        PartSpec bytes{bs, ZF_BYTES, (const uint8_t*)col.data, nbytes, cb};
+        bytes.offsets = col.offsets;
+        bytes.nrows = col.n;
+        specs.push_back(bytes);
         specs.push_back({os, ZF_I32, (const uint8_t*)col.offsets, col.n + 1, 65536});
     } else {
         if (!scheme_fits(plan.scheme, dt) || plan.scheme == ZF_LZ77) return ZF_EINVAL;
@@ -588,6 +681,7 @@ zf_status encode_column(const zf_plan_t& plan, const zf_column& col, zf_compress
 // tile_rows rows (bytes for a raw byte chunk).
 uint32_t tiles_of(const ChunkInfo& ch, uint32_t tile_rows) {
     if (ch.scheme == ZF_LZ77) return 1;
+    if (ch.scheme == ZF_STRDICT) return (ch.units + tile_rows - 1) / tile_rows;   // jobs of tile_rows tokens
     return (ch.rows + tile_rows - 1) / tile_rows;
 }
 
@@ -621,6 +715,7 @@ bool check_chunk(const uint8_t* c, uint64_t len, int scheme, int dtype, uint32_t
     case ZF_RLE: nsec = 3; break;
     case ZF_LZ77: nsec = (c[7] & 1) ? 1 : 3; break;
     case ZF_FLOAT2INT: nsec = 3; break;
+    case ZF_STRDICT: nsec = 3; break;
     default: return fail(why, "unknown scheme");
     }
     for (int s = 0; s < nsec; s++)
@@ -672,6 +767,28 @@ bool check_chunk(const uint8_t* c, uint64_t len, int scheme, int dtype, uint32_t
         *bmax = (uint8_t)b;
         break;
     }
+    case ZF_STRDICT: {
+        const uint64_t T = rd<uint64_t>(c + 16), ntiles = (T + kStrTile - 1) / kStrTile;
+        if (n_aux == 0 || n_aux > kStrDictMax || b != bits_of(n_aux - 1) || T > rows || (rows && T == 0) ||
+            ln[0] != 4ull * (n_aux + 1 + ntiles) || ln[2] != packed_bytes(T, b))
+            return fail(why, "string-dictionary sections");
+        // dictionary entries of 1..kStrTokenMax bytes, in order, filling s1
+        const uint8_t* d = c + off[0];
+        if (rd<uint32_t>(d) != 0 || rd<uint32_t>(d + 4ull * n_aux) != ln[1])
+            return fail(why, "string-dictionary offsets");
+        for (uint32_t k = 0; k < n_aux; k++) {
+            const uint32_t a0 = rd<uint32_t>(d + 4ull * k), a1 = rd<uint32_t>(d + 4ull * (k + 1));
+            if (a1 <= a0 || a1 - a0 > kStrTokenMax) return fail(why, "string-dictionary entry");
+        }
+        // tile starts: the first is 0, then nondecreasing and inside the chunk
+        for (uint64_t j = 0; j < ntiles; j++) {
+            const uint32_t t0 = rd<uint32_t>(d + 4ull * (n_aux + 1 + j));
+            if ((j == 0 && t0 != 0) || t0 > rows || (j && t0 < rd<uint32_t>(d + 4ull * (n_aux + j))))
+                return fail(why, "string-dictionary tile starts");
+        }
+        *bmax = (uint8_t)b;
+        break;
+    }
     case ZF_LZ77:
         if (rows > kLzBlock) return fail(why, "LZ77 block above 64 KiB");
         if ((c[7] & 1) && ln[0] != rows) return fail(why, "raw LZ77 block length");
@@ -718,8 +835,10 @@ zf_status parse_serialized(zf_compressed* c, std::string* why) {
             fail(why, "column above 2^48 rows");
             return ZF_ECORRUPT;
         }
-        if (pi.dtype == ZF_BYTES && pi.chunk_rows != kLzBlock) {
-            fail(why, "byte chunks must be 65536 bytes");
+        if (pi.dtype == ZF_BYTES && (pi.scheme == ZF_STRDICT
+                                         ? (pi.chunk_rows % kLzBlock || pi.chunk_rows > kStrChunkMax)
+                                         : pi.chunk_rows != kLzBlock)) {
+            fail(why, "byte chunks must be 65536 bytes (string dictionary: a multiple, at most 2^26)");
             return ZF_ECORRUPT;
         }
         pi.first_chunk = (uint32_t)c->chunks.size();
@@ -739,6 +858,7 @@ zf_status parse_serialized(zf_compressed* c, std::string* why) {
             }
             expect += ch.bytes;
             if (!check_chunk(h + ch.off, ch.bytes, pi.scheme, pi.dtype, ch.rows, &ch.bmax, why)) return ZF_ECORRUPT;
+            if (pi.scheme == ZF_STRDICT) ch.units = (uint32_t)rd<uint64_t>(h + ch.off + 16);
             ch.off += pos;
             ch.scheme = (uint8_t)pi.scheme;
             ch.dtype = (uint8_t)pi.dtype;

@@ -42,6 +42,10 @@ constexpr uint32_t kLzMinMatch = 4;
 constexpr uint32_t kLzMaxOffset = 65535;
 constexpr uint32_t kMaxDict = 65536;
 constexpr uint32_t kMaxTileRows = 16384;   // rows per warp job (16 warp tiles)
+constexpr uint32_t kStrTokenMax = 64;          // bytes of one string-dictionary token at most
+constexpr uint32_t kStrDictMax = 65536;        // string-dictionary entries at most
+constexpr uint32_t kStrTile = 1024;            // tokens per tile-start entry
+constexpr uint32_t kStrChunkMax = 1u << 26;    // bytes of one string-dictionary chunk at most
 
 inline uint64_t align16(uint64_t x) { return (x + 15) & ~uint64_t(15); }
 inline uint32_t bits_of(uint64_t x) { return x ? 64u - (uint32_t)__builtin_clzll(x) : 0u; }
@@ -57,6 +61,7 @@ struct ChunkInfo {
     uint32_t rows;
     uint8_t scheme, dtype, part;
     uint8_t bmax;     // widest bit width in the chunk (FOR/DICT: b; DELTA: widest block)
+    uint32_t units = 0;   // string dictionary: tokens of the chunk
 };
 
 struct PartInfo {

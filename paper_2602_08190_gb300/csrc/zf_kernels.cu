@@ -52,6 +52,8 @@ __device__ __forceinline__ void decode_one(const ZfDevChunk& c, const zfd::Hdr& 
     } else if constexpr (DT == ZF_F64) {
         // doubles travel as their 64-bit patterns
         if constexpr (SCHEME == ZF_RAW || SCHEME == ZF_FLOAT2INT) zfd::fp_job<int64_t, SCHEME>(c, h, r0, nrows, wsm, err);
+    } else if constexpr (DT == ZF_BYTES && SCHEME == ZF_STRDICT) {
+        zfd::strdict_job(c, h, r0, nrows, wsm, err);   // r0, nrows count tokens
     } else if constexpr (DT == ZF_BYTES && SCHEME == ZF_RAW) {
         // raw bytes: 16-byte copies
         const uint32_t lane = threadIdx.x & 31;
@@ -75,7 +77,7 @@ __device__ __noinline__ void decode_mixed(const ZfDevChunk& c, const zfd::Hdr& h
         ZF_CASE(ZF_DICT_BP, ZF_I32) ZF_CASE(ZF_DICT_BP, ZF_I64)
         ZF_CASE(ZF_DELTA_BP, ZF_I32) ZF_CASE(ZF_DELTA_BP, ZF_I64)
         ZF_CASE(ZF_RLE, ZF_I32) ZF_CASE(ZF_RLE, ZF_I64)
-        ZF_CASE(ZF_RAW, ZF_F64) ZF_CASE(ZF_FLOAT2INT, ZF_F64)
+        ZF_CASE(ZF_RAW, ZF_F64) ZF_CASE(ZF_FLOAT2INT, ZF_F64) ZF_CASE(ZF_STRDICT, ZF_BYTES)
 #undef ZF_CASE
     default:
         if ((threadIdx.x & 31) == 0) zfd::report(err, ZF_EINVAL, c.chunk_id);
@@ -149,7 +151,7 @@ KernelFn pick(int scheme, int dtype) {
         ZF_K(ZF_DICT_BP, ZF_I32) ZF_K(ZF_DICT_BP, ZF_I64)
         ZF_K(ZF_DELTA_BP, ZF_I32) ZF_K(ZF_DELTA_BP, ZF_I64)
         ZF_K(ZF_RLE, ZF_I32) ZF_K(ZF_RLE, ZF_I64)
-        ZF_K(ZF_RAW, ZF_F64) ZF_K(ZF_FLOAT2INT, ZF_F64)
+        ZF_K(ZF_RAW, ZF_F64) ZF_K(ZF_FLOAT2INT, ZF_F64) ZF_K(ZF_STRDICT, ZF_BYTES)
 #undef ZF_K
     }
     if (scheme < 0) return tiles_kernel<-1, -1, THREADS>;

@@ -321,6 +321,7 @@ void johnson_order(std::vector<Work>& work) {
             case ZF_RLE: rate = 3500; break;
             case ZF_DELTA_BP: case ZF_DICT_BP: rate = 5000; break;
             case ZF_FLOAT2INT: rate = 1500; break;
+            case ZF_STRDICT: rate = 1000; break;
             default: rate = 6000; break;
             }
             copy += (double)c.bytes / 200.0;
@@ -980,6 +981,14 @@ extern "C" zf_status zf_plan(zf_ctx* ctx, const zf_column* col, const zf_plan_op
     if (o.scheme >= 0) {
         if (o.scheme >= ZF_NSCHEMES) return ZF_EINVAL;
         p.scheme = o.scheme;
+        if (p.scheme == ZF_STRDICT && col->dtype == ZF_BYTES) {
+            // string-dictionary chunks: o.chunk_rows bytes (a multiple of 64 KiB), else 4 MiB
+            p.chunk_rows = o.chunk_rows ? o.chunk_rows : (4u << 20);
+            if (p.chunk_rows % zf::kLzBlock || p.chunk_rows > zf::kStrChunkMax) {
+                if (ctx) ctx->last_error = "string-dictionary chunks are a multiple of 65536 bytes, at most 2^26";
+                return ZF_EINVAL;
+            }
+        }
     } else if (o.selector == 0) {
         p.scheme = zf::heuristic_scheme(*col, p.chunk_rows);
     } else if (o.selector == 1) {

@@ -105,6 +105,72 @@ def test_raw_string_columns(gpu):
         g.close()
 
 
+def test_strdict_strings(gpu):
+    """String dictionary + bit-packing: library- and oracle-encoded text
+    columns, ragged chunks, long and byte-heavy tokens, through the transfer,
+    resident and batched paths."""
+    rng = np.random.default_rng(12)
+    raw = rng.integers(0, 256, 150000).astype(np.uint8)
+    cases = [(W.text_column(7, 1000003), 1 << 20), (W.text_column(8, 300001), 65536),
+             ((raw, np.array([0, 70000, 70000, 150000], np.int32)), 131072),
+             ((np.frombuffer(b"xyz", np.uint8).copy(), np.array([0, 3], np.int32)), 65536)]
+    for (t, o), cb in cases:
+        for enc in ("library", "oracle"):
+            if enc == "library":
+                col = zf.Column(t, o)
+                h = zf.zf_compress_host(zf.zf_plan(None, col, scheme=zf.ZF_STRDICT, chunk_rows=cb), col)
+            else:
+                h = zf.zf_compressed_from_bytes(oracle.encode_strings(t, o, cb, scheme=oracle.STRDICT))
+            try:
+                for resident in (False, True):
+                    got_t, got_o = gpu.decode([h], out_specs(t, o), resident=resident)
+                    assert np.array_equal(got_t, t), (enc, cb, resident)
+                    assert np.array_equal(got_o, o), (enc, cb, resident)
+            finally:
+                zf.zf_compressed_free(h)
+    t, o = cases[0][0]
+    g = Gpu(flags=zf.ZF_KCFG_BATCHED)
+    h = zf.zf_compressed_from_bytes(oracle.encode_strings(t, o, 1 << 18, scheme=oracle.STRDICT))
+    try:
+        got_t, got_o = g.decode([h], out_specs(t, o))
+        assert np.array_equal(got_t, t) and np.array_equal(got_o, o)
+    finally:
+        zf.zf_compressed_free(h)
+        g.close()
+
+
+def test_strdict_device_detects_corrupt_streams(gpu):
+    """A code past the dictionary, and a tile start that the lengths do not
+    reach (both pass the host's structural checks): ZF_ECORRUPT, no fault."""
+    import struct
+    from oracle_pins import chunks_of
+    t, o = W.text_column(9, 400000)
+    b = oracle.encode_strings(t, o, 1 << 18, scheme=oracle.STRDICT)
+    off, ln, r0, rows, ch = chunks_of(oracle.default(), b)[0]
+    nd, bw = ch["n_aux"], ch["bw"]
+    assert nd < (1 << bw)                                   # a free code exists above the dictionary
+    c2 = off + ch["offs"][2]
+    def code_past_dictionary(bb):
+        w = int.from_bytes(bb[c2:c2 + 4], "little")
+        w = (w & ~((1 << bw) - 1)) | ((1 << bw) - 1)        # token 0 takes the largest code
+        bb[c2:c2 + 4] = w.to_bytes(4, "little")
+    tile1 = off + ch["offs"][0] + 4 * (nd + 2)              # start of the second 1024-token tile
+    def tile_start_plus_one(bb):
+        struct.pack_into("<I", bb, tile1, struct.unpack_from("<I", bb, tile1)[0] + 1)
+    for fn in (code_past_dictionary, tile_start_plus_one):
+        h = zf.zf_compressed_from_bytes(_corrupt(b, fn))
+        try:
+            gpu.decode([h], out_specs(t, o), expect=zf.ZF_ECORRUPT)
+        finally:
+            zf.zf_compressed_free(h)
+    h = zf.zf_compressed_from_bytes(b)                      # the context stays usable
+    try:
+        got_t, got_o = gpu.decode([h], out_specs(t, o))
+        assert np.array_equal(got_t, t) and np.array_equal(got_o, o)
+    finally:
+        zf.zf_compressed_free(h)
+
+
 def test_lz77_edge_blocks(gpu):
     cases = [
         np.frombuffer(b"a" * 70000, np.uint8),                            # one long overlapping run

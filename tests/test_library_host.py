@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import zf_workloads as W
-from oracle_pins import chunks_of
+from oracle_pins import chunks_of, parse_chunk
 
 zf = pytest.importorskip("paper_2602_08190_gb300")
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -192,3 +192,45 @@ def test_column_rejects_unsupported_dtypes():
     with pytest.raises(TypeError):
         zf.Column(np.zeros(8, np.int32), np.array([0, 8], np.int32))   # string bytes must be uint8
     assert zf.Column(np.zeros(8, np.float64)).c.dtype == zf.ZF_F64
+
+
+def test_strdict_bytes_equal_the_oracle():
+    """String dictionary + bit-packing: the library's encoder writes the same
+    bytes as the oracle (the encoding is canonical), for several chunk sizes."""
+    cases = [(W.text_column(3, 1000003), 1 << 20), (W.text_column(4, 200000), 65536),
+             ((np.frombuffer(b"ab cdab", np.uint8).copy(), np.array([0, 5, 7], np.int32)), 65536)]
+    rng = np.random.default_rng(3)
+    raw = rng.integers(0, 256, 150000).astype(np.uint8)              # few spaces: long tokens, byte-heavy
+    cases.append(((raw, np.array([0, 70000, 70000, 150000], np.int32)), 131072))
+    for (t, o), cb in cases:
+        col = zf.Column(t, o)
+        h = zf.zf_compress_host(zf.zf_plan(None, col, scheme=zf.ZF_STRDICT, chunk_rows=cb), col)
+        try:
+            lb = zf.zf_compressed_bytes(h)
+            assert lb == oracle.encode_strings(t, o, cb, scheme=oracle.STRDICT)
+            t2, o2 = oracle.decode_strings(lb)
+            assert np.array_equal(t2, t) and np.array_equal(o2, o)
+        finally:
+            zf.zf_compressed_free(h)
+
+
+def test_strdict_plan_and_host_checks():
+    t, o = W.text_column(5, 300000)
+    col = zf.Column(t, o)
+    assert zf.zf_plan(None, col, scheme=zf.ZF_STRDICT).chunk_rows == 4 << 20
+    for cb in (65536 + 1024, 1 << 27):
+        with pytest.raises(zf.ZfError):
+            zf.zf_plan(None, col, scheme=zf.ZF_STRDICT, chunk_rows=cb)
+    b = oracle.encode_strings(t, o, 131072, scheme=oracle.STRDICT)
+    off = oracle.chunk_span(b, 0)[0]
+    ch = parse_chunk(b[off:off + 64])
+    nd = ch["n_aux"]
+    bad_cases = []
+    bb = bytearray(b); struct.pack_into("<I", bb, off + ch["offs"][0] + 4, 0); bad_cases.append(bb)  # empty entry
+    bb = bytearray(b); struct.pack_into("<I", bb, off + ch["offs"][0] + 4 * (nd + 1), 3); bad_cases.append(bb)  # tile 0 at 3
+    bb = bytearray(b); bb[off + 6] += 1; bad_cases.append(bb)                                        # code width
+    bb = bytearray(b); struct.pack_into("<I", bb, 12, 65536 + 1024); bad_cases.append(bb)          # chunk bytes
+    for bb in bad_cases:
+        with pytest.raises(zf.ZfError) as e:
+            zf.zf_compressed_from_bytes(bytes(bb))
+        assert e.value.status == zf.ZF_ECORRUPT
