@@ -14,6 +14,7 @@
 
 #include "zf_device.cuh"
 #include "zf_launch.h"
+#include "zf_strdict.cuh"
 
 namespace {
 
