@@ -20,11 +20,11 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-RAW, FOR_BP, DICT_BP, DELTA_BP, RLE, LZ77, FLOAT2INT, STRDICT = range(8)
+RAW, FOR_BP, DICT_BP, DELTA_BP, RLE, LZ77, FLOAT2INT, STRDICT, ANS = range(9)
 I32, I64, BYTES, F64 = range(4)
 OK, EINVAL, ENOMEM, ECUDA, ECORRUPT = 0, 1, 2, 3, 4
 SCHEMES = {"raw": RAW, "for_bp": FOR_BP, "dict_bp": DICT_BP, "delta_bp": DELTA_BP, "rle": RLE, "lz77": LZ77,
-           "float2int": FLOAT2INT, "strdict": STRDICT}
+           "float2int": FLOAT2INT, "strdict": STRDICT, "ans": ANS}
 _DT = {np.dtype(np.int32): I32, np.dtype(np.int64): I64, np.dtype(np.uint8): BYTES, np.dtype(np.float64): F64}
 _NP = {I32: np.int32, I64: np.int64, BYTES: np.uint8, F64: np.float64}
 

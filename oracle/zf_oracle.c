@@ -15,6 +15,9 @@
  *   Float2Int (+ bit-packing)          Section 2.1 ("Float2Int"); Table 2
  *   String dictionary (+ bit-packing)  Section 2.1 (dictionary encoding); Section 5.3.1
  *                                      (the comment column's words as dictionary codes)
+ *   Dictionary + ANS                   Section 2.1 (entropy-based algorithms, ANS);
+ *                                      Section 3.1 (ANS decode as the Non-Parallel example);
+ *                                      the rANS coder itself is Duda's published method
  *   Independent chunks                 Section 3.1 (Non-Parallel "file chunking")
  *
  * Decoders are the definitions written out: values are read bit by bit,
@@ -39,7 +42,7 @@
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_ECORRUPT = 4 };
 /* ---- schemes and dtypes ---- */
 enum { ORC_RAW = 0, ORC_FOR_BP = 1, ORC_DICT_BP = 2, ORC_DELTA_BP = 3, ORC_RLE = 4, ORC_LZ77 = 5, ORC_F2I = 6,
-       ORC_STRDICT = 7 };
+       ORC_STRDICT = 7, ORC_ANS = 8 };
 enum { ORC_I32 = 0, ORC_I64 = 1, ORC_BYTES = 2, ORC_F64 = 3 };
 
 #define COL_MAGIC 0x4C4F435Au   /* "ZCOL" */
@@ -52,6 +55,10 @@ enum { ORC_I32 = 0, ORC_I64 = 1, ORC_BYTES = 2, ORC_F64 = 3 };
 #define STR_TOKEN_MAX 64u     /* bytes in one string-dictionary token at most */
 #define STR_DICT_MAX 65536u   /* dictionary entries at most */
 #define STR_TILE 1024u        /* tokens per tile-start entry */
+#define ANS_SCALE 12u         /* frequencies sum to M = 2^12 */
+#define ANS_M (1u << ANS_SCALE)
+#define ANS_L (1u << 23)      /* states stay in [L, 256 L) */
+#define ANS_SUB 4096u         /* symbols per independent stream */
 
 /* ------------------------------------------------------------------------- */
 /* little-endian byte helpers                                                */
@@ -162,6 +169,7 @@ static uint64_t chunk_bound(int scheme, int dtype, uint64_t rows) {
     case ORC_LZ77: return b + rows + rows / 2 + 64;
     case ORC_F2I: return b + rows * (8 + 4 + 8) + 32;
     case ORC_STRDICT: return b + 4 * (rows + 2 + rows / STR_TILE + 1) + rows + 2 * rows + 32;
+    case ORC_ANS: return b + 256 * sz + 512 + 8 * (rows / ANS_SUB + 2) + 2 * rows + 32;
     }
     return 0;
 }
@@ -448,6 +456,109 @@ static uint64_t enc_f2i(uint8_t* p, const void* x, uint32_t m) {
 }
 
 
+/* ---- dictionary + rANS ----
+ * The chunk's distinct values (at most 256, sorted) are the symbols; each
+ * row is coded as its rank.  rANS (Duda's range variant, byte-wise
+ * renormalization): symbol s has frequency f_s >= 1 and cumulative frequency
+ * c_s = f_0 + ... + f_{s-1} out of M; a state x maps to
+ *   C(s, x) = floor(x / f_s) * M + (x mod f_s) + c_s
+ * and back, with slot = x mod M and s the symbol whose [c_s, c_s + f_s)
+ * holds the slot, to D(x) = f_s * floor(x / M) + slot - c_s.  States stay in
+ * [L, 256 L): before C the encoder emits the low byte of x while
+ * x >= (L / M) * 256 * f_s; after D the decoder reads a byte while x < L.
+ * Every ANS_SUB rows form an independent stream: encoding runs from its last
+ * row to its first starting at x = L; the stream is the final state (4 bytes,
+ * little-endian) followed by the emitted bytes, last emitted first, so the
+ * decoder reads it front to back and ends at x = L.
+ * Sections: s0 = the sorted values; s1 = u16 f_s per symbol (padded to 4
+ * bytes), then u32 start of each stream in s2 and the end of the last; s2 =
+ * the streams.  Header: b = 12 (log2 M), n_aux = symbols, reference = streams. */
+
+/* Frequencies out of M for counts cnt[0..nd) of n rows: f_s = max(1,
+ * floor(cnt_s * M / n)); a shortfall goes to the most frequent symbol (the
+ * first on a tie); an excess from the max(1) rule is taken one at a time
+ * from the largest f_s above 1 (the first on a tie). */
+static void ans_freqs(const uint32_t* cnt, uint32_t nd, uint32_t n, uint32_t* f) {
+    uint64_t F = 0;
+    for (uint32_t k = 0; k < nd; k++) {
+        f[k] = (uint32_t)((uint64_t)cnt[k] * ANS_M / n);
+        if (f[k] == 0) f[k] = 1;
+        F += f[k];
+    }
+    if (F < ANS_M) {
+        uint32_t best = 0;
+        for (uint32_t k = 1; k < nd; k++)
+            if (cnt[k] > cnt[best]) best = k;
+        f[best] += (uint32_t)(ANS_M - F);
+        F = ANS_M;
+    }
+    while (F > ANS_M) {
+        uint32_t best = nd;
+        for (uint32_t k = 0; k < nd; k++)
+            if (f[k] > 1 && (best == nd || f[k] > f[best])) best = k;
+        f[best]--;
+        F--;
+    }
+}
+
+/* one stream of n symbols; returns its length in bytes */
+static uint32_t ans_encode(const uint32_t* sym, uint32_t n, const uint32_t* f, const uint32_t* c, uint8_t* out,
+                           uint8_t* tmp) {
+    uint32_t x = ANS_L, k = 0;
+    for (uint32_t i = n; i-- > 0;) {
+        uint32_t s = sym[i];
+        uint64_t xmax = ((uint64_t)(ANS_L >> ANS_SCALE) << 8) * f[s];
+        while (x >= xmax) { tmp[k++] = (uint8_t)(x & 0xFF); x >>= 8; }
+        x = (x / f[s]) * ANS_M + (x % f[s]) + c[s];
+    }
+    put_u32(out, x);
+    for (uint32_t j = 0; j < k; j++) out[4 + j] = tmp[k - 1 - j];
+    return 4 + k;
+}
+
+static uint64_t enc_ans(uint8_t* p, int dtype, const void* x, uint32_t m, int* err) {
+    int64_t* s = (int64_t*)malloc(sizeof(int64_t) * (m ? m : 1));
+    uint32_t* sym = (uint32_t*)malloc(sizeof(uint32_t) * (m ? m : 1));
+    uint8_t* tmp = (uint8_t*)malloc(2ull * ANS_SUB + 16);
+    uint8_t* streams = (uint8_t*)malloc(2ull * m + 8ull * (m / ANS_SUB + 1) + 16);
+    if (!s || !sym || !tmp || !streams) { free(s); free(sym); free(tmp); free(streams); *err = ORC_ENOMEM; return 0; }
+    for (uint32_t i = 0; i < m; i++) s[i] = load_val(x, dtype, i);
+    qsort(s, m, sizeof(int64_t), cmp_i64);
+    uint32_t nd = 0;
+    for (uint32_t i = 0; i < m; i++)
+        if (i == 0 || s[i] != s[nd - 1]) s[nd++] = s[i];
+    if (nd > 256) { free(s); free(sym); free(tmp); free(streams); *err = ORC_EINVAL; return 0; }
+    uint32_t cnt[256] = {0}, f[256], c[256];
+    for (uint32_t i = 0; i < m; i++) {
+        int64_t v = load_val(x, dtype, i);
+        uint32_t lo = 0, hi = nd;
+        while (lo < hi) { uint32_t mid = (lo + hi) / 2; if (s[mid] < v) lo = mid + 1; else hi = mid; }
+        sym[i] = lo;
+        cnt[lo]++;
+    }
+    if (nd) ans_freqs(cnt, nd, m, f);
+    for (uint32_t k = 0, acc = 0; k < nd; k++) { c[k] = acc; acc += f[k]; }
+    uint32_t K = (m + ANS_SUB - 1) / ANS_SUB;
+    chunk_w w = {p, 64};
+    chunk_header(p, ORC_ANS, dtype, ANS_SCALE, 0, m, nd, K);
+    uint64_t o0 = sec_begin(&w, 0, (uint64_t)nd * size_of(dtype));
+    for (uint32_t k = 0; k < nd; k++) store_val(p + o0, dtype, k, (uint64_t)s[k]);
+    uint64_t fbytes = (2ull * nd + 3) / 4 * 4;
+    uint64_t o1 = sec_begin(&w, 1, fbytes + 4ull * (K + 1));
+    for (uint32_t k = 0; k < nd; k++) put_u16(p + o1 + 2ull * k, f[k]);
+    uint64_t pos = 0;
+    for (uint32_t j = 0; j < K; j++) {
+        uint32_t r0 = j * ANS_SUB, n = m - r0 < ANS_SUB ? m - r0 : ANS_SUB;
+        put_u32(p + o1 + fbytes + 4ull * j, (uint32_t)pos);
+        pos += ans_encode(sym + r0, n, f, c, streams + pos, tmp);
+    }
+    put_u32(p + o1 + fbytes + 4ull * K, (uint32_t)pos);
+    uint64_t o2 = sec_begin(&w, 2, pos);
+    memcpy(p + o2, streams, pos);
+    free(s); free(sym); free(tmp); free(streams);
+    return align16(w.end);
+}
+
 /* ---- string dictionary + bit-packing (bytes) ----
  * The chunk's bytes are cut into tokens: a token ends after a space byte,
  * before the first byte of a row, after STR_TOKEN_MAX bytes, or at the end of
@@ -545,7 +656,7 @@ static int scheme_ok(int scheme, int dtype) {
     if (dtype == ORC_BYTES) return scheme == ORC_RAW || scheme == ORC_LZ77 || scheme == ORC_STRDICT;
     if (dtype == ORC_F64) return scheme == ORC_RAW || scheme == ORC_F2I;
     if (dtype != ORC_I32 && dtype != ORC_I64) return 0;
-    return scheme >= ORC_RAW && scheme <= ORC_RLE;
+    return (scheme >= ORC_RAW && scheme <= ORC_RLE) || scheme == ORC_ANS;
 }
 
 /* Encode n values (BYTES: n bytes) in chunks of chunk_rows rows.
@@ -574,6 +685,7 @@ int orc_encode(int scheme, int dtype, const void* data, uint64_t n, uint32_t chu
         case ORC_LZ77: len = enc_lz(p, x, m); break;
         case ORC_F2I: len = enc_f2i(p, x, m); break;
         case ORC_STRDICT: return ORC_EINVAL;   /* needs the row offsets: orc_encode_strdict */
+        case ORC_ANS: len = enc_ans(p, dtype, x, m, &err); break;
         }
         if (err) return err;
         uint8_t* d = out + 64 + 32 * c;
@@ -740,6 +852,46 @@ int orc_decode_chunk(const uint8_t* c, uint64_t len, void* out, uint64_t out_cap
             uint64_t bits = get_u64(s2 + 8ull * k);
             memcpy(&o[pos], &bits, 8);
         }
+        return ORC_OK;
+    }
+    case ORC_ANS: {
+        /* each stream: read the state, then per row find the symbol of slot
+         * x mod M, emit its value, step x = f * (x / M) + slot - c and read
+         * bytes while x < L; the stream must end at x = L with every byte read */
+        uint32_t nd = n_aux;
+        uint64_t K = ref, fbytes = (2ull * nd + 3) / 4 * 4;
+        if (!sec_ok(c, len, 0) || !sec_ok(c, len, 1) || !sec_ok(c, len, 2) || b != ANS_SCALE || nd == 0 ||
+            nd > 256 || l0 != (uint64_t)nd * sz || K != (m + ANS_SUB - 1) / ANS_SUB || l1 != fbytes + 4 * (K + 1))
+            return ORC_ECORRUPT;
+        uint32_t f[256], cum[256], acc = 0;
+        for (uint32_t k = 0; k < nd; k++) {
+            f[k] = get_u16(s1 + 2ull * k);
+            if (f[k] == 0) return ORC_ECORRUPT;
+            cum[k] = acc;
+            acc += f[k];
+        }
+        if (acc != ANS_M) return ORC_ECORRUPT;
+        const uint8_t* st = s1 + fbytes;
+        if (get_u32(st) != 0 || get_u32(st + 4 * K) != l2) return ORC_ECORRUPT;
+        for (uint64_t j = 0; j < K; j++) {
+            uint32_t a0 = get_u32(st + 4 * j), a1 = get_u32(st + 4 * (j + 1));
+            if (a1 < a0 || a1 - a0 < 4) return ORC_ECORRUPT;
+            const uint8_t* q = s2 + a0;
+            uint32_t ql = a1 - a0, qp = 4, x = get_u32(q);
+            uint32_t r0 = (uint32_t)j * ANS_SUB, n = m - r0 < ANS_SUB ? m - r0 : ANS_SUB;
+            for (uint32_t i = 0; i < n; i++) {
+                uint32_t slot = x & (ANS_M - 1), sym = 0;
+                while (!(cum[sym] <= slot && slot < cum[sym] + f[sym])) sym++;
+                store_val(out, dtype, r0 + i, (uint64_t)load_val(s0, dtype, sym) & msk);
+                x = f[sym] * (x >> ANS_SCALE) + slot - cum[sym];
+                while (x < ANS_L) {
+                    if (qp >= ql) return ORC_ECORRUPT;
+                    x = (x << 8) | q[qp++];
+                }
+            }
+            if (x != ANS_L || qp != ql) return ORC_ECORRUPT;
+        }
+        (void)flags;
         return ORC_OK;
     }
     case ORC_STRDICT: {

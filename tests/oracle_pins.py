@@ -599,4 +599,106 @@ def pin_strdict_rejects_corrupt(orc):
         else:
             raise AssertionError("malformed string-dictionary chunk accepted")
 
+
+# ---- dictionary + ANS (Section 2.1 entropy-based algorithms; Section 3.1 takes
+# ---- ANS decode as the Non-Parallel example; the coder is Duda's rANS) ----
+
+def _ans_parts(orc, x, chunk_rows):
+    """(frequencies, stream starts, streams, state words) of every chunk."""
+    buf = orc.encode(x, O.ANS, chunk_rows)
+    out = []
+    for off, ln, r0, rows, ch in chunks_of(orc, buf):
+        nd, K = ch["n_aux"], ch["ref"]
+        fb = (2 * nd + 3) // 4 * 4
+        f = list(struct.unpack_from(f"<{nd}H", ch["secs"][1]))
+        starts = list(struct.unpack_from(f"<{K + 1}I", ch["secs"][1], fb))
+        out.append((ch, f, starts))
+    return buf, out
+
+
+def pin_ans_frequencies(orc):
+    # f_s = max(1, floor(count * 4096 / n)); a shortfall goes to the most
+    # frequent symbol (the first on a tie), an excess leaves the largest f_s
+    cases = [
+        (np.array([5, 7, 7, 9], np.int32), [1024, 2048, 1024]),
+        (np.array([1, 2, 3], np.int32), [1366, 1365, 1365]),
+        (np.array([0] * 9999 + [1], np.int64), [4095, 1]),
+        (np.arange(256, dtype=np.int32), [16] * 256),
+        (np.full(777, -3, np.int64), [4096]),
+        # 255 symbols once and one symbol 4000 times: floor gives 0 -> 1 for the
+        # rare ones (255), and floor(4000 * 4096 / 4255) = 3850 for the common one:
+        # 4105 in all, 9 too many, all taken from the largest
+        (np.array(list(range(255)) + [1000] * 4000, np.int32), [1] * 255 + [3841]),
+    ]
+    for x, want in cases:
+        _, parts = _ans_parts(orc, x, 1 << 20)
+        (ch, f, starts), = parts
+        assert f == want and sum(f) == 4096 and ch["bw"] == 12, (f[:4], want[:4])
+        assert np.array_equal(orc.decode(orc.encode(x, O.ANS, 1 << 20)), x)
+
+
+def pin_ans_size_is_the_information(orc):
+    # Each coding step multiplies the state by about M / f_s, so the emitted
+    # bits plus log2(final state / L) equal sum(log2(4096 / f_s)) up to
+    # 2^-11 relative per step; 16 equal symbols cost exactly 4 bits each.
+    rng = np.random.default_rng(21)
+    x = np.repeat(np.arange(16, dtype=np.int32), 256)
+    rng.shuffle(x)
+    _, ((ch, f, starts),) = _ans_parts(orc, x, 4096)
+    assert f == [256] * 16 and starts == [0, 2052] and ch["lens"][2] == 2052
+    for x in (rng.choice([65, 78, 82], 4096, p=[0.25, 0.5, 0.25]).astype(np.int32),
+              (rng.geometric(0.2, 4096) % 150).astype(np.int64)):
+        _, ((ch, f, starts),) = _ans_parts(orc, x, 4096)
+        vals = np.unique(x)
+        need = sum(np.log2(4096 / f[np.searchsorted(vals, v)]) for v in x)
+        s2 = ch["secs"][2]
+        state = struct.unpack_from("<I", s2)[0]
+        got = 8 * (len(s2) - 4) + np.log2(state) - 23
+        assert abs(got - need) <= 1 + len(x) * 2.0 ** -10, (got, need)
+
+
+def pin_ans_round_trip_and_streams(orc):
+    rng = np.random.default_rng(22)
+    cases = [
+        rng.choice([65, 78, 82], 100001, p=[0.25, 0.5, 0.25]).astype(np.int32),   # ragged, several streams
+        rng.integers(I64_MIN, I64_MAX, 256, dtype=np.int64)[rng.integers(0, 256, 9000)],
+        np.full(5000, 7, np.int64),
+        np.array([I32_MIN, I32_MAX] * 3000, np.int32),
+    ]
+    for x in cases:
+        buf, parts = _ans_parts(orc, x, 65536)
+        assert np.array_equal(orc.decode(buf), x)
+        for ch, f, starts in parts:
+            K = (ch["rows"] + 4095) // 4096
+            assert ch["ref"] == K and len(starts) == K + 1 and starts[0] == 0
+            assert starts[-1] == ch["lens"][2] and all(b - a >= 4 for a, b in zip(starts, starts[1:]))
+    try:
+        orc.encode(np.arange(257, dtype=np.int32), O.ANS, 65536)
+    except O.OracleError as err:
+        assert err.code == O.EINVAL
+    else:
+        raise AssertionError("257 distinct values accepted by the ANS encoder")
+
+
+def pin_ans_rejects_corrupt(orc):
+    x = np.random.default_rng(23).choice([1, 2, 3, 4], 9000, p=[0.4, 0.3, 0.2, 0.1]).astype(np.int32)
+    buf, ((ch, f, starts),) = _ans_parts(orc, x, 65536)
+    off = orc.chunk_span(buf, 0)[0]
+    blob = bytes(buf[off:off + orc.chunk_span(buf, 0)[1]])
+    o1, o2 = ch["offs"][1], ch["offs"][2]
+    bad = []
+    b1 = bytearray(blob); struct.pack_into("<H", b1, o1, f[0] + 1); bad.append(b1)         # sum above 4096
+    b2 = bytearray(blob); struct.pack_into("<I", b2, o1 + 8 + 4, starts[1] + 1); bad.append(b2)  # stream start
+    b3 = bytearray(blob); b3[o2 + 4] ^= 0x40; bad.append(b3)                                # a stream byte
+    b4 = bytearray(blob); b4[6] = 11; bad.append(b4)                                       # scale bits
+    for bb in bad:
+        try:
+            got = orc.decode_chunk(bytes(bb), np.int32)
+        except O.OracleError as err:
+            assert err.code == O.ECORRUPT
+        else:
+            assert not np.array_equal(got, x), "corrupt ANS chunk decoded to the column"
+            raise AssertionError("malformed ANS chunk accepted")
+
+
 PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

@@ -52,6 +52,13 @@ MUTANTS = {
     "f2i_reference_is_max": ("if (ok[i] && (!have || d[i] < mn)) { mn = d[i]; have = 1; }",
                              "if (ok[i] && (!have || d[i] > mn)) { mn = d[i]; have = 1; }"),
     "lz_no_raw_fallback": ("if ((uint64_t)nl + no + nlit >= m) {", "if (0) {"),
+    "ans_renorm_threshold_halved": ("uint64_t xmax = ((uint64_t)(ANS_L >> ANS_SCALE) << 8) * f[s];",
+                                    "uint64_t xmax = ((uint64_t)(ANS_L >> ANS_SCALE) << 7) * f[s];"),
+    "ans_shortfall_to_last_on_tie": ("            if (cnt[k] > cnt[best]) best = k;",
+                                     "            if (cnt[k] >= cnt[best]) best = k;"),
+    "ans_decode_cum_off_by_one": ("x = f[sym] * (x >> ANS_SCALE) + slot - cum[sym];",
+                                  "x = f[sym] * (x >> ANS_SCALE) + slot - cum[sym] + (sym > 0);"),
+    "ans_encode_drops_remainder": ("x = (x / f[s]) * ANS_M + (x % f[s]) + c[s];", "x = (x / f[s]) * ANS_M + c[s];"),
     "strdict_tokens_cross_rows": ("while (j < m && x[j - 1] != ' ' && !row_start[j] && j - i < STR_TOKEN_MAX) j++;",
                                   "while (j < m && x[j - 1] != ' ' && j - i < STR_TOKEN_MAX) j++;"),
     "strdict_token_cap_65": ("while (j < m && x[j - 1] != ' ' && !row_start[j] && j - i < STR_TOKEN_MAX) j++;",
