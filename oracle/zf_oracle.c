@@ -58,7 +58,7 @@ enum { ORC_I32 = 0, ORC_I64 = 1, ORC_BYTES = 2, ORC_F64 = 3 };
 #define ANS_SCALE 12u         /* frequencies sum to M = 2^12 */
 #define ANS_M (1u << ANS_SCALE)
 #define ANS_L (1u << 23)      /* states stay in [L, 256 L) */
-#define ANS_SUB 4096u         /* symbols per independent stream */
+#define ANS_SUB 512u          /* symbols per independent stream */
 
 /* ------------------------------------------------------------------------- */
 /* little-endian byte helpers                                                */

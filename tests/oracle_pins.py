@@ -638,23 +638,26 @@ def pin_ans_frequencies(orc):
 
 
 def pin_ans_size_is_the_information(orc):
-    # Each coding step multiplies the state by about M / f_s, so the emitted
-    # bits plus log2(final state / L) equal sum(log2(4096 / f_s)) up to
-    # 2^-11 relative per step; 16 equal symbols cost exactly 4 bits each.
+    # Each coding step multiplies the state by about M / f_s, so a stream's
+    # emitted bits plus log2(final state / L) equal sum(log2(4096 / f_s)) over
+    # its rows, up to 2^-11 relative per step; 16 equal symbols cost exactly
+    # 4 bits each, so every 512-row stream is 4 + 256 bytes.
     rng = np.random.default_rng(21)
     x = np.repeat(np.arange(16, dtype=np.int32), 256)
     rng.shuffle(x)
     _, ((ch, f, starts),) = _ans_parts(orc, x, 4096)
-    assert f == [256] * 16 and starts == [0, 2052] and ch["lens"][2] == 2052
+    assert f == [256] * 16 and starts == [260 * k for k in range(9)] and ch["lens"][2] == 2080
     for x in (rng.choice([65, 78, 82], 4096, p=[0.25, 0.5, 0.25]).astype(np.int32),
               (rng.geometric(0.2, 4096) % 150).astype(np.int64)):
         _, ((ch, f, starts),) = _ans_parts(orc, x, 4096)
         vals = np.unique(x)
-        need = sum(np.log2(4096 / f[np.searchsorted(vals, v)]) for v in x)
         s2 = ch["secs"][2]
-        state = struct.unpack_from("<I", s2)[0]
-        got = 8 * (len(s2) - 4) + np.log2(state) - 23
-        assert abs(got - need) <= 1 + len(x) * 2.0 ** -10, (got, need)
+        for k in range(len(starts) - 1):
+            rows = x[512 * k:512 * (k + 1)]
+            need = sum(np.log2(4096 / f[np.searchsorted(vals, v)]) for v in rows)
+            q = s2[starts[k]:starts[k + 1]]
+            got = 8 * (len(q) - 4) + np.log2(struct.unpack_from("<I", q)[0]) - 23
+            assert abs(got - need) <= 1 + len(rows) * 2.0 ** -10, (k, got, need)
 
 
 def pin_ans_round_trip_and_streams(orc):
@@ -669,7 +672,7 @@ def pin_ans_round_trip_and_streams(orc):
         buf, parts = _ans_parts(orc, x, 65536)
         assert np.array_equal(orc.decode(buf), x)
         for ch, f, starts in parts:
-            K = (ch["rows"] + 4095) // 4096
+            K = (ch["rows"] + 511) // 512
             assert ch["ref"] == K and len(starts) == K + 1 and starts[0] == 0
             assert starts[-1] == ch["lens"][2] and all(b - a >= 4 for a, b in zip(starts, starts[1:]))
     try:
