@@ -538,6 +538,12 @@ def run_profile(args, zf, torch):
         # 12 bits of the counter-based generator), FOR + 12-bit packing,
         # 65,536-row chunks
         cols = [(W.uniform_int(1, 0, 0, args.rows, 0, 4096).astype(np.int32), zf.ZF_FOR_BP, 65536)]
+    elif args.profile == "ans":
+        # a return-flag-like column: 'A', 'N', 'R' as int32 with shares 1/4, 1/2, 1/4
+        # (uniform on [0, 4) from the counter-based generator, 1 and 2 both 'N'),
+        # dictionary + ANS in 1M-row chunks
+        u = W.uniform_int(1, 11, 0, args.rows, 0, 4)
+        cols = [(np.array([65, 78, 78, 82], np.int32)[u], zf.ZF_ANS, CHUNK_ROWS)]
     elif args.profile == "float":
         # float64 prices with two decimals (log-normal cents / 100), Float2Int + packing, 1M-row chunks
         cols = [(W.decimal_prices(1, 7, 0, args.rows), zf.ZF_FLOAT2INT, CHUNK_ROWS)]
@@ -590,7 +596,7 @@ def main():
     ap.add_argument("--slots", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--no-graph", action="store_true", help="enqueue transfers call by call (no CUDA graph)")
-    ap.add_argument("--profile", choices=["keys", "dates", "both", "for", "float"], default=None,
+    ap.add_argument("--profile", choices=["keys", "dates", "both", "for", "float", "ans"], default=None,
                     help="only decode the resident column(s) --steps times (for ncu captures)")
     ap.add_argument("--rows", type=int, default=N_ROWS, help="rows per column (profile / batched runs)")
     ap.add_argument("--workload", choices=["group_parallel", "batched", "selector", "text"], default="group_parallel",

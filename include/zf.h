@@ -75,6 +75,16 @@
  *              64 bytes and at the chunk end, sorts the distinct tokens by
  *              their bytes (a prefix first), and above 65536 distinct tokens
  *              makes every byte a token
+ *     ANS      (I32/I64) n_aux = distinct values (1..256), reference =
+ *              streams K = ceil(rows/512), b = 12.  s0 = the sorted values;
+ *              s1 = u16 frequency of each value (>= 1, summing to M = 4096;
+ *              padded to 4 bytes), then u32 start of each stream in s2 and
+ *              the end of the last; s2 = the streams.  Stream k holds rows
+ *              512k.. as range ANS: a u32 state x, then bytes; per row the
+ *              value is the one whose [cumulative, cumulative + frequency)
+ *              holds x mod M, x becomes f * (x / M) + x mod M - cumulative,
+ *              and while x < 2^23 the next byte enters as x = 256 x + byte.
+ *              A stream ends at x = 2^23 with every byte read
  *   Bit-packing: value i occupies stream bits [i*b, i*b+b), least
  *   significant bit first; stream bit k is bit k%8 of byte k/8.
  */
@@ -105,7 +115,8 @@ typedef enum {
     ZF_RAW = 0, ZF_FOR_BP = 1, ZF_DICT_BP = 2, ZF_DELTA_BP = 3, ZF_RLE = 4, ZF_LZ77 = 5,
     ZF_FLOAT2INT = 6,     /* float64 columns (Section 2.1 "Float2Int", with bit-packing as in Table 2) */
     ZF_STRDICT = 7,       /* byte columns: dictionary of tokens + bit-packed codes (Section 2.1; Section 5.3.1) */
-    ZF_NSCHEMES = 8
+    ZF_ANS = 8,           /* integer columns of at most 256 values per chunk: dictionary + range ANS (Section 2.1) */
+    ZF_NSCHEMES = 9
 } zf_scheme;
 
 typedef struct zf_ctx zf_ctx;

@@ -17,7 +17,7 @@ _L = ctypes.CDLL(LIB_PATH)
 __all__ = [
     "ZF_OK", "ZF_EINVAL", "ZF_ENOMEM", "ZF_ECUDA", "ZF_ECORRUPT", "ZF_ETIMEOUT", "ZF_EUNSUPPORTED", "ZF_EBUSY",
     "ZF_I32", "ZF_I64", "ZF_BYTES", "ZF_F64", "ZF_RAW", "ZF_FOR_BP", "ZF_DICT_BP", "ZF_DELTA_BP", "ZF_RLE", "ZF_LZ77",
-    "ZF_FLOAT2INT", "ZF_STRDICT",
+    "ZF_FLOAT2INT", "ZF_STRDICT", "ZF_ANS",
     "ZF_KCFG_BATCHED", "ZF_KCFG_GRAPH", "SCHEME_NAMES", "ZfError", "zf_column", "zf_kcfg", "zf_plan_opts",
     "zf_plan_t", "zf_stats", "Column", "zf_ctx_create", "zf_ctx_destroy", "zf_last_error", "zf_ctx_set_kcfg",
     "zf_ctx_set_ring", "zf_plan", "zf_compress_host", "zf_compressed_info", "zf_compressed_free",
@@ -32,9 +32,9 @@ ZF_MLP_PARAMS, ZF_MLP_CLASSES = 7052, 12
 
 (ZF_OK, ZF_EINVAL, ZF_ENOMEM, ZF_ECUDA, ZF_ECORRUPT, ZF_ETIMEOUT, ZF_EUNSUPPORTED, ZF_EBUSY) = range(8)
 ZF_I32, ZF_I64, ZF_BYTES, ZF_F64 = range(4)
-ZF_RAW, ZF_FOR_BP, ZF_DICT_BP, ZF_DELTA_BP, ZF_RLE, ZF_LZ77, ZF_FLOAT2INT, ZF_STRDICT = range(8)
+ZF_RAW, ZF_FOR_BP, ZF_DICT_BP, ZF_DELTA_BP, ZF_RLE, ZF_LZ77, ZF_FLOAT2INT, ZF_STRDICT, ZF_ANS = range(9)
 ZF_KCFG_BATCHED, ZF_KCFG_GRAPH = 1, 2
-SCHEME_NAMES = ["raw", "for_bp", "dict_bp", "delta_bp", "rle", "lz77", "float2int", "strdict"]
+SCHEME_NAMES = ["raw", "for_bp", "dict_bp", "delta_bp", "rle", "lz77", "float2int", "strdict", "ans"]
 _STATUS = ["ok", "einval", "enomem", "ecuda", "ecorrupt", "etimeout", "eunsupported", "ebusy"]
 
 

@@ -4,8 +4,9 @@
 // validator used when a serialized column is imported.
 //
 // Codecs (Section 2.1): FOR + bit-packing, dictionary + bit-packing, delta +
-// bit-packing, run-length, LZ77.  Encoding is canonical for all but LZ77, so
-// two correct encoders produce the same bytes.
+// bit-packing, run-length, LZ77, Float2Int + bit-packing, string dictionary
+// + bit-packing, dictionary + ANS.  Encoding is canonical for all but LZ77,
+// so two correct encoders produce the same bytes.
 #include <cuda_runtime_api.h>
 
 #include <algorithm>
@@ -286,6 +287,92 @@ zf_status enc_dict(const T* x, uint32_t m, Out& o) {
     return ZF_OK;
 }
 
+// ------------------------------------------------------------------ dictionary + ANS
+// The chunk's sorted distinct values (at most kAnsMaxSymbols) are symbols,
+// coded with range ANS (Duda; byte-wise renormalization, states in
+// [kAnsL, 256 kAnsL)): encoding symbol s with frequency f and cumulative
+// frequency c out of M = 2^kAnsScale maps x to (x / f) * M + x % f + c after
+// emitting low bytes while x >= (kAnsL / M) * 256 * f.  Every kAnsStream rows
+// form a stream coded from its last row to its first from x = kAnsL and
+// stored as the final state (4 bytes) followed by the emitted bytes, the last
+// emitted first.  Frequencies: max(1, count * M / n), a shortfall to the most
+// frequent symbol (the first on a tie), an excess taken one at a time from
+// the largest frequency above 1 (the first on a tie).  Sections: s0 = values,
+// s1 = u16 frequencies (padded to 4 bytes) then u32 stream starts and end,
+// s2 = streams.
+template <class T>
+zf_status enc_ans(const T* x, uint32_t m, Out& o) {
+    std::vector<T> d(x, x + m);
+    std::sort(d.begin(), d.end());
+    d.erase(std::unique(d.begin(), d.end()), d.end());
+    if (d.size() > kAnsMaxSymbols) return ZF_EINVAL;
+    const uint32_t nd = (uint32_t)d.size(), K = (m + kAnsStream - 1) / kAnsStream;
+    std::vector<uint32_t> sym(m), cnt(nd, 0), f(nd, 0), c(nd, 0);
+    for (uint32_t i = 0; i < m; i++) {
+        sym[i] = (uint32_t)(std::lower_bound(d.begin(), d.end(), x[i]) - d.begin());
+        cnt[sym[i]]++;
+    }
+    if (nd) {
+        uint64_t total = 0;
+        for (uint32_t k = 0; k < nd; k++) {
+            f[k] = std::max<uint32_t>(1, (uint32_t)((uint64_t)cnt[k] * kAnsM / m));
+            total += f[k];
+        }
+        if (total < kAnsM) {
+            const uint32_t top = (uint32_t)(std::max_element(cnt.begin(), cnt.end()) - cnt.begin());  // first maximum
+            f[top] += (uint32_t)(kAnsM - total);
+        }
+        for (; total > kAnsM; total--) {
+            uint32_t top = nd;
+            for (uint32_t k = 0; k < nd; k++)
+                if (f[k] > 1 && (top == nd || f[k] > f[top])) top = k;
+            f[top]--;
+        }
+        for (uint32_t k = 1; k < nd; k++) c[k] = c[k - 1] + f[k - 1];
+    }
+    // streams, each written back to front into its own buffer
+    std::vector<std::vector<uint8_t>> st(K);
+    uint64_t sbytes = 0;
+    for (uint32_t j = 0; j < K; j++) {
+        const uint32_t r0 = j * kAnsStream, n = std::min(kAnsStream, m - r0);
+        std::vector<uint8_t> rev;
+        rev.reserve(2 * n + 8);
+        uint32_t s_x = kAnsL;
+        for (uint32_t i = n; i-- > 0;) {
+            const uint32_t s = sym[r0 + i];
+            const uint64_t lim = (uint64_t)(kAnsL >> kAnsScale) * 256u * f[s];
+            while (s_x >= lim) {
+                rev.push_back((uint8_t)s_x);
+                s_x >>= 8;
+            }
+            s_x = (s_x / f[s]) * kAnsM + s_x % f[s] + c[s];
+        }
+        auto& out = st[j];
+        out.resize(4 + rev.size());
+        memcpy(out.data(), &s_x, 4);
+        std::copy(rev.rbegin(), rev.rend(), out.begin() + 4);
+        sbytes += out.size();
+    }
+    const uint64_t fbytes = (2ull * nd + 3) / 4 * 4, l0 = (uint64_t)nd * sizeof(T), l1 = fbytes + 4ull * (K + 1);
+    o.b.assign(align16(align16(align16(kChunkHeader + l0) + l1) + sbytes), 0);
+    ChunkWriter w(o);
+    w.header(ZF_ANS, dtype_code<T>(), kAnsScale, 0, m, nd, K);
+    const uint64_t s0 = w.section(0, l0), s1 = w.section(1, l1), s2 = w.section(2, sbytes);
+    if (nd) memcpy(&o.b[s0], d.data(), l0);
+    for (uint32_t k = 0; k < nd; k++) {
+        const uint16_t v = (uint16_t)f[k];
+        memcpy(&o.b[s1 + 2ull * k], &v, 2);
+    }
+    uint64_t pos = 0;
+    for (uint32_t j = 0; j < K; j++) {
+        o.put32(s1 + fbytes + 4ull * j, (uint32_t)pos);
+        memcpy(o.b.data() + s2 + pos, st[j].data(), st[j].size());
+        pos += st[j].size();
+    }
+    o.put32(s1 + fbytes + 4ull * K, (uint32_t)pos);
+    return ZF_OK;
+}
+
 // ------------------------------------------------------------------ delta + BP
 template <class T>
 void enc_delta(const T* x, uint32_t m, Out& o) {
@@ -510,6 +597,7 @@ zf_status encode_part(const PartSpec& p, std::vector<Out>& blobs, std::string* w
             case ZF_DICT_BP: st = enc_dict(v, m, o); break;
             case ZF_DELTA_BP: enc_delta(v, m, o); break;
             case ZF_RLE: enc_rle(v, m, o); break;
+            case ZF_ANS: st = enc_ans(v, m, o); break;
             }
         } else {
             auto* v = reinterpret_cast<const int64_t*>(x);
@@ -519,12 +607,13 @@ zf_status encode_part(const PartSpec& p, std::vector<Out>& blobs, std::string* w
             case ZF_DICT_BP: st = enc_dict(v, m, o); break;
             case ZF_DELTA_BP: enc_delta(v, m, o); break;
             case ZF_RLE: enc_rle(v, m, o); break;
+            case ZF_ANS: st = enc_ans(v, m, o); break;
             }
         }
         if (st != ZF_OK) err = st;
     });
     if (err != ZF_OK) {
-        if (why) *why = "scheme does not fit the column (dictionary above 65,536 entries)";
+        if (why) *why = "scheme does not fit the column (dictionary above 65,536 entries, or ANS above 256 values)";
         return (zf_status)err.load();
     }
     return ZF_OK;
@@ -576,7 +665,7 @@ bool scheme_fits(int scheme, int dtype) {
     if (dtype == ZF_BYTES) return scheme == ZF_RAW || scheme == ZF_LZ77 || scheme == ZF_STRDICT;
     if (dtype == ZF_F64) return scheme == ZF_RAW || scheme == ZF_FLOAT2INT;
     if (dtype != ZF_I32 && dtype != ZF_I64) return false;
-    return scheme >= ZF_RAW && scheme <= ZF_RLE;
+    return (scheme >= ZF_RAW && scheme <= ZF_RLE) || scheme == ZF_ANS;
 }
 
 }  // namespace
@@ -682,6 +771,7 @@ zf_status encode_column(const zf_plan_t& plan, const zf_column& col, zf_compress
 uint32_t tiles_of(const ChunkInfo& ch, uint32_t tile_rows) {
     if (ch.scheme == ZF_LZ77) return 1;
     if (ch.scheme == ZF_STRDICT) return (ch.units + tile_rows - 1) / tile_rows;   // jobs of tile_rows tokens
+    if (ch.scheme == ZF_ANS) return (ch.units + kAnsStreamsPerJob - 1) / kAnsStreamsPerJob;   // 32 streams a job
     return (ch.rows + tile_rows - 1) / tile_rows;
 }
 
@@ -716,6 +806,7 @@ bool check_chunk(const uint8_t* c, uint64_t len, int scheme, int dtype, uint32_t
     case ZF_LZ77: nsec = (c[7] & 1) ? 1 : 3; break;
     case ZF_FLOAT2INT: nsec = 3; break;
     case ZF_STRDICT: nsec = 3; break;
+    case ZF_ANS: nsec = 3; break;
     default: return fail(why, "unknown scheme");
     }
     for (int s = 0; s < nsec; s++)
@@ -765,6 +856,25 @@ bool check_chunk(const uint8_t* c, uint64_t len, int scheme, int dtype, uint32_t
                 return fail(why, "Float2Int exception rows");
         }
         *bmax = (uint8_t)b;
+        break;
+    }
+    case ZF_ANS: {
+        const uint64_t K = rd<uint64_t>(c + 16), fb = (2ull * n_aux + 3) / 4 * 4;
+        if (b != kAnsScale || n_aux == 0 || n_aux > kAnsMaxSymbols || ln[0] != (uint64_t)n_aux * sz ||
+            K != (rows + kAnsStream - 1) / kAnsStream || ln[1] != fb + 4 * (K + 1))
+            return fail(why, "ANS sections");
+        // frequencies of at least 1 that fill M; streams of at least the 4 state bytes that fill s2
+        uint32_t total = 0;
+        for (uint32_t k = 0; k < n_aux; k++) {
+            const uint32_t fk = rd<uint16_t>(c + off[1] + 2ull * k);
+            if (fk == 0) return fail(why, "ANS frequency");
+            total += fk;
+        }
+        if (total != kAnsM) return fail(why, "ANS frequencies do not fill M");
+        const uint8_t* st = c + off[1] + fb;
+        if (rd<uint32_t>(st) != 0 || rd<uint32_t>(st + 4 * K) != ln[2]) return fail(why, "ANS stream table");
+        for (uint64_t j = 0; j < K; j++)
+            if (rd<uint32_t>(st + 4 * (j + 1)) < rd<uint32_t>(st + 4 * j) + 4ull) return fail(why, "ANS stream");
         break;
     }
     case ZF_STRDICT: {
@@ -858,7 +968,7 @@ zf_status parse_serialized(zf_compressed* c, std::string* why) {
             }
             expect += ch.bytes;
             if (!check_chunk(h + ch.off, ch.bytes, pi.scheme, pi.dtype, ch.rows, &ch.bmax, why)) return ZF_ECORRUPT;
-            if (pi.scheme == ZF_STRDICT) ch.units = (uint32_t)rd<uint64_t>(h + ch.off + 16);
+            if (pi.scheme == ZF_STRDICT || pi.scheme == ZF_ANS) ch.units = (uint32_t)rd<uint64_t>(h + ch.off + 16);
             ch.off += pos;
             ch.scheme = (uint8_t)pi.scheme;
             ch.dtype = (uint8_t)pi.dtype;

@@ -46,6 +46,12 @@ constexpr uint32_t kStrTokenMax = 64;          // bytes of one string-dictionary
 constexpr uint32_t kStrDictMax = 65536;        // string-dictionary entries at most
 constexpr uint32_t kStrTile = 1024;            // tokens per tile-start entry
 constexpr uint32_t kStrChunkMax = 1u << 26;    // bytes of one string-dictionary chunk at most
+constexpr uint32_t kAnsMaxSymbols = 256;       // ANS: distinct values of a chunk at most
+constexpr uint32_t kAnsScale = 12;             // ANS: frequencies sum to M = 2^12
+constexpr uint32_t kAnsM = 1u << kAnsScale;
+constexpr uint32_t kAnsL = 1u << 23;           // ANS: states stay in [L, 256 L)
+constexpr uint32_t kAnsStream = 512;           // ANS: rows per independent stream
+constexpr uint32_t kAnsStreamsPerJob = 32;     // ANS: one stream per lane of a warp job
 
 inline uint64_t align16(uint64_t x) { return (x + 15) & ~uint64_t(15); }
 inline uint32_t bits_of(uint64_t x) { return x ? 64u - (uint32_t)__builtin_clzll(x) : 0u; }
@@ -61,7 +67,7 @@ struct ChunkInfo {
     uint32_t rows;
     uint8_t scheme, dtype, part;
     uint8_t bmax;     // widest bit width in the chunk (FOR/DICT: b; DELTA: widest block)
-    uint32_t units = 0;   // string dictionary: tokens of the chunk
+    uint32_t units = 0;   // string dictionary: tokens of the chunk; ANS: streams
 };
 
 struct PartInfo {

@@ -23,5 +23,7 @@ struct TileLaunch {
 uint32_t warp_smem_bytes(int scheme, int dtype, uint32_t bmax);
 cudaError_t launch_tiles(const TileLaunch& L, cudaStream_t s);
 cudaError_t launch_lz(const ZfDevChunk* chunks, uint32_t n, uint32_t* err, int num_sms, cudaStream_t s);
+// ANS chunks: njobs warp jobs of up to 32 streams (chunk descriptors carry tile0 in jobs).
+cudaError_t launch_ans(const ZfDevChunk* chunks, uint32_t nchunks, uint32_t njobs, uint32_t* err, cudaStream_t s);
 
 }  // namespace zf

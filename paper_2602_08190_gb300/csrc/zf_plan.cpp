@@ -18,6 +18,7 @@ void scheme_sizes(const T* x, uint64_t n, uint32_t chunk_rows, uint64_t out[ZF_N
     out[ZF_LZ77] = ~0ull;
     out[ZF_FLOAT2INT] = ~0ull;
     out[ZF_STRDICT] = ~0ull;
+    out[ZF_ANS] = ~0ull;
     for (uint64_t r0 = 0; r0 < n; r0 += chunk_rows) {
         uint32_t m = (uint32_t)std::min<uint64_t>(chunk_rows, n - r0);
         const T* y = x + r0;

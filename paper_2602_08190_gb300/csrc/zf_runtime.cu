@@ -242,6 +242,8 @@ void build_groups(const zf_ctx* ctx, const std::vector<Work>& w, size_t b, size_
         int s = w[i].ch->scheme, d = w[i].ch->dtype;
         if (s == ZF_LZ77) {
             d = ZF_BYTES;
+        } else if (s == ZF_ANS) {
+            // ANS streams have their own kernel, batched or not
         } else if (batched) {
             s = -1;
             d = -1;
@@ -256,9 +258,10 @@ void build_groups(const zf_ctx* ctx, const std::vector<Work>& w, size_t b, size_
         Group g{key.first, key.second, (uint32_t)desc.size(), 0, 0, 16, geo.tile_rows, geo.threads};
         for (size_t i = b; i < e; i++) {
             int s = w[i].ch->scheme, d = w[i].ch->dtype;
-            bool lz = s == ZF_LZ77;
-            bool match = lz ? key.first == ZF_LZ77 : (key.first < 0 ? true : (key.first == s && key.second == d));
-            if (!match || (key.first < 0 && lz)) continue;
+            bool lz = s == ZF_LZ77, own = lz || s == ZF_ANS;   // chunks with a kernel of their own
+            bool match = lz ? key.first == ZF_LZ77
+                            : (key.first < 0 ? true : (key.first == s && key.second == d));
+            if (!match || (key.first < 0 && own)) continue;
             ZfDevChunk dc{};
             dc.blob = w[i].dev;
             dc.dst = w[i].dst;
@@ -287,6 +290,8 @@ zf_status launch_groups(zf_ctx* ctx, const std::vector<Group>& groups, const ZfD
         cudaError_t e;
         if (g.scheme == ZF_LZ77) {
             e = zf::launch_lz(dchunks, g.count, ctx->d_errw, ctx->num_sms, stream);
+        } else if (g.scheme == ZF_ANS) {
+            e = zf::launch_ans(dchunks, g.count, g.ntiles, ctx->d_errw, stream);
         } else {
             uint32_t smem = ((g.warp_smem + 15) & ~15u) * (g.threads / 32);
             zf::TileLaunch L{dchunks, g.count, g.ntiles, g.scheme, g.dtype, g.tile_rows, g.threads,
@@ -322,6 +327,7 @@ void johnson_order(std::vector<Work>& work) {
             case ZF_DELTA_BP: case ZF_DICT_BP: rate = 5000; break;
             case ZF_FLOAT2INT: rate = 1500; break;
             case ZF_STRDICT: rate = 1000; break;
+            case ZF_ANS: rate = 500; break;
             default: rate = 6000; break;
             }
             copy += (double)c.bytes / 200.0;

@@ -171,6 +171,60 @@ def test_strdict_device_detects_corrupt_streams(gpu):
         zf.zf_compressed_free(h)
 
 
+def test_ans_columns(gpu):
+    """Dictionary + ANS: library- and oracle-encoded low-cardinality columns
+    (ragged chunks and streams, one value, 256 values, type extremes) through
+    the transfer, resident and batched paths; a flipped stream byte is
+    reported, and the context stays usable."""
+    rng = np.random.default_rng(31)
+    cases = [
+        (rng.choice([65, 78, 82], 300001, p=[0.25, 0.5, 0.25]).astype(np.int32), 1 << 17),
+        (rng.integers(-(1 << 63), (1 << 63) - 1, 256, dtype=np.int64)[rng.integers(0, 256, 70000)], 16384),
+        (np.full(5000, 7, np.int64), 4096),
+        (np.array([-2**31, 2**31 - 1] * 3001, np.int32), 2048),
+        ((rng.geometric(0.05, 200003) % 256).astype(np.int32), 1 << 20),
+    ]
+    for x, cr in cases:
+        for enc in ("library", "oracle"):
+            if enc == "library":
+                col = zf.Column(x)
+                h = zf.zf_compress_host(zf.zf_plan(None, col, scheme=zf.ZF_ANS, chunk_rows=cr), col)
+            else:
+                h = zf.zf_compressed_from_bytes(oracle.encode(x, oracle.ANS, cr))
+            try:
+                for resident in (False, True):
+                    got, = gpu.decode([h], out_specs(x), resident=resident)
+                    assert np.array_equal(got, x), (enc, cr, resident)
+            finally:
+                zf.zf_compressed_free(h)
+    x, cr = cases[0]
+    g = Gpu(flags=zf.ZF_KCFG_BATCHED)
+    h = zf.zf_compressed_from_bytes(oracle.encode(x, oracle.ANS, cr))
+    h2 = compress(W.sorted_keys(3, 100000), zf.ZF_DELTA_BP, 65536)       # a mixed call
+    try:
+        got, got2 = g.decode([h, h2], out_specs(x) + out_specs(W.sorted_keys(3, 100000)))
+        assert np.array_equal(got, x) and np.array_equal(got2, W.sorted_keys(3, 100000))
+    finally:
+        zf.zf_compressed_free(h)
+        zf.zf_compressed_free(h2)
+        g.close()
+    from oracle_pins import chunks_of
+    b = oracle.encode(x, oracle.ANS, cr)
+    off, ln, r0, rows, ch = chunks_of(oracle.default(), b)[0]
+    bad = _corrupt(b, lambda bb: bb.__setitem__(off + ch["offs"][2] + 9, bb[off + ch["offs"][2] + 9] ^ 0x21))
+    h = zf.zf_compressed_from_bytes(bad)
+    try:
+        gpu.decode([h], out_specs(x), expect=zf.ZF_ECORRUPT)
+    finally:
+        zf.zf_compressed_free(h)
+    h = zf.zf_compressed_from_bytes(b)
+    try:
+        got, = gpu.decode([h], out_specs(x))
+        assert np.array_equal(got, x)
+    finally:
+        zf.zf_compressed_free(h)
+
+
 def test_lz77_edge_blocks(gpu):
     cases = [
         np.frombuffer(b"a" * 70000, np.uint8),                            # one long overlapping run

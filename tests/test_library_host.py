@@ -234,3 +234,50 @@ def test_strdict_plan_and_host_checks():
         with pytest.raises(zf.ZfError) as e:
             zf.zf_compressed_from_bytes(bytes(bb))
         assert e.value.status == zf.ZF_ECORRUPT
+
+
+def _ans_cases():
+    rng = np.random.default_rng(1)
+    return [rng.choice([65, 78, 82], 100001, p=[0.25, 0.5, 0.25]).astype(np.int32),
+            rng.integers(I64_LO, I64_HI, 256, dtype=np.int64)[rng.integers(0, 256, 9000)],
+            np.full(5000, 7, np.int64), np.array([-2**31, 2**31 - 1] * 3000, np.int32),
+            (rng.geometric(0.05, 300000) % 256).astype(np.int32),
+            np.array(list(range(255)) + [1000] * 4000, np.int32)]
+
+
+I64_LO, I64_HI = -(1 << 63), (1 << 63) - 1
+
+
+def test_ans_bytes_equal_the_oracle():
+    """Dictionary + ANS: the library's encoder writes the oracle's bytes
+    (canonical frequencies, streams of 512 rows)."""
+    for x in _ans_cases():
+        for cr in (1024, 65536, 1 << 20):
+            col = zf.Column(x)
+            h = zf.zf_compress_host(zf.zf_plan(None, col, scheme=zf.ZF_ANS, chunk_rows=cr), col)
+            try:
+                lb = zf.zf_compressed_bytes(h)
+                assert lb == oracle.encode(x, oracle.ANS, cr), (len(x), cr)
+            finally:
+                zf.zf_compressed_free(h)
+    col = zf.Column(np.arange(300, dtype=np.int32))                     # 300 values in one chunk
+    with pytest.raises(zf.ZfError) as e:
+        zf.zf_compress_host(zf.zf_plan(None, col, scheme=zf.ZF_ANS), col)
+    assert e.value.status == zf.ZF_EINVAL
+
+
+def test_ans_host_checks():
+    x = _ans_cases()[0]
+    b = oracle.encode(x, oracle.ANS, 65536)
+    off = oracle.chunk_span(b, 0)[0]
+    ch = parse_chunk(b[off:off + 64])
+    o1 = off + ch["offs"][1]
+    bad = []
+    bb = bytearray(b); struct.pack_into("<H", bb, o1, 0); bad.append(bb)                     # frequency 0
+    bb = bytearray(b); struct.pack_into("<H", bb, o1, struct.unpack_from("<H", b, o1)[0] + 1); bad.append(bb)  # sum
+    bb = bytearray(b); struct.pack_into("<I", bb, o1 + 8 + 4, 2); bad.append(bb)              # stream of 2 bytes
+    bb = bytearray(b); bb[off + 6] = 11; bad.append(bb)                                       # scale bits
+    for bb in bad:
+        with pytest.raises(zf.ZfError) as e:
+            zf.zf_compressed_from_bytes(bytes(bb))
+        assert e.value.status == zf.ZF_ECORRUPT
