@@ -358,7 +358,7 @@ zf_status zf_ctx_set_selector(zf_ctx* ctx, zf_mlp* net, const float* mean, const
  * array (each call rewrites what it uses); calls that overlap on the GPU,
  * from several host threads or streams at once, race -- serialize them.
  * Both pointers must be 16-byte aligned; `out_bytes` must hold all rows.
- * Returns ZF_EUNSUPPORTED for BYTES columns.  Besides the checks of the
+ * Returns ZF_EUNSUPPORTED for BYTES and ANS columns.  Besides the checks of the
  * other entry points' kernels, the device checks that each Float2Int chunk's
  * exception rows are strictly increasing and inside the chunk. */
 zf_status zf_decompress_device_noalloc(const void* d_column, uint64_t column_bytes, void* d_out,

@@ -267,6 +267,7 @@ extern "C" zf_status zf_decompress_device_noalloc(const void* d_column, uint64_t
     memcpy(&total, hdr + 32, 8);
     if (magic != zf::kColMagic || ver != 1) return ZF_ECORRUPT;
     if (dtype != ZF_I32 && dtype != ZF_I64 && dtype != ZF_F64) return ZF_EUNSUPPORTED;
+    if (scheme == ZF_ANS) return ZF_EUNSUPPORTED;   // decoded by its own kernel on the regular paths
     const bool scheme_ok = dtype == ZF_F64 ? (scheme == ZF_RAW || scheme == ZF_FLOAT2INT)
                                            : (scheme >= ZF_RAW && scheme <= ZF_RLE);
     if (!scheme_ok || chunk_rows == 0 || chunk_rows % 1024 || chunk_rows > (1u << 30) || n_rows > (1ull << 48))
