@@ -379,24 +379,22 @@ static uint64_t enc_lz(uint8_t* p, const uint8_t* src, uint32_t m) {
 /* ---- Float2Int + bit-packing (Section 2.1 "Float2Int", Table 2) ----
  * A double v becomes the integer d with v = d / 10^e for a decimal exponent
  * e of the chunk (0..18); the integers are stored FOR + bit-packed.  The
- * decoded value of d is q + r * 10^-e with q = d * 10^-e and r = d - q * 10^e
- * (both products in fused multiply-adds), which is the double nearest to
- * d / 10^e; a value that does not come back bit for bit from its rounded
+ * decoded value of d is the double nearest to d / 10^e: for |d| <= 2^53 and
+ * e <= 18 both d and 10^e are doubles exactly, so one IEEE division (which
+ * rounds its exact quotient to nearest) is that value, written as the
+ * definition says; a value that does not come back bit for bit from its rounded
  * integer (non-decimal values, NaN, infinities, -0.0, |v * 10^e| >= 2^53) is
  * an exception, stored as its row and its 64 bits.  The chunk's e has the
  * fewest exceptions (the smallest e on a tie). */
 #define F2I_EMAX 18
+#define F2I_DMAX 9007199254740992LL   /* 2^53 */
 static double f2i_pow10(int e) {
     double p = 1.0;
     for (int k = 0; k < e; k++) p *= 10.0;   /* exact up to 10^22 */
     return p;
 }
 static double f2i_value(int64_t d, int e) {
-    double p = f2i_pow10(e), inv = 1.0 / p;  /* the double nearest 10^-e */
-    double x = (double)d;
-    double q = x * inv;
-    double r = fma(-q, p, x);
-    return fma(r, inv, q);
+    return (double)d / f2i_pow10(e);         /* exact operands: the correctly rounded quotient */
 }
 static int f2i_fits(double v, int e, int64_t* d) {
     if (!isfinite(v)) return 0;
@@ -839,13 +837,19 @@ int orc_decode_chunk(const uint8_t* c, uint64_t len, void* out, uint64_t out_cap
         return ORC_OK;
     }
     case ORC_F2I: {
-        /* v_i = f2i_value(ref + u_i, e); the rows listed in s1 take the 64 bits in s2 */
+        /* v_i = f2i_value(ref + u_i, e); the rows listed in s1 take the 64 bits in s2.
+         * The encoder's integers satisfy |d| <= 2^53 (|v * 10^e| < 2^53, rounded):
+         * a stream with a larger one is malformed. */
         uint32_t e = c[48];
         if (!sec_ok(c, len, 0) || !sec_ok(c, len, 1) || !sec_ok(c, len, 2) || b > 64 || e > F2I_EMAX ||
             n_aux > m || l0 != orc_packed_bytes(m, b) || l1 != 4ull * n_aux || l2 != 8ull * n_aux)
             return ORC_ECORRUPT;
         double* o = (double*)out;
-        for (uint32_t i = 0; i < m; i++) o[i] = f2i_value((int64_t)(ref + orc_unpack_one(s0, i, b)), (int)e);
+        for (uint32_t i = 0; i < m; i++) {
+            int64_t d = (int64_t)(ref + orc_unpack_one(s0, i, b));
+            if (d > F2I_DMAX || d < -F2I_DMAX) return ORC_ECORRUPT;
+            o[i] = f2i_value(d, (int)e);
+        }
         for (uint32_t k = 0; k < n_aux; k++) {
             uint32_t pos = get_u32(s1 + 4ull * k);
             if (pos >= m || (k > 0 && pos <= get_u32(s1 + 4ull * (k - 1)))) return ORC_ECORRUPT;

@@ -480,7 +480,13 @@ def pin_f2i_exceptions(orc):
         _f2i_blob(0, 2, 5, bigint_pack([0, 1, 2, 3], 2), [4], [1.0], 4),
         _f2i_blob(19, 2, 5, bigint_pack([0, 1, 2, 3], 2), [], [], 4),
         _f2i_blob(0, 3, 5, bigint_pack([0, 1, 2, 3], 2), [], [], 4),
+        # an integer beyond 2^53 (the encoder stores |d| <= 2^53 only), either sign
+        _f2i_blob(2, 1, 2**53, bigint_pack([0, 1], 1), [], [], 2),
+        _f2i_blob(2, 1, -2**53 - 1, bigint_pack([1, 0], 1), [], [], 2),
     ]
+    # the bounds themselves are valid: +-2^53 / 10^2
+    ok = orc.decode_chunk(_f2i_blob(2, 55, -2**53, bigint_pack([0, 2**54], 55), [], [], 2), np.float64)
+    assert _same_bits(ok, [float(-2**53) / 100, float(2**53) / 100])
     for blob in bad:
         try:
             orc.decode_chunk(blob, np.float64)

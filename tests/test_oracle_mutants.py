@@ -44,7 +44,8 @@ MUTANTS = {
                              "ll |= (uint32_t)(byte & 0x7F) << sh;\n                sh += 8;"),
     "lz_varint_five_bytes": ("if (vp >= l0 || sh > 14) return ORC_ECORRUPT; /* at most 3 bytes */",
                              "if (vp >= l0 || sh > 28) return ORC_ECORRUPT;"),
-    "f2i_multiply_only": ("    return fma(r, inv, q);", "    (void)r;\n    return q;"),
+    "f2i_multiply_by_reciprocal": ("return (double)d / f2i_pow10(e);", "return (double)d * (1.0 / f2i_pow10(e));"),
+    "f2i_no_integer_range_check": ("if (d > F2I_DMAX || d < -F2I_DMAX) return ORC_ECORRUPT;", ""),
     "f2i_no_exception_patch": ("            memcpy(&o[pos], &bits, 8);", "            (void)bits;"),
     "f2i_truncates": ("int64_t k = (int64_t)nearbyint(t);", "int64_t k = (int64_t)t;"),
     "f2i_largest_exponent_on_tie": ("if (ex < best_ex) { best_ex = ex; best_e = e; }",
