@@ -547,18 +547,25 @@ def run_profile(args, zf, torch):
     elif args.profile == "float":
         # float64 prices with two decimals (log-normal cents / 100), Float2Int + packing, 1M-row chunks
         cols = [(W.decimal_prices(1, 7, 0, args.rows), zf.ZF_FLOAT2INT, CHUNK_ROWS)]
+    elif args.profile in ("strdict", "lz77"):
+        # the text column (Zipf words), as a string dictionary in 4 MiB chunks or as LZ77 blocks
+        t, o = W.text_column(1, int(args.text_mb * (1 << 20)))
+        cols = [((t, o), zf.ZF_STRDICT if args.profile == "strdict" else zf.ZF_LZ77,
+                 int(args.text_chunk_mb * (1 << 20)) if args.profile == "strdict" else 0)]
     else:
         keys, dates = make_workload(1, args.rows)
         cols = [(x, s, CHUNK_ROWS) for x, s, on in ((keys, zf.ZF_DELTA_BP, args.profile in ("keys", "both")),
                                                    (dates, zf.ZF_RLE, args.profile in ("dates", "both"))) if on]
     for x, s, cr in cols:
-        c = zf.Column(x)
+        parts = list(x) if isinstance(x, tuple) else [x]
+        c = zf.Column(*parts)
         h = zf.zf_compress_host(zf.zf_plan(ctx, c, scheme=s, chunk_rows=cr), c)
         hs.append(h)
-        b = torch.empty(x.nbytes, dtype=torch.uint8, device="cuda")
-        bufs.append(b)
-        outs.append(b.data_ptr())
-        caps.append(x.nbytes)
+        for p in parts:
+            b = torch.empty(p.nbytes, dtype=torch.uint8, device="cuda")
+            bufs.append(b)
+            outs.append(b.data_ptr())
+            caps.append(p.nbytes)
     rs = [zf.zf_upload(ctx, h) for h in hs]
     ms = []
     for i in range(args.warmup + args.steps):
@@ -596,7 +603,7 @@ def main():
     ap.add_argument("--slots", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--no-graph", action="store_true", help="enqueue transfers call by call (no CUDA graph)")
-    ap.add_argument("--profile", choices=["keys", "dates", "both", "for", "float", "ans"], default=None,
+    ap.add_argument("--profile", choices=["keys", "dates", "both", "for", "float", "ans", "strdict", "lz77"], default=None,
                     help="only decode the resident column(s) --steps times (for ncu captures)")
     ap.add_argument("--rows", type=int, default=N_ROWS, help="rows per column (profile / batched runs)")
     ap.add_argument("--workload", choices=["group_parallel", "batched", "selector", "text"], default="group_parallel",

@@ -60,9 +60,9 @@
  *              s0 = bit-packed (d - reference), b = bits(max - min), of the
  *              integers d with v = d / 10^e; s1 = u32 rows of the n_aux
  *              exceptions (ascending), s2 = their 64-bit patterns.  The value
- *              of d is q + r * 10^-e with q = d * 10^-e and r = d - q * 10^e
- *              (fused multiply-adds; 10^-e = the double nearest it): the
- *              double nearest d / 10^e.  Exception rows hold u = 0 in s0.
+ *              of d is the double nearest d / 10^e; every d of a valid chunk
+ *              has |d| <= 2^53 (decoders report larger ones as corrupt).
+ *              Exception rows hold u = 0 in s0.
  *     STRDICT  (BYTES only; chunk_rows = bytes per chunk, a multiple of 65536,
  *              at most 2^26) rows = bytes of the chunk, n_aux = dictionary
  *              entries (1..65536), reference = tokens T, b = bits(n_aux - 1).
@@ -104,7 +104,8 @@ typedef enum {
     ZF_ENOMEM = 2,        /* host, pinned or device allocation failed */
     ZF_ECUDA = 3,         /* a CUDA runtime call failed */
     ZF_ECORRUPT = 4,      /* a compressed stream is malformed (host check or device decoder) */
-    ZF_ETIMEOUT = 5,      /* a bounded device wait gave up */
+    ZF_ETIMEOUT = 5,      /* reserved for a bounded device wait that gives up; no decoder of this
+                             build waits (the batched work queue only counts), so none raises it */
     ZF_EUNSUPPORTED = 6,  /* feature not available in this build */
     ZF_EBUSY = 7          /* a transfer is in flight: call zf_sync first */
 } zf_status;
@@ -147,11 +148,13 @@ typedef struct {
     uint32_t stage_bytes;     /* pipeline stage: compressed bytes per H2D copy + decode step (default 64 MiB) */
     uint32_t flags;           /* ZF_KCFG_BATCHED: one work-queue launch per stage for all schemes
                                  (else one launch per (scheme, dtype) group);
-                                 ZF_KCFG_GRAPH: capture repeated transfers in a CUDA graph */
+                                 ZF_KCFG_GRAPH: capture repeated transfers in a CUDA graph;
+                                 ZF_KCFG_KEEP_ORDER: copy columns in the order given */
 } zf_kcfg;
 
 #define ZF_KCFG_BATCHED 1u
 #define ZF_KCFG_GRAPH 2u
+#define ZF_KCFG_KEEP_ORDER 4u   /* transfers keep the caller's column order (no Johnson's rule) */
 
 typedef struct {
     int32_t scheme;           /* zf_scheme, or -1 to let the selector choose */
@@ -203,7 +206,7 @@ zf_status zf_ctx_set_ring(zf_ctx* ctx, uint32_t slots, uint64_t slot_bytes);
 
 /* Choose scheme, chunk size and kernel geometry for a column.  With
  * opts->scheme >= 0 the scheme is forced; otherwise opts->selector picks the
- * heuristic (0), the learned MLP (1, needs zf_selector_load) or exhaustive
+ * heuristic (0), the learned MLP (1, needs zf_ctx_set_selector) or exhaustive
  * measurement on the GPU (2).  F64 columns take FLOAT2INT (or a forced RAW):
  * the selector's classes cover integer and byte columns only.  `opts` may
  * be NULL. */
@@ -238,9 +241,34 @@ zf_status zf_compressed_from_bytes(const uint8_t* data, uint64_t len, zf_compres
 zf_status zf_transfer_decompress(zf_ctx* ctx, const zf_compressed* const* cols, uint32_t ncols,
                                  void* const* d_out, const uint64_t* d_out_bytes);
 /* Wait for the last transfer (or resident decode) to finish.  Returns the
- * first host-side error, else ZF_ECORRUPT / ZF_ETIMEOUT raised by the
- * decoders.  `stats` may be NULL. */
+ * first host-side error, else ZF_ECORRUPT raised by the decoders.
+ * `stats` may be NULL. */
 zf_status zf_sync(zf_ctx* ctx, zf_stats* stats);
+
+/* Columns of a transfer are copied in the order of Johnson's rule for the
+ * two-stage flow (copy, then decode) of Section 3.3: columns whose copy is
+ * shorter than their decode first, by increasing copy time, then the rest by
+ * decreasing decode time (minimum makespan of the two-machine flow shop).  A
+ * column's copy time is its compressed bytes over the link rate last measured
+ * by zf_measure_copy on the context (200 GB/s before any), its decode time
+ * each chunk's plain bytes over the decode rate zf_tune measured for the
+ * chunk's (scheme, dtype, bit-width bucket) class (a nominal rate per scheme
+ * before any).  ZF_KCFG_KEEP_ORDER turns the reordering off. */
+
+/* The order Johnson's rule gives n jobs with times copy_ms[i] (first stage)
+ * and decode_ms[i] (second stage): order[] receives a permutation of 0..n-1
+ * (host arrays; ties keep the input order).  ZF_EINVAL for a negative or NaN
+ * time.  This is the ordering zf_transfer_decompress applies to columns. */
+zf_status zf_johnson_order(const float* copy_ms, const float* decode_ms, uint32_t n, uint32_t* order);
+
+/* The raw link at a call's own piece sizes: copy the columns' compressed
+ * bytes host-to-device exactly as zf_transfer_decompress would stage them
+ * (same stages, same 128-byte aligned pieces, same staging slots and copy
+ * stream) without decoding, `reps` times after one warm-up (0 = 5).  *ms =
+ * the fastest run (CUDA events on the copy stream).  The rate (compressed
+ * bytes / *ms) is kept by the context for Johnson's rule.  Returns ZF_EBUSY
+ * while a transfer is in flight. */
+zf_status zf_measure_copy(zf_ctx* ctx, const zf_compressed* const* cols, uint32_t ncols, uint32_t reps, float* ms);
 
 /* Copy a compressed column into device memory once, for decoding with the
  * compressed bytes already resident in HBM. */
@@ -273,7 +301,9 @@ typedef struct {
  * 32, 64) -- the result is kept for that class: later launches of the class
  * use it while the context's tile_rows / threads are 0 (automatic), so one
  * tuning run per column kind gives every kind its own geometry.  Otherwise
- * the result becomes the context's geometry.  Outputs as in
+ * the result becomes the context's geometry.  A resident search of one
+ * class also records the class's decode rate at the fastest point (plain
+ * bytes / time), which Johnson's rule then uses.  Outputs as in
  * zf_transfer_decompress; the columns are decoded into them many times. */
 zf_status zf_tune(zf_ctx* ctx, const zf_compressed* const* cols, uint32_t ncols, void* const* d_out,
                   const uint64_t* d_out_bytes, int32_t transfer, uint32_t reps, zf_tune_point* points,

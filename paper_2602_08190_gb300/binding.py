@@ -23,7 +23,7 @@ __all__ = [
     "zf_ctx_set_ring", "zf_plan", "zf_compress_host", "zf_compressed_info", "zf_compressed_free",
     "zf_compressed_bytes", "zf_compressed_from_bytes", "zf_transfer_decompress", "zf_sync", "zf_upload",
     "zf_resident_free", "zf_decompress_resident", "zf_decompress_device_noalloc", "zf_tune", "zf_tune_point",
-    "zf_ctx_tuned_geometry",
+    "zf_ctx_tuned_geometry", "zf_measure_copy", "zf_johnson_order", "ZF_KCFG_KEEP_ORDER",
     "zf_column_features", "zf_measure_classes", "zf_ctx_set_selector", "zf_mlp_create", "zf_mlp_destroy",
     "zf_mlp_get_params", "zf_mlp_set_params", "zf_mlp_forward", "zf_mlp_grad", "zf_mlp_adam", "zf_mlp_train",
     "zf_mlp_predict", "ZF_MLP_PARAMS", "ZF_MLP_CLASSES", "EXPORTED", "LIB_PATH",
@@ -33,7 +33,7 @@ ZF_MLP_PARAMS, ZF_MLP_CLASSES = 7052, 12
 (ZF_OK, ZF_EINVAL, ZF_ENOMEM, ZF_ECUDA, ZF_ECORRUPT, ZF_ETIMEOUT, ZF_EUNSUPPORTED, ZF_EBUSY) = range(8)
 ZF_I32, ZF_I64, ZF_BYTES, ZF_F64 = range(4)
 ZF_RAW, ZF_FOR_BP, ZF_DICT_BP, ZF_DELTA_BP, ZF_RLE, ZF_LZ77, ZF_FLOAT2INT, ZF_STRDICT, ZF_ANS = range(9)
-ZF_KCFG_BATCHED, ZF_KCFG_GRAPH = 1, 2
+ZF_KCFG_BATCHED, ZF_KCFG_GRAPH, ZF_KCFG_KEEP_ORDER = 1, 2, 4
 SCHEME_NAMES = ["raw", "for_bp", "dict_bp", "delta_bp", "rle", "lz77", "float2int", "strdict", "ans"]
 _STATUS = ["ok", "einval", "enomem", "ecuda", "ecorrupt", "etimeout", "eunsupported", "ebusy"]
 
@@ -106,6 +106,8 @@ _SIGS = {
     "zf_mlp_train": [_vp, _vp, _vp, _vp, _u32, _u32, _u32, ctypes.c_float, _u64, _vp],
     "zf_mlp_predict": [_vp, _vp, _vp, _u32, _vp],
     "zf_ctx_tuned_geometry": [_vp, ctypes.c_int32, ctypes.c_int32, _u32, ctypes.POINTER(zf_kcfg)],
+    "zf_measure_copy": [_vp, ctypes.POINTER(_vp), _u32, _u32, ctypes.POINTER(ctypes.c_float)],
+    "zf_johnson_order": [_vp, _vp, _u32, _vp],
     "zf_tune": [_vp, ctypes.POINTER(_vp), _u32, ctypes.POINTER(_vp), ctypes.POINTER(_u64), ctypes.c_int32, _u32,
                 ctypes.POINTER(zf_tune_point), _u32, ctypes.POINTER(_u32), ctypes.POINTER(zf_kcfg)],
 }
@@ -338,3 +340,22 @@ def zf_mlp_predict(net: int, x, mask) -> np.ndarray:
     out = np.zeros(len(x), np.int32)
     _check(_L.zf_mlp_predict(net, x.ctypes.data, m.ctypes.data, len(x), out.ctypes.data), "zf_mlp_predict")
     return out
+
+
+def zf_measure_copy(ctx: int, cols: list[int], reps: int = 5) -> float:
+    """Milliseconds of the fastest host-to-device copy of the columns in the
+    transfer's own pieces (no decode)."""
+    arr = (_vp * len(cols))(*cols)
+    ms = ctypes.c_float()
+    _check(_L.zf_measure_copy(ctx, arr, len(cols), reps, ctypes.byref(ms)), "zf_measure_copy", ctx)
+    return ms.value
+
+
+def zf_johnson_order(copy_ms, decode_ms) -> np.ndarray:
+    """Johnson's-rule order (indices) of jobs with the given stage times."""
+    c = np.ascontiguousarray(copy_ms, np.float32)
+    d = np.ascontiguousarray(decode_ms, np.float32)
+    assert c.shape == d.shape
+    out = np.zeros(max(1, len(c)), np.uint32)
+    _check(_L.zf_johnson_order(c.ctypes.data, d.ctypes.data, len(c), out.ctypes.data), "zf_johnson_order")
+    return out[:len(c)].astype(np.int64)

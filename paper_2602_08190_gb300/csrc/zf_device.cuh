@@ -11,9 +11,9 @@
 //   fp_job      Fully-Parallel: FOR / dictionary / Float2Int / raw.  Every
 //               lane extracts C = 16/sizeof(T) consecutive values of the
 //               staged bits with funnel shifts and writes them with one
-//               16-byte store (coalesced).  Float2Int makes each integer a
-//               double (an integer-built conversion, one multiply, two fused
-//               multiply-adds) and then patches the chunk's exceptions.
+//               16-byte store (coalesced).  Float2Int makes each integer
+//               the double nearest d / 10^e with integer multiplies
+//               (zf_f2i.h) and then patches the chunk's exceptions.
 //   delta_job   Group-Parallel: one 1024-row block per step.  Lane l owns
 //               values [32l, 32l+32): it sums its differences, one warp
 //               shuffle scan gives every lane its offset, the values are
@@ -37,9 +37,14 @@
 
 #include <type_traits>
 
+#include "zf_f2i.h"
 #include "zf_internal.h"
 
 namespace zfd {
+
+// Reciprocals of 5^e for the Float2Int value (zf_f2i.h); a warp job reads one
+// row, the same for all its lanes.
+static __constant__ zf::F2IRecip kF2IRecip[zf::kF2IMaxExp + 1] = {ZF_F2I_RECIP_ROWS};
 
 constexpr uint32_t kWarpRows = 1024;
 
@@ -182,29 +187,16 @@ __device__ __forceinline__ void extract4(const uint32_t* wsm, uint32_t bitpos, u
 __host__ __device__ inline uint32_t stage_bytes_for(uint32_t bmax) { return ((kWarpRows * bmax / 8 + 15) & ~15u) + 32; }
 
 // ---------------------------------------------------------------- Fully-Parallel
-// Extract and store the rows of a staged FOR/dictionary warp tile; returns
-// true if a dictionary code was out of range.
-// The double of an integer d, exactly when |d| < 2^53, built with integer
-// instructions (sign, the leading bit's position as exponent, the bits below
-// it as fraction): the FP64 pipe -- a small part of a GB300 SM -- is left to
-// the multiply and the two fused multiply-adds.  Larger magnitudes (only in
-// malformed streams) take the rounding conversion.
-__device__ __forceinline__ double exact_i2d(long long d) {
-    const unsigned long long a = d < 0 ? 0ull - (unsigned long long)d : (unsigned long long)d;
-    if (a >= (1ull << 53)) return __ll2double_rn(d);
-    if (a == 0) return 0.0;
-    const int lz = __clzll((long long)a);
-    const unsigned long long bits = ((unsigned long long)(d < 0) << 63) |
-                                    ((unsigned long long)(1023 + 63 - lz) << 52) | (((a << lz) << 1) >> 12);
-    return __longlong_as_double((long long)bits);
-}
-
+// Extract and store the rows of a staged FOR/dictionary/Float2Int warp tile;
+// returns true if a dictionary code was out of range or a Float2Int integer
+// was beyond 2^53.
 // FLOAT2INT (T = int64 bits of the doubles): the integer d = reference + u
-// becomes q + r * 10^-e, q = d * 10^-e, r = d - q * 10^e (p10 = 10^e,
-// inv10 = the double nearest 10^-e).
+// becomes the double nearest d / 10^e, built with integer multiplies
+// (zf::f2i_bits; `e` and its reciprocal row `rr` are the chunk's).
 template <class T, int SCHEME, bool NARROW>
 __device__ __forceinline__ bool fp_rows(const ZfDevChunk& c, const Hdr& h, T* dst, const uint32_t* wsm, uint32_t nr,
-                                        uint32_t b, uint32_t lane, double p10 = 1.0, double inv10 = 1.0) {
+                                        uint32_t b, uint32_t lane, uint32_t e = 0,
+                                        const zf::F2IRecip& rr = zf::F2IRecip{0, 0, 0, 0}) {
     constexpr int V = 16 / sizeof(T);
     const T* dict = reinterpret_cast<const T*>(c.blob + h.off[0]);
     const T ref = (T)h.ref;
@@ -227,9 +219,9 @@ __device__ __forceinline__ bool fp_rows(const ZfDevChunk& c, const Hdr& h, T* ds
             if constexpr (SCHEME == ZF_FOR_BP) {
                 v[k] = (T)(ref + (T)u[k]);
             } else if constexpr (SCHEME == ZF_FLOAT2INT) {
-                const double x = exact_i2d((long long)(h.ref + u[k]));
-                const double q = __dmul_rn(x, inv10);
-                v[k] = (T)__double_as_longlong(__fma_rn(__fma_rn(-q, p10, x), inv10, q));
+                const int64_t d = (int64_t)(h.ref + u[k]);
+                bad |= i0 + k < nr && (d > zf::kF2IDMax || d < -zf::kF2IDMax);
+                v[k] = (T)zf::f2i_bits(d, e, rr);
             } else {
                 const bool in = i0 + k < nr;
                 bad |= in && u[k] >= h.n_aux;
@@ -296,15 +288,15 @@ __device__ void fp_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t 
         }
     } else {
         const uint32_t b = h.b;
-        double p10 = 1.0, inv10 = 1.0;
+        uint32_t e = 0;
+        zf::F2IRecip rr{0, 0, 0, 0};
         if constexpr (SCHEME == ZF_FLOAT2INT) {
-            const uint32_t e = c.blob[48];
+            e = c.blob[48];
             if (e > (uint32_t)zf::kF2IMaxExp) {
                 if (lane == 0) report(err, ZF_ECORRUPT, c.chunk_id);
                 return;
             }
-            for (uint32_t k = 0; k < e; k++) p10 *= 10.0;   // exact: every power up to 10^22 is a double
-            inv10 = 1.0 / p10;                               // IEEE division: the double nearest 10^-e
+            rr = kF2IRecip[e];
         }
         if (b > 8 * sizeof(T) || (SCHEME == ZF_DICT_BP && b > 16)) {
             if (lane == 0) report(err, ZF_ECORRUPT, c.chunk_id);
@@ -331,7 +323,7 @@ __device__ void fp_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t 
             const uint32_t nr = min(kWarpRows, nrows - i * kWarpRows);
             const uint32_t* buf = wsm + (i & 1) * sb;
             if (V == 4 && b <= 8) bad |= fp_rows<T, SCHEME, true>(c, h, dst + i * kWarpRows, buf, nr, b, lane);
-            else bad |= fp_rows<T, SCHEME, false>(c, h, dst + i * kWarpRows, buf, nr, b, lane, p10, inv10);
+            else bad |= fp_rows<T, SCHEME, false>(c, h, dst + i * kWarpRows, buf, nr, b, lane, e, rr);
             __syncwarp();
         }
         if (bad) report(err, ZF_ECORRUPT, c.chunk_id);

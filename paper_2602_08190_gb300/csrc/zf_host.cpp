@@ -165,28 +165,25 @@ void enc_strdict(const uint8_t* x, uint32_t m, const std::vector<uint8_t>& row_s
 // ------------------------------------------------------------------ Float2Int + BP
 // A double v is stored as the integer d with v = d / 10^e, e the chunk's
 // decimal exponent (0..18), and the integers FOR + bit-packed (Section 2.1
-// "Float2Int"; Table 2 pairs it with bit-packing).  d decodes to
-// q + r * 10^-e, q = d * 10^-e, r = d - q * 10^e (fused multiply-adds), the
-// double nearest d / 10^e.  A value that does not come back bit for bit
+// "Float2Int"; Table 2 pairs it with bit-packing).  d decodes to the double
+// nearest d / 10^e.  A value that does not come back bit for bit
 // from its rounded integer is an exception (row + 64 bits).  The chunk takes
 // the exponent with the fewest exceptions, the smallest on a tie.
 struct Pow10 {
-    double p[kF2IMaxExp + 1], inv[kF2IMaxExp + 1];
+    double p[kF2IMaxExp + 1];
     Pow10() {
         double x = 1.0;   // exact: 10^18 < 2^63 and every power up to 10^22 is a double
         for (int e = 0; e <= kF2IMaxExp; e++) {
             p[e] = x;
-            inv[e] = 1.0 / x;
             x *= 10.0;
         }
     }
 };
 const Pow10 kPow10;
 
-inline double f2i_value(int64_t d, int e) {
-    const double x = (double)d, q = x * kPow10.inv[e];
-    return std::fma(std::fma(-q, kPow10.p[e], x), kPow10.inv[e], q);
-}
+// |d| <= 2^53 and 10^e (e <= 18) are doubles exactly, so one IEEE division
+// is the double nearest d / 10^e.
+inline double f2i_value(int64_t d, int e) { return (double)d / kPow10.p[e]; }
 
 inline bool f2i_fits(double v, int e, int64_t* d) {
     if (!std::isfinite(v)) return false;

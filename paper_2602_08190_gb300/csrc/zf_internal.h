@@ -113,4 +113,7 @@ zf_status encode_column(const zf_plan_t& plan, const zf_column& col, zf_compress
 zf_status parse_serialized(zf_compressed* c, std::string* why);
 void free_compressed(zf_compressed* c);
 uint32_t tiles_of(const ChunkInfo& ch, uint32_t tile_rows);
+// Johnson's rule for a two-machine flow shop (zf_plan.cpp): the order of n
+// jobs with times copy[i] on the first machine and dec[i] on the second.
+void johnson_sequence(const double* copy, const double* dec, uint32_t n, uint32_t* order);
 }  // namespace zf

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstring>
 #include <unordered_set>
+#include <vector>
 
 #include "zf_internal.h"
 
@@ -80,3 +81,30 @@ int heuristic_scheme(const zf_column& col, uint32_t chunk_rows) {
 }
 
 }  // namespace zf
+
+// ---------------------------------------------------------------- Johnson's rule
+// Section 3.3 orders the chunks of a call for the two-stage flow (host-to-
+// device copy, then decode) with Johnson's rule (S. M. Johnson, "Optimal two-
+// and three-stage production schedules with setup times included", 1954):
+// the jobs whose copy is shorter than their decode come first, by increasing
+// copy time, then the others, by decreasing decode time.  The order minimizes
+// the makespan of the two-machine flow shop.  Ties keep the input order.
+namespace zf {
+void johnson_sequence(const double* copy, const double* dec, uint32_t n, uint32_t* order) {
+    for (uint32_t i = 0; i < n; i++) order[i] = i;
+    std::stable_sort(order, order + n, [&](uint32_t x, uint32_t y) {
+        const bool fx = copy[x] < dec[x], fy = copy[y] < dec[y];
+        if (fx != fy) return fx;
+        return fx ? copy[x] < copy[y] : dec[x] > dec[y];
+    });
+}
+}  // namespace zf
+
+extern "C" zf_status zf_johnson_order(const float* copy_ms, const float* decode_ms, uint32_t n, uint32_t* order) {
+    if (n && (!copy_ms || !decode_ms || !order)) return ZF_EINVAL;
+    std::vector<double> c(copy_ms, copy_ms + n), d(decode_ms, decode_ms + n);
+    for (uint32_t i = 0; i < n; i++)
+        if (!(c[i] >= 0) || !(d[i] >= 0)) return ZF_EINVAL;   // negative or NaN
+    zf::johnson_sequence(c.data(), d.data(), n, order);
+    return ZF_OK;
+}

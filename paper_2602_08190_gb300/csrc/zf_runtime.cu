@@ -69,7 +69,9 @@ struct zf_ctx {
     // by launches of that class while the context's tile_rows / threads are 0.
     struct Tuned {
         uint32_t tile_rows = 0, threads = 0;
+        float gbs = 0;                 // measured decode rate at that geometry (plain GB/s), 0 = none
     } tuned[ZF_NSCHEMES][4][4];
+    float link_gbs = 0;               // measured host-to-device rate of the call's pieces (zf_measure_copy), 0 = none
     uint64_t tuned_gen = 0;
     uint64_t slots_gen = 0;        // bumped whenever the staging slots are reallocated
     // CUDA graph of the last transfer (ZF_KCFG_GRAPH) and what it was built for
@@ -304,49 +306,106 @@ zf_status launch_groups(zf_ctx* ctx, const std::vector<Group>& groups, const ZfD
     return ZF_OK;
 }
 
+// Nominal decode rates (GB/s of plain output per scheme on GB300), used for
+// Johnson's rule when no rate of the class has been measured.
+double nominal_decode_gbs(int scheme) {
+    switch (scheme) {
+    case ZF_LZ77: return 300;
+    case ZF_RLE: return 3500;
+    case ZF_DELTA_BP: case ZF_DICT_BP: return 5000;
+    case ZF_FLOAT2INT: return 1500;
+    case ZF_STRDICT: return 1000;
+    case ZF_ANS: return 500;
+    default: return 6000;
+    }
+}
+
 // Johnson's rule for the two-machine flow shop of Section 3.3 (copy, then
-// decode): jobs whose copy is shorter than their decode go first, by
-// increasing copy time, the others after them, by decreasing decode time.
-// A job is a column (its chunks are contiguous in one host buffer and stay
-// in order, so they still leave in few copies).  Times are estimated from
-// bytes: copies at 200 GB/s, decodes at nominal rates of plain output per
-// scheme on GB300.
-void johnson_order(std::vector<Work>& work) {
-    struct Job { size_t b, e; double copy, dec; };
-    std::vector<Job> jobs;
+// decode) over the columns of a call: a job is a column (its chunks are
+// contiguous in one host buffer and stay in order, so they still leave in
+// few copies).  A job's copy time is its compressed bytes over the host link
+// rate measured by zf_measure_copy (200 GB/s if none was measured), its
+// decode time the plain bytes of each chunk over the rate zf_tune measured
+// for the chunk's (scheme, dtype, bit-width bucket) class (a nominal rate if
+// none).  With ZF_KCFG_KEEP_ORDER the caller's order stays.
+void johnson_order(const zf_ctx* ctx, std::vector<Work>& work) {
+    std::vector<std::pair<size_t, size_t>> span;
+    std::vector<double> copy, dec;
+    const double link = ctx->link_gbs > 0 ? ctx->link_gbs : 200.0;
     for (size_t i = 0; i < work.size();) {
         size_t j = i;
-        double copy = 0, dec = 0;
+        double cp = 0, dc = 0;
         while (j < work.size() && work[j].host == work[i].host) {
             const zf::ChunkInfo& c = *work[j].ch;
             const double plain = (double)c.rows * zf::dtype_size(c.dtype);
-            double rate;   // GB/s of plain output
-            switch (c.scheme) {
-            case ZF_LZ77: rate = 300; break;
-            case ZF_RLE: rate = 3500; break;
-            case ZF_DELTA_BP: case ZF_DICT_BP: rate = 5000; break;
-            case ZF_FLOAT2INT: rate = 1500; break;
-            case ZF_STRDICT: rate = 1000; break;
-            case ZF_ANS: rate = 500; break;
-            default: rate = 6000; break;
-            }
-            copy += (double)c.bytes / 200.0;
-            dec += plain / rate;
+            double rate = 0;
+            if (c.scheme < ZF_NSCHEMES && c.dtype < 4) rate = ctx->tuned[c.scheme][c.dtype][width_bucket(c.bmax)].gbs;
+            if (!(rate > 0)) rate = nominal_decode_gbs(c.scheme);
+            cp += (double)c.bytes / link;
+            dc += plain / rate;
             j++;
         }
-        jobs.push_back({i, j, copy, dec});
+        span.push_back({i, j});
+        copy.push_back(cp);
+        dec.push_back(dc);
         i = j;
     }
-    if (jobs.size() < 2) return;
-    std::stable_sort(jobs.begin(), jobs.end(), [](const Job& x, const Job& y) {
-        const bool fx = x.copy < x.dec, fy = y.copy < y.dec;
-        if (fx != fy) return fx;
-        return fx ? x.copy < y.copy : x.dec > y.dec;
-    });
+    if (span.size() < 2) return;
+    std::vector<uint32_t> order(span.size());
+    zf::johnson_sequence(copy.data(), dec.data(), (uint32_t)span.size(), order.data());
     std::vector<Work> out;
     out.reserve(work.size());
-    for (const Job& jb : jobs) out.insert(out.end(), work.begin() + jb.b, work.begin() + jb.e);
+    for (uint32_t k : order) out.insert(out.end(), work.begin() + span[k].first, work.begin() + span[k].second);
     work.swap(out);
+}
+
+// Stages and copy pieces of a transfer.  Stages: consecutive chunks up to
+// stage_bytes of compressed bytes, cut from the end so that the last stages
+// are small (1/8, 1/4, 1/2 of stage_bytes): the decode left after the last
+// copy is short.  Copy plan: runs of chunks contiguous in one host buffer
+// become one copy, started at a 128-byte aligned host address (on GB300 an
+// H2D copy from an address that is not runs about 15% slower): up to 112
+// bytes before the run (never before its buffer) come along, and the run
+// lands that far into the slot, so chunk blobs stay 16-byte aligned there.
+struct Piece { const uint8_t* src; uint64_t bytes; uint64_t slot_off; };
+struct StagePlan {
+    std::vector<std::pair<size_t, size_t>> stages;
+    std::vector<std::vector<Piece>> pieces;
+    std::vector<uint64_t> dev_off;   // offset of each work item's blob in its stage's slot
+    uint64_t slot_need = 16;
+};
+void plan_stages(const std::vector<Work>& work, uint64_t stage_bytes, StagePlan& P) {
+    uint64_t max_stage = 0;
+    for (size_t j = work.size(), n = 0; j > 0; n++) {
+        const uint64_t cap = n < 3 ? std::min<uint64_t>(stage_bytes, std::max<uint64_t>(stage_bytes >> (3 - n), 1u << 20))
+                                   : stage_bytes;
+        size_t i = j;
+        uint64_t bytes = 0;
+        while (i > 0 && (i == j || bytes + work[i - 1].ch->bytes <= cap)) bytes += work[--i].ch->bytes;
+        P.stages.push_back({i, j});
+        max_stage = std::max(max_stage, bytes);
+        j = i;
+    }
+    std::reverse(P.stages.begin(), P.stages.end());
+    P.pieces.assign(P.stages.size(), {});
+    P.dev_off.assign(work.size(), 0);
+    P.slot_need = std::max<uint64_t>(max_stage, 16);
+    for (size_t s = 0; s < P.stages.size(); s++) {
+        auto [b, e] = P.stages[s];
+        uint64_t pos = 0;
+        for (size_t i = b; i < e;) {
+            size_t j = i + 1;
+            while (j < e && work[j].host == work[i].host && work[j].ch->off == work[j - 1].ch->off + work[j - 1].ch->bytes) j++;
+            const uint8_t* src = work[i].host + work[i].ch->off;
+            const uint64_t lead = std::min<uint64_t>(reinterpret_cast<uintptr_t>(src) & 127, work[i].ch->off);
+            const uint64_t bytes = work[j - 1].ch->off + work[j - 1].ch->bytes - work[i].ch->off;
+            P.pieces[s].push_back({src - lead, bytes + lead, pos});
+            for (size_t q = i; q < j; q++) P.dev_off[q] = pos + lead + (work[q].ch->off - work[i].ch->off);
+            pos += (bytes + lead + 15) & ~15ull;
+            i = j;
+        }
+        P.slot_need = std::max(P.slot_need, pos);
+    }
 }
 
 zf_status begin_call(zf_ctx* ctx) {
@@ -564,8 +623,10 @@ zf_status zf_transfer_decompress(zf_ctx* ctx, const zf_compressed* const* cols, 
             key.push_back((uint64_t)(uintptr_t)d_out[o]);
             key.push_back(d_out_bytes[o]);
         }
-        key.insert(key.end(), {k.tile_rows, k.threads, k.ctas_per_sm, k.stage_bytes, k.flags, ctx->tuned_gen, ctx->nslots,
-                               ctx->slot_req, ctx->slots_gen});
+        uint32_t link_bits;
+        memcpy(&link_bits, &ctx->link_gbs, 4);   // the column order depends on the measured rates
+        key.insert(key.end(), {k.tile_rows, k.threads, k.ctas_per_sm, k.stage_bytes, k.flags, ctx->tuned_gen, link_bits,
+                               ctx->nslots, ctx->slot_req, ctx->slots_gen});
         if (ctx->graph_exec && key == ctx->graph_key) {
             ZF_CU(ctx, cudaEventRecord(ctx->ev_t0, ctx->copy));
             ZF_CU(ctx, cudaGraphLaunch(ctx->graph_exec, ctx->copy));
@@ -579,53 +640,16 @@ zf_status zf_transfer_decompress(zf_ctx* ctx, const zf_compressed* const* cols, 
     uint64_t raw = 0, comp = 0;
     st = map_outputs<zf_compressed>(ctx, cols, ncols, d_out, d_out_bytes, work, &raw, &comp, host_of, nodev_of);
     if (st) return st;
-    johnson_order(work);
-    // Stages: consecutive chunks up to stage_bytes of compressed bytes, cut
-    // from the end so that the last stages are small (1/8, 1/4, 1/2 of
-    // stage_bytes): the decode left after the last copy is short.
-    std::vector<std::pair<size_t, size_t>> stages;
-    uint64_t max_stage = 0;
-    for (size_t j = work.size(), n = 0; j > 0; n++) {
-        const uint64_t cap = n < 3 ? std::min<uint64_t>(k.stage_bytes, std::max<uint64_t>(k.stage_bytes >> (3 - n), 1u << 20))
-                                   : k.stage_bytes;
-        size_t i = j;
-        uint64_t bytes = 0;
-        while (i > 0 && (i == j || bytes + work[i - 1].ch->bytes <= cap)) bytes += work[--i].ch->bytes;
-        stages.push_back({i, j});
-        max_stage = std::max(max_stage, bytes);
-        j = i;
-    }
-    std::reverse(stages.begin(), stages.end());
-    // Copy plan: runs of chunks contiguous in one host buffer become one copy,
-    // started at a 128-byte aligned host address (on GB300 an H2D copy from
-    // an address that is not runs about 15% slower): up to 112 bytes before
-    // the run (never before its buffer) come along, and the run lands that
-    // far into the slot, so chunk blobs stay 16-byte aligned there.
-    struct Piece { const uint8_t* src; uint64_t bytes; uint64_t slot_off; };
-    std::vector<std::vector<Piece>> pieces(stages.size());
-    std::vector<uint64_t> dev_off(work.size());
-    uint64_t slot_need = std::max<uint64_t>(max_stage, 16);
-    for (size_t s = 0; s < stages.size(); s++) {
-        auto [b, e] = stages[s];
-        uint64_t pos = 0;
-        for (size_t i = b; i < e;) {
-            size_t j = i + 1;
-            while (j < e && work[j].host == work[i].host && work[j].ch->off == work[j - 1].ch->off + work[j - 1].ch->bytes) j++;
-            const uint8_t* src = work[i].host + work[i].ch->off;
-            const uint64_t lead = std::min<uint64_t>(reinterpret_cast<uintptr_t>(src) & 127, work[i].ch->off);
-            const uint64_t bytes = work[j - 1].ch->off + work[j - 1].ch->bytes - work[i].ch->off;
-            pieces[s].push_back({src - lead, bytes + lead, pos});
-            for (size_t q = i; q < j; q++) dev_off[q] = pos + lead + (work[q].ch->off - work[i].ch->off);
-            pos += (bytes + lead + 15) & ~15ull;
-            i = j;
-        }
-        slot_need = std::max(slot_need, pos);
-    }
-    st = ensure_slots(ctx, std::max(slot_need, ctx->slot_req));
+    if (!(k.flags & ZF_KCFG_KEEP_ORDER)) johnson_order(ctx, work);
+    StagePlan P;
+    plan_stages(work, k.stage_bytes, P);
+    const auto& stages = P.stages;
+    const auto& pieces = P.pieces;
+    st = ensure_slots(ctx, std::max(P.slot_need, ctx->slot_req));
     if (st) return st;
     if (use_graph) key.back() = ctx->slots_gen;
     for (size_t s = 0; s < stages.size(); s++)
-        for (size_t q = stages[s].first; q < stages[s].second; q++) work[q].dev = ctx->slots[s % ctx->nslots] + dev_off[q];
+        for (size_t q = stages[s].first; q < stages[s].second; q++) work[q].dev = ctx->slots[s % ctx->nslots] + P.dev_off[q];
     std::vector<ZfDevChunk> desc;
     std::vector<std::vector<Group>> groups(stages.size());
     for (size_t s = 0; s < stages.size(); s++) build_groups(ctx, work, stages[s].first, stages[s].second, k, desc, groups[s]);
@@ -771,6 +795,45 @@ zf_status zf_sync(zf_ctx* ctx, zf_stats* stats) {
         if (bits & (1u << ZF_ETIMEOUT)) return ZF_ETIMEOUT;
         return ZF_EINVAL;
     }
+    return ZF_OK;
+}
+
+zf_status zf_measure_copy(zf_ctx* ctx, const zf_compressed* const* cols, uint32_t ncols, uint32_t reps, float* ms) {
+    zf::KeepDevice keep_device;
+    if (!ctx || !ms || !ncols || !cols) return ZF_EINVAL;
+    if (ctx->busy) return ZF_EBUSY;
+    ZF_CU(ctx, cudaSetDevice(ctx->device));
+    if (!reps) reps = 5;
+    std::vector<Work> work;
+    uint64_t comp = 0;
+    for (uint32_t c = 0; c < ncols; c++) {
+        if (!cols[c]) return ZF_EINVAL;
+        for (const zf::ChunkInfo& ch : cols[c]->chunks) {
+            work.push_back({cols[c]->host, nullptr, &ch, nullptr, 0, 0});
+            comp += ch.bytes;
+        }
+    }
+    const zf_kcfg k = effective_kcfg(ctx);
+    if (!(k.flags & ZF_KCFG_KEEP_ORDER)) johnson_order(ctx, work);
+    StagePlan P;
+    plan_stages(work, k.stage_bytes, P);
+    zf_status st = ensure_slots(ctx, std::max(P.slot_need, ctx->slot_req));
+    if (st) return st;
+    float best = 3.0e38f;
+    for (uint32_t r = 0; r < reps + 1; r++) {
+        ZF_CU(ctx, cudaEventRecord(ctx->ev_t0, ctx->copy));
+        for (size_t s = 0; s < P.stages.size(); s++)
+            for (const Piece& p : P.pieces[s])
+                ZF_CU(ctx, cudaMemcpyAsync(ctx->slots[s % ctx->nslots] + p.slot_off, p.src, p.bytes,
+                                           cudaMemcpyHostToDevice, ctx->copy));
+        ZF_CU(ctx, cudaEventRecord(ctx->ev_t1, ctx->copy));
+        ZF_CU(ctx, cudaEventSynchronize(ctx->ev_t1));
+        float t = 0;
+        ZF_CU(ctx, cudaEventElapsedTime(&t, ctx->ev_t0, ctx->ev_t1));
+        if (r) best = std::min(best, t);
+    }
+    *ms = best;
+    if (best > 0) ctx->link_gbs = (float)((double)comp / (best * 1e6));
     return ZF_OK;
 }
 
@@ -1116,6 +1179,11 @@ extern "C" zf_status zf_tune(zf_ctx* ctx, const zf_compressed* const* cols, uint
     if (one && cs >= 0) {
         ctx->tuned[cs][cd][cb].tile_rows = best_k.tile_rows;
         ctx->tuned[cs][cd][cb].threads = best_k.threads;
+        if (!transfer && best_ms > 0) {
+            uint64_t raw = 0;
+            for (uint32_t c = 0; c < ncols; c++) raw += cols[c]->raw_bytes;
+            ctx->tuned[cs][cd][cb].gbs = (float)((double)raw / (best_ms * 1e6));
+        }
         ctx->tuned_gen++;
         ctx->kcfg = saved;
         if (transfer) ctx->kcfg.stage_bytes = best_k.stage_bytes;
