@@ -68,6 +68,9 @@ class Oracle:
         L.orc_encode.restype = ctypes.c_int
         L.orc_encode.argtypes = [ctypes.c_int, ctypes.c_int, u8p, ctypes.c_uint64, ctypes.c_uint32, u8p,
                                  ctypes.c_uint64, u64p]
+        L.orc_encode_ans.restype = ctypes.c_int
+        L.orc_encode_ans.argtypes = [ctypes.c_int, u8p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, u8p,
+                                     ctypes.c_uint64, u64p]
         L.orc_encode_strdict.restype = ctypes.c_int
         L.orc_encode_strdict.argtypes = [u8p, ctypes.c_uint64, u8p, ctypes.c_uint64, ctypes.c_uint32, u8p,
                                          ctypes.c_uint64, u64p]
@@ -97,8 +100,9 @@ class Oracle:
         a = np.frombuffer(bytes(buf) + b"\0" * 16, np.uint8)
         return np.array([self.L.orc_unpack_one(_ptr(a), i, b) for i in range(n)], dtype=np.uint64)
 
-    def encode(self, x: np.ndarray, scheme: int, chunk_rows: int) -> bytes:
-        """Serialize column ``x`` (int32, int64 or uint8 bytes) with one scheme."""
+    def encode(self, x: np.ndarray, scheme: int, chunk_rows: int, ans_stream_rows: int | None = None) -> bytes:
+        """Serialize column ``x`` (int32, int64 or uint8 bytes) with one scheme
+        (ANS: ``ans_stream_rows`` rows per stream, 512 if None)."""
         x = np.ascontiguousarray(x)
         dt = _DT[x.dtype]
         cap = int(self.L.orc_encode_bound(scheme, dt, len(x), chunk_rows))
@@ -107,7 +111,12 @@ class Oracle:
         out = np.empty(cap, np.uint8)
         n = ctypes.c_uint64(0)
         xx = x if len(x) else np.zeros(1, x.dtype)
-        st = self.L.orc_encode(scheme, dt, _ptr(xx), len(x), chunk_rows, _ptr(out), cap, ctypes.byref(n))
+        if ans_stream_rows is not None:
+            assert scheme == ANS
+            st = self.L.orc_encode_ans(dt, _ptr(xx), len(x), chunk_rows, ans_stream_rows, _ptr(out), cap,
+                                       ctypes.byref(n))
+        else:
+            st = self.L.orc_encode(scheme, dt, _ptr(xx), len(x), chunk_rows, _ptr(out), cap, ctypes.byref(n))
         if st:
             raise OracleError(st, "encode")
         return bytes(out[: n.value])

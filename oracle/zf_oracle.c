@@ -58,7 +58,9 @@ enum { ORC_I32 = 0, ORC_I64 = 1, ORC_BYTES = 2, ORC_F64 = 3 };
 #define ANS_SCALE 12u         /* frequencies sum to M = 2^12 */
 #define ANS_M (1u << ANS_SCALE)
 #define ANS_L (1u << 23)      /* states stay in [L, 256 L) */
-#define ANS_SUB 512u          /* symbols per independent stream */
+#define ANS_LOG_MIN 5u        /* rows per independent stream: 2^5 .. 2^12, stored as log2 in header byte 48 */
+#define ANS_LOG_MAX 12u
+#define ANS_SUB_DEFAULT 512u  /* rows per stream when the caller names none */
 
 /* ------------------------------------------------------------------------- */
 /* little-endian byte helpers                                                */
@@ -169,7 +171,7 @@ static uint64_t chunk_bound(int scheme, int dtype, uint64_t rows) {
     case ORC_LZ77: return b + rows + rows / 2 + 64;
     case ORC_F2I: return b + rows * (8 + 4 + 8) + 32;
     case ORC_STRDICT: return b + 4 * (rows + 2 + rows / STR_TILE + 1) + rows + 2 * rows + 32;
-    case ORC_ANS: return b + 256 * sz + 512 + 8 * (rows / ANS_SUB + 2) + 2 * rows + 32;
+    case ORC_ANS: return b + 256 * sz + 512 + 8 * (rows / (1u << ANS_LOG_MIN) + 2) + 2 * rows + 32;
     }
     return 0;
 }
@@ -464,7 +466,9 @@ static uint64_t enc_f2i(uint8_t* p, const void* x, uint32_t m) {
  * holds the slot, to D(x) = f_s * floor(x / M) + slot - c_s.  States stay in
  * [L, 256 L): before C the encoder emits the low byte of x while
  * x >= (L / M) * 256 * f_s; after D the decoder reads a byte while x < L.
- * Every ANS_SUB rows form an independent stream: encoding runs from its last
+ * Every L rows form an independent stream (L = 2^k rows, k in 5..12, stored
+ * in header byte 48; Section 5.2.3 varies the ANS chunk size to trade ratio
+ * for throughput, and L is that size here): encoding runs from its last
  * row to its first starting at x = L; the stream is the final state (4 bytes,
  * little-endian) followed by the emitted bytes, last emitted first, so the
  * decoder reads it front to back and ends at x = L.
@@ -514,11 +518,14 @@ static uint32_t ans_encode(const uint32_t* sym, uint32_t n, const uint32_t* f, c
     return 4 + k;
 }
 
-static uint64_t enc_ans(uint8_t* p, int dtype, const void* x, uint32_t m, int* err) {
+static uint64_t enc_ans(uint8_t* p, int dtype, const void* x, uint32_t m, uint32_t L, int* err) {
+    uint32_t lg = 0;
+    while ((1u << lg) < L) lg++;
+    if ((1u << lg) != L || lg < ANS_LOG_MIN || lg > ANS_LOG_MAX) { *err = ORC_EINVAL; return 0; }
     int64_t* s = (int64_t*)malloc(sizeof(int64_t) * (m ? m : 1));
     uint32_t* sym = (uint32_t*)malloc(sizeof(uint32_t) * (m ? m : 1));
-    uint8_t* tmp = (uint8_t*)malloc(2ull * ANS_SUB + 16);
-    uint8_t* streams = (uint8_t*)malloc(2ull * m + 8ull * (m / ANS_SUB + 1) + 16);
+    uint8_t* tmp = (uint8_t*)malloc(2ull * L + 16);
+    uint8_t* streams = (uint8_t*)malloc(2ull * m + 8ull * (m / L + 1) + 16);
     if (!s || !sym || !tmp || !streams) { free(s); free(sym); free(tmp); free(streams); *err = ORC_ENOMEM; return 0; }
     for (uint32_t i = 0; i < m; i++) s[i] = load_val(x, dtype, i);
     qsort(s, m, sizeof(int64_t), cmp_i64);
@@ -536,9 +543,10 @@ static uint64_t enc_ans(uint8_t* p, int dtype, const void* x, uint32_t m, int* e
     }
     if (nd) ans_freqs(cnt, nd, m, f);
     for (uint32_t k = 0, acc = 0; k < nd; k++) { c[k] = acc; acc += f[k]; }
-    uint32_t K = (m + ANS_SUB - 1) / ANS_SUB;
+    uint32_t K = (m + L - 1) / L;
     chunk_w w = {p, 64};
     chunk_header(p, ORC_ANS, dtype, ANS_SCALE, 0, m, nd, K);
+    p[48] = (uint8_t)lg;
     uint64_t o0 = sec_begin(&w, 0, (uint64_t)nd * size_of(dtype));
     for (uint32_t k = 0; k < nd; k++) store_val(p + o0, dtype, k, (uint64_t)s[k]);
     uint64_t fbytes = (2ull * nd + 3) / 4 * 4;
@@ -546,7 +554,7 @@ static uint64_t enc_ans(uint8_t* p, int dtype, const void* x, uint32_t m, int* e
     for (uint32_t k = 0; k < nd; k++) put_u16(p + o1 + 2ull * k, f[k]);
     uint64_t pos = 0;
     for (uint32_t j = 0; j < K; j++) {
-        uint32_t r0 = j * ANS_SUB, n = m - r0 < ANS_SUB ? m - r0 : ANS_SUB;
+        uint32_t r0 = j * L, n = m - r0 < L ? m - r0 : L;
         put_u32(p + o1 + fbytes + 4ull * j, (uint32_t)pos);
         pos += ans_encode(sym + r0, n, f, c, streams + pos, tmp);
     }
@@ -657,10 +665,9 @@ static int scheme_ok(int scheme, int dtype) {
     return (scheme >= ORC_RAW && scheme <= ORC_RLE) || scheme == ORC_ANS;
 }
 
-/* Encode n values (BYTES: n bytes) in chunks of chunk_rows rows.
- * `out` must hold orc_encode_bound(...) bytes.  *out_len receives the size. */
-int orc_encode(int scheme, int dtype, const void* data, uint64_t n, uint32_t chunk_rows,
-               uint8_t* out, uint64_t cap, uint64_t* out_len) {
+/* Column assembly shared by orc_encode and orc_encode_ans. */
+static int encode_column(int scheme, int dtype, const void* data, uint64_t n, uint32_t chunk_rows,
+                         uint32_t ans_stream, uint8_t* out, uint64_t cap, uint64_t* out_len) {
     if (!scheme_ok(scheme, dtype) || chunk_rows == 0) return ORC_EINVAL;
     if (cap < orc_encode_bound(scheme, dtype, n, chunk_rows)) return ORC_EINVAL;
     uint64_t nch = (n + chunk_rows - 1) / chunk_rows;
@@ -683,7 +690,7 @@ int orc_encode(int scheme, int dtype, const void* data, uint64_t n, uint32_t chu
         case ORC_LZ77: len = enc_lz(p, x, m); break;
         case ORC_F2I: len = enc_f2i(p, x, m); break;
         case ORC_STRDICT: return ORC_EINVAL;   /* needs the row offsets: orc_encode_strdict */
-        case ORC_ANS: len = enc_ans(p, dtype, x, m, &err); break;
+        case ORC_ANS: len = enc_ans(p, dtype, x, m, ans_stream, &err); break;
         }
         if (err) return err;
         uint8_t* d = out + 64 + 32 * c;
@@ -705,6 +712,21 @@ int orc_encode(int scheme, int dtype, const void* data, uint64_t n, uint32_t chu
     put_u64(out + 32, pos);
     *out_len = pos;
     return ORC_OK;
+}
+
+/* Encode n values (BYTES: n bytes) in chunks of chunk_rows rows (ANS:
+ * streams of 512 rows).  `out` must hold orc_encode_bound(...) bytes.
+ * *out_len receives the size. */
+int orc_encode(int scheme, int dtype, const void* data, uint64_t n, uint32_t chunk_rows,
+               uint8_t* out, uint64_t cap, uint64_t* out_len) {
+    return encode_column(scheme, dtype, data, n, chunk_rows, ANS_SUB_DEFAULT, out, cap, out_len);
+}
+
+/* The same for dictionary + ANS with `stream_rows` rows per independent
+ * stream (a power of two, 32 .. 4096). */
+int orc_encode_ans(int dtype, const void* data, uint64_t n, uint32_t chunk_rows, uint32_t stream_rows,
+                   uint8_t* out, uint64_t cap, uint64_t* out_len) {
+    return encode_column(ORC_ANS, dtype, data, n, chunk_rows, stream_rows, out, cap, out_len);
 }
 
 
@@ -864,8 +886,11 @@ int orc_decode_chunk(const uint8_t* c, uint64_t len, void* out, uint64_t out_cap
          * bytes while x < L; the stream must end at x = L with every byte read */
         uint32_t nd = n_aux;
         uint64_t K = ref, fbytes = (2ull * nd + 3) / 4 * 4;
+        uint32_t lg = c[48];
+        if (lg < ANS_LOG_MIN || lg > ANS_LOG_MAX) return ORC_ECORRUPT;
+        uint32_t L = 1u << lg;
         if (!sec_ok(c, len, 0) || !sec_ok(c, len, 1) || !sec_ok(c, len, 2) || b != ANS_SCALE || nd == 0 ||
-            nd > 256 || l0 != (uint64_t)nd * sz || K != (m + ANS_SUB - 1) / ANS_SUB || l1 != fbytes + 4 * (K + 1))
+            nd > 256 || l0 != (uint64_t)nd * sz || K != (m + L - 1) / L || l1 != fbytes + 4 * (K + 1))
             return ORC_ECORRUPT;
         uint32_t f[256], cum[256], acc = 0;
         for (uint32_t k = 0; k < nd; k++) {
@@ -882,7 +907,7 @@ int orc_decode_chunk(const uint8_t* c, uint64_t len, void* out, uint64_t out_cap
             if (a1 < a0 || a1 - a0 < 4) return ORC_ECORRUPT;
             const uint8_t* q = s2 + a0;
             uint32_t ql = a1 - a0, qp = 4, x = get_u32(q);
-            uint32_t r0 = (uint32_t)j * ANS_SUB, n = m - r0 < ANS_SUB ? m - r0 : ANS_SUB;
+            uint32_t r0 = (uint32_t)j * L, n = m - r0 < L ? m - r0 : L;
             for (uint32_t i = 0; i < n; i++) {
                 uint32_t slot = x & (ANS_M - 1), sym = 0;
                 while (!(cum[sym] <= slot && slot < cum[sym] + f[sym])) sym++;

@@ -31,7 +31,7 @@ def parse_chunk(blob: bytes) -> dict:
     assert magic == 0x4B48435A
     secs = [bytes(blob[o:o + l]) if (o or l) else b"" for o, l in zip(offs, lens)]
     return dict(scheme=scheme, dtype=dtype, bw=bw, flags=flags, rows=rows, n_aux=n_aux, ref=ref,
-                offs=offs, lens=lens, secs=secs)
+                offs=offs, lens=lens, secs=secs, b48=blob[48])
 
 
 def chunks_of(orc, buf: bytes):
@@ -679,6 +679,7 @@ def pin_ans_round_trip_and_streams(orc):
         assert np.array_equal(orc.decode(buf), x)
         for ch, f, starts in parts:
             K = (ch["rows"] + 511) // 512
+            assert ch["b48"] == 9                          # 512 rows per stream unless named
             assert ch["ref"] == K and len(starts) == K + 1 and starts[0] == 0
             assert starts[-1] == ch["lens"][2] and all(b - a >= 4 for a, b in zip(starts, starts[1:]))
     try:
@@ -687,6 +688,49 @@ def pin_ans_round_trip_and_streams(orc):
         assert err.code == O.EINVAL
     else:
         raise AssertionError("257 distinct values accepted by the ANS encoder")
+
+
+def pin_ans_stream_length(orc):
+    # Section 5.2.3 trades ratio for throughput through the ANS chunk size;
+    # here each chunk names its rows per stream L = 2^k (header byte 48 = k,
+    # 5 <= k <= 12) and holds K = ceil(rows / L) streams
+    rng = np.random.default_rng(24)
+    x = np.repeat(np.arange(16, dtype=np.int32), 640)
+    rng.shuffle(x)                                          # 10,240 rows, 16 equal symbols: 4 bits a row
+    sizes = []
+    for k in range(5, 13):
+        L = 1 << k
+        buf = orc.encode(x, O.ANS, 1 << 20, ans_stream_rows=L)
+        (off, ln, r0, rows, ch), = chunks_of(orc, buf)
+        K = -(-len(x) // L)
+        nd = ch["n_aux"]
+        starts = list(struct.unpack_from(f"<{K + 1}I", ch["secs"][1], (2 * nd + 3) // 4 * 4))
+        assert ch["b48"] == k and ch["ref"] == K and len(ch["secs"][1]) == 32 + 4 * (K + 1)
+        # each stream: the 4-byte state and exactly half a byte per row
+        lens = [(min(L, len(x) - L * j) + 1) // 2 + 4 for j in range(K)]
+        assert [b - a for a, b in zip(starts, starts[1:])] == lens, k
+        assert np.array_equal(orc.decode(buf), x)
+        sizes.append(len(buf))
+    assert sizes == sorted(sizes, reverse=True)             # fewer streams, fewer bytes
+    for L in (16, 48, 8192):
+        try:
+            orc.encode(x, O.ANS, 1 << 20, ans_stream_rows=L)
+        except O.OracleError as err:
+            assert err.code == O.EINVAL
+        else:
+            raise AssertionError(f"{L} rows per ANS stream accepted")
+    # a chunk whose length byte disagrees with its streams is malformed
+    buf = orc.encode(x[:3000], O.ANS, 1 << 20, ans_stream_rows=256)
+    off, ln, _, _ = orc.chunk_span(buf, 0)
+    for k in (4, 13, 7, 9):
+        bb = bytearray(buf[off:off + ln])
+        bb[48] = k
+        try:
+            orc.decode_chunk(bytes(bb), np.int32)
+        except O.OracleError as err:
+            assert err.code == O.ECORRUPT
+        else:
+            raise AssertionError(f"ANS chunk with stream length byte {k} accepted")
 
 
 def pin_ans_rejects_corrupt(orc):

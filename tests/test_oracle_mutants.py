@@ -59,6 +59,7 @@ MUTANTS = {
                                      "            if (cnt[k] >= cnt[best]) best = k;"),
     "ans_decode_cum_off_by_one": ("x = f[sym] * (x >> ANS_SCALE) + slot - cum[sym];",
                                   "x = f[sym] * (x >> ANS_SCALE) + slot - cum[sym] + (sym > 0);"),
+    "ans_stream_length_ignored": ("uint32_t L = 1u << lg;", "uint32_t L = 512u;"),
     "ans_encode_drops_remainder": ("x = (x / f[s]) * ANS_M + (x % f[s]) + c[s];", "x = (x / f[s]) * ANS_M + c[s];"),
     "strdict_tokens_cross_rows": ("while (j < m && x[j - 1] != ' ' && !row_start[j] && j - i < STR_TOKEN_MAX) j++;",
                                   "while (j < m && x[j - 1] != ' ' && j - i < STR_TOKEN_MAX) j++;"),
