@@ -75,12 +75,13 @@
  *              64 bytes and at the chunk end, sorts the distinct tokens by
  *              their bytes (a prefix first), and above 65536 distinct tokens
  *              makes every byte a token
- *     ANS      (I32/I64) n_aux = distinct values (1..256), reference =
- *              streams K = ceil(rows/512), b = 12.  s0 = the sorted values;
+ *     ANS      (I32/I64) header byte 48 = k (5..12): every 2^k rows form an
+ *              independent stream; n_aux = distinct values (1..256),
+ *              reference = streams K = ceil(rows/2^k), b = 12.  s0 = the sorted values;
  *              s1 = u16 frequency of each value (>= 1, summing to M = 4096;
  *              padded to 4 bytes), then u32 start of each stream in s2 and
- *              the end of the last; s2 = the streams.  Stream k holds rows
- *              512k.. as range ANS: a u32 state x, then bytes; per row the
+ *              the end of the last; s2 = the streams.  Stream j holds rows
+ *              j*2^k.. as range ANS: a u32 state x, then bytes; per row the
  *              value is the one whose [cumulative, cumulative + frequency)
  *              holds x mod M, x becomes f * (x / M) + x mod M - cumulative,
  *              and while x < 2^23 the next byte enters as x = 256 x + byte.
@@ -161,6 +162,8 @@ typedef struct {
     uint32_t chunk_rows;      /* rows per chunk (BYTES: bytes per LZ77 block, fixed 65536); 0 = default */
     int32_t selector;         /* 0 = forced/heuristic, 1 = learned MLP, 2 = exhaustive measurement */
     int32_t offsets_scheme;   /* BYTES: scheme of the offsets column (FOR_BP or DELTA_BP); -1 = DELTA_BP */
+    uint32_t ans_stream_rows; /* ANS: rows per independent stream, a power of two 32..4096 (0 = 512);
+                                 Section 5.2.3's chunk-size trade of ratio for throughput */
 } zf_plan_opts;
 
 typedef struct {
@@ -170,6 +173,7 @@ typedef struct {
     zf_kcfg kcfg;
     float predicted_ms;       /* selector's or autotuner's estimate, 0 if none */
     int32_t label;            /* selector class (scheme, chunk size), -1 if none */
+    uint32_t ans_stream_rows; /* ANS: rows per stream (0 = 512) */
 } zf_plan_t;
 
 /* Per-call statistics filled by zf_sync. */
@@ -298,7 +302,8 @@ typedef struct {
  * order), sets *n_points to the number visited and stores the fastest
  * geometry in *best (nullable).  When all chunks of the columns are of one
  * class -- the same scheme, dtype and bit-width bucket (widest b <= 8, 16,
- * 32, 64) -- the result is kept for that class: later launches of the class
+ * 32, 64; for string columns the class of their bytes, the offsets being a
+ * small second part) -- the result is kept for that class: later launches of the class
  * use it while the context's tile_rows / threads are 0 (automatic), so one
  * tuning run per column kind gives every kind its own geometry.  Otherwise
  * the result becomes the context's geometry.  A resident search of one
@@ -314,6 +319,13 @@ zf_status zf_tune(zf_ctx* ctx, const zf_compressed* const* cols, uint32_t ncols,
  * built-in values (128 threads; warp jobs of 2048 rows for delta, 4096 for
  * the others).  bmax = the widest bit width of the launch's chunks. */
 zf_status zf_ctx_tuned_geometry(const zf_ctx* ctx, int32_t scheme, int32_t dtype, uint32_t bmax, zf_kcfg* out);
+
+/* The measured rates Johnson's rule reads for a class: the decode rate a
+ * resident zf_tune of that class recorded (plain GB/s) and the link rate the
+ * last zf_measure_copy recorded (compressed GB/s); 0 where none was measured
+ * (the ordering then uses nominal rates).  Either pointer may be NULL. */
+zf_status zf_ctx_rates(const zf_ctx* ctx, int32_t scheme, int32_t dtype, uint32_t bmax, float* decode_gbs,
+                       float* link_gbs);
 
 /* ---- learned selector ------------------------------------------------------ */
 
@@ -334,7 +346,8 @@ typedef struct zf_mlp zf_mlp;
 /* He-normal weights from `seed`, zero biases, Adam state cleared. */
 zf_status zf_mlp_create(int device, uint64_t seed, zf_mlp** out);
 zf_status zf_mlp_destroy(zf_mlp* net);
-/* Copy the parameters out (host, 7,052 floats) or in (also clears Adam state). */
+/* Copy the parameters out (host, 7,052 floats) or in (also clears Adam state
+ * and the fitted input scaling). */
 zf_status zf_mlp_get_params(const zf_mlp* net, float* host);
 zf_status zf_mlp_set_params(zf_mlp* net, const float* host);
 /* Device buffers: d_x batch x 32, d_logits batch x 12, d_y batch labels,
@@ -348,11 +361,15 @@ zf_status zf_mlp_grad(zf_mlp* net, const float* d_x, const int32_t* d_y, const u
 zf_status zf_mlp_adam(zf_mlp* net, const float* d_grad, float lr, void* stream);
 /* Train on host arrays (count samples): `epochs` passes in seeded random
  * order, mini-batches of `batch`, Adam at lr.  h_losses (nullable) gets the
- * mean loss of each epoch. */
+ * mean loss of each epoch.  The inputs are standardized as (x - mean) / std
+ * per feature, with the mean and standard deviation of these rows (std 1 for
+ * a constant feature); the network keeps them and zf_mlp_predict and the
+ * learned selector of zf_plan apply them (zf_mlp_get_scaling reads them). */
 zf_status zf_mlp_train(zf_mlp* net, const float* h_x, const int32_t* h_y, const uint8_t* h_mask, uint32_t count,
                        uint32_t epochs, uint32_t batch, float lr, uint64_t seed, float* h_losses);
 /* Class of each host row (argmax of the logits over its allowed classes, -1
- * if none allowed), computed on the GPU. */
+ * if none allowed), computed on the GPU; rows are standardized first with the
+ * scaling zf_mlp_train fitted (none after zf_mlp_set_params). */
 zf_status zf_mlp_predict(zf_mlp* net, const float* h_x, const uint8_t* h_mask, uint32_t count, int32_t* h_class);
 /* Time every selector class on a column: compress with the class's scheme
  * and chunk size, then transfer + decode (reps runs after one warm-up, median
@@ -360,9 +377,13 @@ zf_status zf_mlp_predict(zf_mlp* net, const float* h_x, const uint8_t* h_mask, u
  * This is the exhaustive search zf_plan's selector 2 uses and the label
  * source for training the selector. */
 zf_status zf_measure_classes(zf_ctx* ctx, const zf_column* col, uint32_t reps, float* ms);
-/* Use `net` (kept, not owned) for zf_plan's selector 1; features are
- * standardized as (f - mean) / std with the given 32-float host vectors. */
+/* Use `net` (kept, not owned) for zf_plan's selector 1.  With mean and std
+ * NULL the features go through the scaling the network fitted in
+ * zf_mlp_train; given (32-float host vectors, for a network loaded with
+ * zf_mlp_set_params) they are standardized as (f - mean) / std instead. */
 zf_status zf_ctx_set_selector(zf_ctx* ctx, zf_mlp* net, const float* mean, const float* std);
+/* The input scaling the network fitted (mean 0, std 1 if none): 32 floats each. */
+zf_status zf_mlp_get_scaling(const zf_mlp* net, float* mean, float* std);
 
 /* ---- decode without allocation ------------------------------------------ */
 

@@ -23,7 +23,7 @@ __all__ = [
     "zf_ctx_set_ring", "zf_plan", "zf_compress_host", "zf_compressed_info", "zf_compressed_free",
     "zf_compressed_bytes", "zf_compressed_from_bytes", "zf_transfer_decompress", "zf_sync", "zf_upload",
     "zf_resident_free", "zf_decompress_resident", "zf_decompress_device_noalloc", "zf_tune", "zf_tune_point",
-    "zf_ctx_tuned_geometry", "zf_measure_copy", "zf_johnson_order", "ZF_KCFG_KEEP_ORDER",
+    "zf_ctx_tuned_geometry", "zf_measure_copy", "zf_johnson_order", "ZF_KCFG_KEEP_ORDER", "zf_ctx_rates", "zf_mlp_get_scaling",
     "zf_column_features", "zf_measure_classes", "zf_ctx_set_selector", "zf_mlp_create", "zf_mlp_destroy",
     "zf_mlp_get_params", "zf_mlp_set_params", "zf_mlp_forward", "zf_mlp_grad", "zf_mlp_adam", "zf_mlp_train",
     "zf_mlp_predict", "ZF_MLP_PARAMS", "ZF_MLP_CLASSES", "EXPORTED", "LIB_PATH",
@@ -57,12 +57,13 @@ class zf_kcfg(ctypes.Structure):
 
 class zf_plan_opts(ctypes.Structure):
     _fields_ = [("scheme", ctypes.c_int32), ("chunk_rows", ctypes.c_uint32), ("selector", ctypes.c_int32),
-                ("offsets_scheme", ctypes.c_int32)]
+                ("offsets_scheme", ctypes.c_int32), ("ans_stream_rows", ctypes.c_uint32)]
 
 
 class zf_plan_t(ctypes.Structure):
     _fields_ = [("scheme", ctypes.c_int32), ("chunk_rows", ctypes.c_uint32), ("offsets_scheme", ctypes.c_int32),
-                ("kcfg", zf_kcfg), ("predicted_ms", ctypes.c_float), ("label", ctypes.c_int32)]
+                ("kcfg", zf_kcfg), ("predicted_ms", ctypes.c_float), ("label", ctypes.c_int32),
+                ("ans_stream_rows", ctypes.c_uint32)]
 
 
 class zf_tune_point(ctypes.Structure):
@@ -107,6 +108,9 @@ _SIGS = {
     "zf_mlp_predict": [_vp, _vp, _vp, _u32, _vp],
     "zf_ctx_tuned_geometry": [_vp, ctypes.c_int32, ctypes.c_int32, _u32, ctypes.POINTER(zf_kcfg)],
     "zf_measure_copy": [_vp, ctypes.POINTER(_vp), _u32, _u32, ctypes.POINTER(ctypes.c_float)],
+    "zf_ctx_rates": [_vp, ctypes.c_int32, ctypes.c_int32, _u32, ctypes.POINTER(ctypes.c_float),
+                     ctypes.POINTER(ctypes.c_float)],
+    "zf_mlp_get_scaling": [_vp, _vp, _vp],
     "zf_johnson_order": [_vp, _vp, _u32, _vp],
     "zf_tune": [_vp, ctypes.POINTER(_vp), _u32, ctypes.POINTER(_vp), ctypes.POINTER(_u64), ctypes.c_int32, _u32,
                 ctypes.POINTER(zf_tune_point), _u32, ctypes.POINTER(_u32), ctypes.POINTER(zf_kcfg)],
@@ -173,8 +177,8 @@ def zf_ctx_set_ring(ctx: int, slots: int, slot_bytes: int = 0) -> None:
 
 
 def zf_plan(ctx: int | None, col: Column, scheme: int = -1, chunk_rows: int = 0, selector: int = 0,
-            offsets_scheme: int = -1) -> zf_plan_t:
-    o = zf_plan_opts(scheme, chunk_rows, selector, offsets_scheme)
+            offsets_scheme: int = -1, ans_stream_rows: int = 0) -> zf_plan_t:
+    o = zf_plan_opts(scheme, chunk_rows, selector, offsets_scheme, ans_stream_rows)
     p = zf_plan_t()
     _check(_L.zf_plan(ctx, ctypes.byref(col.c), ctypes.byref(o), ctypes.byref(p)), "zf_plan", ctx)
     return p
@@ -359,3 +363,17 @@ def zf_johnson_order(copy_ms, decode_ms) -> np.ndarray:
     out = np.zeros(max(1, len(c)), np.uint32)
     _check(_L.zf_johnson_order(c.ctypes.data, d.ctypes.data, len(c), out.ctypes.data), "zf_johnson_order")
     return out[:len(c)].astype(np.int64)
+
+
+def zf_ctx_rates(ctx: int, scheme: int, dtype: int, bmax: int) -> tuple[float, float]:
+    """(decode GB/s measured for the class, link GB/s measured), 0 if none."""
+    d, l = ctypes.c_float(), ctypes.c_float()
+    _check(_L.zf_ctx_rates(ctx, scheme, dtype, bmax, ctypes.byref(d), ctypes.byref(l)), "zf_ctx_rates", ctx)
+    return d.value, l.value
+
+
+def zf_mlp_get_scaling(net: int) -> tuple[np.ndarray, np.ndarray]:
+    """(mean, std) of the input standardization the network fitted."""
+    m, sd = np.zeros(32, np.float32), np.zeros(32, np.float32)
+    _check(_L.zf_mlp_get_scaling(net, m.ctypes.data, sd.ctypes.data), "zf_mlp_get_scaling")
+    return m, sd

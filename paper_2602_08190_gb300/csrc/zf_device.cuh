@@ -89,10 +89,11 @@ __device__ __forceinline__ uint64_t extract(const uint32_t* sm, uint32_t bitpos,
 
 // One 256-bit store of four 64-bit words to a 32-byte aligned global address:
 // a lane writes a whole L2 sector at once.  st.global takes a global-space
-// address, so the generic pointer is converted first.  Decoders take a WS
-// template flag: only the single-scheme kernels use this store (in the
-// batched kernel's out-of-line dispatch it wrote only its first word on
-// sm_103a, so that kernel keeps 16-byte stores).
+// address, so the generic pointer is converted first.  The decoders that use
+// it are inlined into their kernels (the batched kernel included): inside a
+// function called out of line (through the ABI) the same store was seen to
+// write only its first word on sm_103a, so no out-of-line function uses it
+// (WS = false there, as in delta_block_wide and the allocation-free kernel).
 __device__ __forceinline__ void store32(void* dst, unsigned long long a, unsigned long long b, unsigned long long c,
                                         unsigned long long d) {
     const size_t g = __cvta_generic_to_global(dst);
@@ -196,10 +197,12 @@ __host__ __device__ inline uint32_t stage_bytes_for(uint32_t bmax) { return ((kW
 template <class T, int SCHEME, bool NARROW>
 __device__ __forceinline__ bool fp_rows(const ZfDevChunk& c, const Hdr& h, T* dst, const uint32_t* wsm, uint32_t nr,
                                         uint32_t b, uint32_t lane, uint32_t e = 0,
-                                        const zf::F2IRecip& rr = zf::F2IRecip{0, 0, 0, 0}) {
-    constexpr int V = 16 / sizeof(T);
+                                        const zf::F2IRecip& rr = zf::F2IRecip{0, 0, 0, 0}, bool chk = true) {
+    // Float2Int: four values (a 32-byte sector) per lane per step
+    constexpr int V = SCHEME == ZF_FLOAT2INT ? 4 : 16 / sizeof(T);
     const T* dict = reinterpret_cast<const T*>(c.blob + h.off[0]);
     const T ref = (T)h.ref;
+    const bool al32 = (reinterpret_cast<uintptr_t>(dst) & 31) == 0;
     bool bad = false;
 #pragma unroll 2
     for (uint32_t i0 = lane * V; i0 < nr; i0 += 32 * V) {
@@ -220,7 +223,7 @@ __device__ __forceinline__ bool fp_rows(const ZfDevChunk& c, const Hdr& h, T* ds
                 v[k] = (T)(ref + (T)u[k]);
             } else if constexpr (SCHEME == ZF_FLOAT2INT) {
                 const int64_t d = (int64_t)(h.ref + u[k]);
-                bad |= i0 + k < nr && (d > zf::kF2IDMax || d < -zf::kF2IDMax);
+                if (chk) bad |= i0 + k < nr && (d > zf::kF2IDMax || d < -zf::kF2IDMax);
                 v[k] = (T)zf::f2i_bits(d, e, rr);
             } else {
                 const bool in = i0 + k < nr;
@@ -228,9 +231,13 @@ __device__ __forceinline__ bool fp_rows(const ZfDevChunk& c, const Hdr& h, T* ds
                 v[k] = (in && u[k] < h.n_aux) ? __ldg(dict + u[k]) : (T)0;
             }
         }
-        if (i0 + V <= nr) store_vec<T, V>(dst + i0, v);
-        else
-            for (uint32_t i = i0; i < nr; i++) dst[i] = v[i - i0];
+        if (i0 + V <= nr) {
+            store_vec<T, V>(dst + i0, v, al32);
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; k++)
+                if (i0 + k < nr) dst[i0 + k] = v[k];
+        }
     }
     return bad;
 }
@@ -290,6 +297,7 @@ __device__ void fp_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t 
         const uint32_t b = h.b;
         uint32_t e = 0;
         zf::F2IRecip rr{0, 0, 0, 0};
+        bool chk = true;   // Float2Int: whether an integer of the chunk can pass 2^53
         if constexpr (SCHEME == ZF_FLOAT2INT) {
             e = c.blob[48];
             if (e > (uint32_t)zf::kF2IMaxExp) {
@@ -297,6 +305,9 @@ __device__ void fp_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t 
                 return;
             }
             rr = kF2IRecip[e];
+            const int64_t ref = (int64_t)h.ref;
+            if (b <= 54 && ref >= -zf::kF2IDMax && ref <= zf::kF2IDMax)
+                chk = ref + (int64_t)((1ull << b) - 1) > zf::kF2IDMax;
         }
         if (b > 8 * sizeof(T) || (SCHEME == ZF_DICT_BP && b > 16)) {
             if (lane == 0) report(err, ZF_ECORRUPT, c.chunk_id);
@@ -323,7 +334,7 @@ __device__ void fp_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t 
             const uint32_t nr = min(kWarpRows, nrows - i * kWarpRows);
             const uint32_t* buf = wsm + (i & 1) * sb;
             if (V == 4 && b <= 8) bad |= fp_rows<T, SCHEME, true>(c, h, dst + i * kWarpRows, buf, nr, b, lane);
-            else bad |= fp_rows<T, SCHEME, false>(c, h, dst + i * kWarpRows, buf, nr, b, lane, e, rr);
+            else bad |= fp_rows<T, SCHEME, false>(c, h, dst + i * kWarpRows, buf, nr, b, lane, e, rr, chk);
             __syncwarp();
         }
         if (bad) report(err, ZF_ECORRUPT, c.chunk_id);
@@ -476,7 +487,9 @@ __device__ __forceinline__ void delta_block_lanes(T* dst, const uint32_t* wsm, u
                 store_vec<T, PER>(dst + j0 + q * PER, v);
             }
         } else {
-            for (uint32_t e = 0; q * PER + e < nv; e++) dst[j0 + q * PER + e] = v[e];
+#pragma unroll
+            for (int e = 0; e < PER; e++)
+                if ((uint32_t)(q * PER + e) < nv) dst[j0 + q * PER + e] = v[e];
         }
     }
 }
@@ -593,16 +606,26 @@ __device__ __forceinline__ void rle_rows(const ZfDevChunk& c, const Hdr& h, T* d
         const uint32_t s4 = min(min(L[0] + L[1], kCap) + min(L[2] + L[3], kCap), kCap);
         const uint32_t incl = warp_incl_sum_sat(s4, kCap, lane);
         uint32_t st = end + incl - s4;  // start of entry k0
+        // the lane's start bits, ORed per bitmask word in registers first (its
+        // runs are consecutive, so their words are nondecreasing): one shared
+        // atomic per word the lane touches instead of one per run
+        uint32_t cw = 0xFFFFFFFFu, cbits = 0;
 #pragma unroll
         for (int e = 0; e < 4; e++) {
             const uint32_t k = k0 + e;
             if (k > sft && k < n && st >= skip && st - skip < nr) {
                 const uint32_t r = st - skip;
-                atomicOr(&bm[r >> 5], 1u << (r & 31));
+                if ((r >> 5) != cw) {
+                    if (cbits) atomicOr(&bm[cw], cbits);
+                    cw = r >> 5;
+                    cbits = 0;
+                }
+                cbits |= 1u << (r & 31);
             }
             if (k + 1 == n) my_last = st;
             st += L[e];
         }
+        if (cbits) atomicOr(&bm[cw], cbits);
         if (g == 0) {
             const uint32_t f0 = sft == 0 ? L[0] : sft == 1 ? L[1] : sft == 2 ? L[2] : L[3];
             first_len = __shfl_sync(0xFFFFFFFFu, f0, 0);   // run 0: entry sft of lane 0
@@ -652,7 +675,9 @@ __device__ __forceinline__ void rle_rows(const ZfDevChunk& c, const Hdr& h, T* d
                 store_vec<T, 4>(dst + j + 4, z, al32);
             }
         } else {
-            for (uint32_t k = 0; j + k < nr; k++) dst[j + k] = v[k];
+#pragma unroll
+            for (int k = 0; k < V; k++)
+                if (j + k < nr) dst[j + k] = v[k];
         }
     }
     __syncwarp();
@@ -764,7 +789,6 @@ __device__ void rle_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t
 
 // ---------------------------------------------------------------- string dictionary sizes
 // (the decoder is in zf_strdict.cuh)
-constexpr uint32_t kStrCodeBuf = (1024u * 16u / 8u) + 32u;   // one tile of codes at b <= 16, plus the reader's overrun
 constexpr uint32_t kStrWin = 32u * zf::kStrTokenMax + 32u;    // 32 tokens of at most 64 bytes, at the output's alignment
 
 // ---------------------------------------------------------------- single-tile entry points
@@ -792,7 +816,7 @@ __host__ __device__ inline uint32_t warp_smem(int scheme, uint32_t value_bytes, 
     case ZF_FOR_BP: case ZF_DICT_BP: case ZF_FLOAT2INT: return 2 * stage_bytes_for(bmax);
     case ZF_DELTA_BP: return 2 * stage_bytes_for(bmax) + 4096;   // + the store transpose buffer
     case ZF_RLE: return 128 + kRleStages * rle_buf_bytes(value_bytes);   // row bitmask + staging buffers
-    case ZF_STRDICT: return kStrCodeBuf + kStrWin;                      // one tile of codes + the output window
+    case ZF_STRDICT: return kStrWin;                                    // the output window (codes are read from L1/L2)
     }
     return 0;
 }

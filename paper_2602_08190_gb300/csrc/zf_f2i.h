@@ -68,36 +68,33 @@ ZF_F2I_HD int f2i_clz(uint64_t a) {
 }
 
 // The 64-bit pattern of the double nearest d / 10^e, for |d| <= 2^53 and
-// 0 <= e <= 18 (`r` = row e of the table; unused when e = 0).
+// 0 <= e <= 18 (`r` = row e of the table; unused when e = 0).  The result is
+// assembled as m + ((E + 1022) << 52) from the 53-bit significand m (leading
+// one included) and the unbiased exponent E: when rounding carries m to
+// 2^53, the sum moves into the next binade by itself.
 ZF_F2I_HD uint64_t f2i_bits(int64_t d, uint32_t e, const F2IRecip& r) {
     const uint64_t sign = d < 0 ? (1ull << 63) : 0ull;
     const uint64_t a = d < 0 ? 0ull - (uint64_t)d : (uint64_t)d;
     if (a == 0) return 0;   // +0.0 (a negative zero is always an exception)
     const int lz = f2i_clz(a);
     const uint64_t A = a << lz;
-    if (e == 0) {           // the integer itself: exact below 2^54
-        return sign | ((uint64_t)(1023 + 63 - lz) << 52) | ((A << 1) >> 12);
-    }
+    if (e == 0)             // the integer itself: exact, its top 53 bits are all of it
+        return sign | ((A >> 11) + ((uint64_t)(1022 + 63 - lz) << 52));
     uint64_t H = f2i_mulhi(A, r.r64);
     uint32_t ub = (uint32_t)(H >> 63);   // H is in [2^62, 2^64)
-    uint32_t k = 9 + ub;                 // H >> k keeps 54 bits: 53 of the result and the round bit
-    const uint32_t f = (uint32_t)(H >> (k - 9)) & 0x3FFu;   // round bit and the nine bits below it
-    if (f == 0x200u || f == 0x1FFu) {
-        // not decided: bits 128..191 of A * R128 (exact, carry included)
+    // round bit and the nine bits below it (all in the low word): undecided at 0x1FF and 0x200
+    if (((((uint32_t)H >> ub) & 0x3FFu) - 0x1FFu) < 2u) {
+        // bits 128..191 of A * R128 (exact, carry included)
         const uint64_t p1h = f2i_mulhi(A, r.r128_hi), p1l = A * r.r128_hi;
         const uint64_t p2h = f2i_mulhi(A, r.r128_lo);
         const uint64_t lo = p1l + p2h;
         H = p1h + (lo < p1l ? 1ull : 0ull);
         ub = (uint32_t)(H >> 63);
-        k = 9 + ub;
     }
-    uint64_t m = ((H >> k) + 1) >> 1;    // round to nearest on the round bit
-    int E = 62 + (int)ub - lz - (int)r.s - (int)e;
-    if (m >> 53) {                        // rounding carried into a new binade
-        m >>= 1;
-        E += 1;
-    }
-    return sign | ((uint64_t)(E + 1023) << 52) | (m & ((1ull << 52) - 1));
+    // round to nearest on the round bit (bit 9 + ub): ((H >> (9 + ub)) + 1) >> 1, from H >> 1 so the add cannot wrap
+    const uint64_t m = ((H >> 1) + (1ull << (8 + ub))) >> (9 + ub);
+    const int E = 62 + (int)ub - lz - (int)r.s - (int)e;
+    return sign | (m + ((uint64_t)(E + 1022) << 52));
 }
 
 }  // namespace zf

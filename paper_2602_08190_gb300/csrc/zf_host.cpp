@@ -262,12 +262,58 @@ void enc_for(const T* x, uint32_t m, Out& o) {
 }
 
 // ------------------------------------------------------------------ dictionary + BP
+// The sorted distinct values of x[0..m) when there are at most `limit`
+// (limit <= 65536), with a rank lookup: an open-addressing hash set of twice
+// the limit's size collects them in one pass (no sort of all m rows), then
+// only the distinct values are sorted.  Returns false above the limit.
+template <class T>
+struct DistinctRanks {
+    using U = typename std::make_unsigned<T>::type;
+    std::vector<T> sorted;           // the distinct values, ascending
+    std::vector<T> key;
+    std::vector<int32_t> slot;       // -1 = empty, else index into `sorted` (after build)
+    uint32_t mask = 0;
+    static uint32_t hash(T v) {
+        uint64_t z = (uint64_t)(U)v * 0x9E3779B97F4A7C15ull;
+        return (uint32_t)(z >> 32);
+    }
+    bool build(const T* x, uint32_t m, uint32_t limit) {
+        uint32_t cap = 16;
+        while (cap < 2 * limit) cap <<= 1;
+        mask = cap - 1;
+        key.assign(cap, T(0));
+        slot.assign(cap, -1);
+        uint32_t n = 0;
+        for (uint32_t i = 0; i < m; i++) {
+            const T v = x[i];
+            uint32_t h = hash(v) & mask;
+            while (slot[h] >= 0 && key[h] != v) h = (h + 1) & mask;
+            if (slot[h] < 0) {
+                if (n == limit) return false;
+                key[h] = v;
+                slot[h] = (int32_t)n++;
+            }
+        }
+        sorted.clear();
+        for (uint32_t h = 0; h < cap; h++)
+            if (slot[h] >= 0) sorted.push_back(key[h]);
+        std::sort(sorted.begin(), sorted.end());
+        for (uint32_t h = 0; h < cap; h++)
+            if (slot[h] >= 0) slot[h] = (int32_t)(std::lower_bound(sorted.begin(), sorted.end(), key[h]) - sorted.begin());
+        return true;
+    }
+    uint32_t rank(T v) const {
+        uint32_t h = hash(v) & mask;
+        while (key[h] != v || slot[h] < 0) h = (h + 1) & mask;
+        return (uint32_t)slot[h];
+    }
+};
+
 template <class T>
 zf_status enc_dict(const T* x, uint32_t m, Out& o) {
-    std::vector<T> d(x, x + m);
-    std::sort(d.begin(), d.end());
-    d.erase(std::unique(d.begin(), d.end()), d.end());
-    if (d.size() > kMaxDict) return ZF_EINVAL;
+    DistinctRanks<T> dr;
+    if (!dr.build(x, m, kMaxDict)) return ZF_EINVAL;
+    const std::vector<T>& d = dr.sorted;
     uint32_t nd = (uint32_t)d.size();
     uint32_t b = nd ? bits_of(nd - 1) : 0;
     uint64_t pb = packed_bytes(m, b);
@@ -278,9 +324,7 @@ zf_status enc_dict(const T* x, uint32_t m, Out& o) {
     uint64_t doff = w.section(0, dict_bytes);
     if (nd) memcpy(&o.b[doff], d.data(), dict_bytes);
     uint64_t coff = w.section(1, pb);
-    pack_stream(m, b, [&](uint64_t i) {
-        return (uint64_t)(std::lower_bound(d.begin(), d.end(), x[i]) - d.begin());
-    }, &o.b[coff]);
+    pack_stream(m, b, [&](uint64_t i) { return (uint64_t)dr.rank(x[i]); }, &o.b[coff]);
     return ZF_OK;
 }
 
@@ -298,15 +342,14 @@ zf_status enc_dict(const T* x, uint32_t m, Out& o) {
 // s1 = u16 frequencies (padded to 4 bytes) then u32 stream starts and end,
 // s2 = streams.
 template <class T>
-zf_status enc_ans(const T* x, uint32_t m, Out& o) {
-    std::vector<T> d(x, x + m);
-    std::sort(d.begin(), d.end());
-    d.erase(std::unique(d.begin(), d.end()), d.end());
-    if (d.size() > kAnsMaxSymbols) return ZF_EINVAL;
-    const uint32_t nd = (uint32_t)d.size(), K = (m + kAnsStream - 1) / kAnsStream;
+zf_status enc_ans(const T* x, uint32_t m, uint32_t L, Out& o) {
+    DistinctRanks<T> dr;
+    if (!dr.build(x, m, kAnsMaxSymbols)) return ZF_EINVAL;
+    const std::vector<T>& d = dr.sorted;
+    const uint32_t nd = (uint32_t)d.size(), K = (m + L - 1) / L;
     std::vector<uint32_t> sym(m), cnt(nd, 0), f(nd, 0), c(nd, 0);
     for (uint32_t i = 0; i < m; i++) {
-        sym[i] = (uint32_t)(std::lower_bound(d.begin(), d.end(), x[i]) - d.begin());
+        sym[i] = dr.rank(x[i]);
         cnt[sym[i]]++;
     }
     if (nd) {
@@ -331,7 +374,7 @@ zf_status enc_ans(const T* x, uint32_t m, Out& o) {
     std::vector<std::vector<uint8_t>> st(K);
     uint64_t sbytes = 0;
     for (uint32_t j = 0; j < K; j++) {
-        const uint32_t r0 = j * kAnsStream, n = std::min(kAnsStream, m - r0);
+        const uint32_t r0 = j * L, n = std::min(L, m - r0);
         std::vector<uint8_t> rev;
         rev.reserve(2 * n + 8);
         uint32_t s_x = kAnsL;
@@ -354,6 +397,7 @@ zf_status enc_ans(const T* x, uint32_t m, Out& o) {
     o.b.assign(align16(align16(align16(kChunkHeader + l0) + l1) + sbytes), 0);
     ChunkWriter w(o);
     w.header(ZF_ANS, dtype_code<T>(), kAnsScale, 0, m, nd, K);
+    o.b[48] = (uint8_t)(31 - __builtin_clz(L));   // log2 of the rows per stream
     const uint64_t s0 = w.section(0, l0), s1 = w.section(1, l1), s2 = w.section(2, sbytes);
     if (nd) memcpy(&o.b[s0], d.data(), l0);
     for (uint32_t k = 0; k < nd; k++) {
@@ -531,6 +575,7 @@ struct PartSpec {
     uint32_t chunk_rows;
     const int32_t* offsets = nullptr;   // string dictionary: row starts (nrows + 1 entries)
     uint64_t nrows = 0;
+    uint32_t ans_stream = kAnsStream;   // ANS: rows per independent stream
 };
 
 void run_parallel(uint32_t n, const std::function<void(uint32_t)>& f) {
@@ -594,7 +639,7 @@ zf_status encode_part(const PartSpec& p, std::vector<Out>& blobs, std::string* w
             case ZF_DICT_BP: st = enc_dict(v, m, o); break;
             case ZF_DELTA_BP: enc_delta(v, m, o); break;
             case ZF_RLE: enc_rle(v, m, o); break;
-            case ZF_ANS: st = enc_ans(v, m, o); break;
+            case ZF_ANS: st = enc_ans(v, m, p.ans_stream, o); break;
             }
         } else {
             auto* v = reinterpret_cast<const int64_t*>(x);
@@ -604,7 +649,7 @@ zf_status encode_part(const PartSpec& p, std::vector<Out>& blobs, std::string* w
             case ZF_DICT_BP: st = enc_dict(v, m, o); break;
             case ZF_DELTA_BP: enc_delta(v, m, o); break;
             case ZF_RLE: enc_rle(v, m, o); break;
-            case ZF_ANS: st = enc_ans(v, m, o); break;
+            case ZF_ANS: st = enc_ans(v, m, p.ans_stream, o); break;
             }
         }
         if (st != ZF_OK) err = st;
@@ -734,6 +779,14 @@ zf_status encode_column(const zf_plan_t& plan, const zf_column& col, zf_compress
             return ZF_EINVAL;
         }
         specs.push_back({plan.scheme, dt, (const uint8_t*)col.data, col.n, cr});
+        if (plan.scheme == ZF_ANS) {
+            const uint32_t L = plan.ans_stream_rows ? plan.ans_stream_rows : kAnsStream;
+            if ((L & (L - 1)) || L < (1u << kAnsLogMin) || L > (1u << kAnsLogMax)) {
+                if (why) *why = "ANS streams are a power of two of 32..4096 rows";
+                return ZF_EINVAL;
+            }
+            specs.back().ans_stream = L;
+        }
     }
     std::vector<std::vector<Out>> blobs(specs.size());
     uint64_t total = 0;
@@ -768,7 +821,10 @@ zf_status encode_column(const zf_plan_t& plan, const zf_column& col, zf_compress
 uint32_t tiles_of(const ChunkInfo& ch, uint32_t tile_rows) {
     if (ch.scheme == ZF_LZ77) return 1;
     if (ch.scheme == ZF_STRDICT) return (ch.units + tile_rows - 1) / tile_rows;   // jobs of tile_rows tokens
-    if (ch.scheme == ZF_ANS) return (ch.units + kAnsStreamsPerJob - 1) / kAnsStreamsPerJob;   // 32 streams a job
+    if (ch.scheme == ZF_ANS) {   // 32 streams a job, a chunk's jobs padded to whole CTAs
+        const uint32_t jobs = (ch.units + kAnsStreamsPerJob - 1) / kAnsStreamsPerJob;
+        return (jobs + kAnsJobsPerCta - 1) / kAnsJobsPerCta * kAnsJobsPerCta;
+    }
     return (ch.rows + tile_rows - 1) / tile_rows;
 }
 
@@ -857,8 +913,11 @@ bool check_chunk(const uint8_t* c, uint64_t len, int scheme, int dtype, uint32_t
     }
     case ZF_ANS: {
         const uint64_t K = rd<uint64_t>(c + 16), fb = (2ull * n_aux + 3) / 4 * 4;
+        const uint32_t lg = c[48];
+        if (lg < kAnsLogMin || lg > kAnsLogMax) return fail(why, "ANS stream length");
+        const uint32_t L = 1u << lg;
         if (b != kAnsScale || n_aux == 0 || n_aux > kAnsMaxSymbols || ln[0] != (uint64_t)n_aux * sz ||
-            K != (rows + kAnsStream - 1) / kAnsStream || ln[1] != fb + 4 * (K + 1))
+            K != (rows + L - 1) / L || ln[1] != fb + 4 * (K + 1))
             return fail(why, "ANS sections");
         // frequencies of at least 1 that fill M; streams of at least the 4 state bytes that fill s2
         uint32_t total = 0;

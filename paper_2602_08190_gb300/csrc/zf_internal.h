@@ -50,8 +50,10 @@ constexpr uint32_t kAnsMaxSymbols = 256;       // ANS: distinct values of a chun
 constexpr uint32_t kAnsScale = 12;             // ANS: frequencies sum to M = 2^12
 constexpr uint32_t kAnsM = 1u << kAnsScale;
 constexpr uint32_t kAnsL = 1u << 23;           // ANS: states stay in [L, 256 L)
-constexpr uint32_t kAnsStream = 512;           // ANS: rows per independent stream
+constexpr uint32_t kAnsStream = 512;           // ANS: rows per independent stream unless the plan names others
+constexpr uint32_t kAnsLogMin = 5, kAnsLogMax = 12;   // ANS: rows per stream = 2^k, k in 5..12 (header byte 48)
 constexpr uint32_t kAnsStreamsPerJob = 32;     // ANS: one stream per lane of a warp job
+constexpr uint32_t kAnsJobsPerCta = 4;         // ANS: a CTA's warps take jobs of one chunk (padded to a multiple)
 
 inline uint64_t align16(uint64_t x) { return (x + 15) & ~uint64_t(15); }
 inline uint32_t bits_of(uint64_t x) { return x ? 64u - (uint32_t)__builtin_clzll(x) : 0u; }

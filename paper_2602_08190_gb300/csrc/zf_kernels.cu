@@ -68,11 +68,11 @@ __device__ __forceinline__ void decode_one(const ZfDevChunk& c, const zfd::Hdr& 
     }
 }
 
-__device__ __noinline__ void decode_mixed(const ZfDevChunk& c, const zfd::Hdr& h, uint32_t r0, uint32_t nrows,
-                                          uint32_t* wsm, uint32_t* err) {
+__device__ __forceinline__ void decode_mixed(const ZfDevChunk& c, const zfd::Hdr& h, uint32_t r0, uint32_t nrows,
+                                             uint32_t* wsm, uint32_t* err) {
     switch (c.scheme * 4 + c.dtype) {
 #define ZF_CASE(S, D) \
-    case S * 4 + D: decode_one<S, D, false>(c, h, r0, nrows, wsm, err); break;
+    case S * 4 + D: decode_one<S, D, true>(c, h, r0, nrows, wsm, err); break;
         ZF_CASE(ZF_RAW, ZF_I32) ZF_CASE(ZF_RAW, ZF_I64) ZF_CASE(ZF_RAW, ZF_BYTES)
         ZF_CASE(ZF_FOR_BP, ZF_I32) ZF_CASE(ZF_FOR_BP, ZF_I64)
         ZF_CASE(ZF_DICT_BP, ZF_I32) ZF_CASE(ZF_DICT_BP, ZF_I64)

@@ -161,6 +161,10 @@ struct zf_mlp {
     float* ls = nullptr;      // per-sample losses
     uint32_t cap = 0;         // samples gs/ls hold
     uint32_t step = 0;
+    // input standardization (x - mean) / std, fitted by zf_mlp_train on its
+    // rows and applied by zf_mlp_train and zf_mlp_predict
+    bool scaled = false;
+    float mean[32] = {0}, sd[32] = {0};
 };
 
 namespace {
@@ -242,6 +246,7 @@ zf_status zf_mlp_set_params(zf_mlp* n, const float* host) {
         cudaMemset(n->m, 0, NP * sizeof(float)) != cudaSuccess || cudaMemset(n->v, 0, NP * sizeof(float)) != cudaSuccess)
         return ZF_ECUDA;
     n->step = 0;
+    n->scaled = false;   // parameters from elsewhere: inputs are taken as given
     return ZF_OK;
 }
 
@@ -293,6 +298,20 @@ zf_status zf_mlp_train(zf_mlp* n, const float* h_x, const int32_t* h_y, const ui
         cudaGetLastError();
         return done(ZF_ENOMEM);
     }
+    // per-feature mean and standard deviation of the training rows (a
+    // constant feature keeps std 1), kept by the network for inference
+    for (uint32_t f = 0; f < IN; f++) {
+        double s1 = 0, s2 = 0;
+        for (uint32_t r = 0; r < count; r++) {
+            const double v = h_x[(size_t)r * IN + f];
+            s1 += v;
+            s2 += v * v;
+        }
+        const double mu = s1 / count, var = std::max(0.0, s2 / count - mu * mu);
+        n->mean[f] = (float)mu;
+        n->sd[f] = var > 0 ? (float)std::sqrt(var) : 1.0f;
+    }
+    n->scaled = true;
     std::vector<uint32_t> order(count);
     std::vector<float> bx((size_t)batch * IN);
     std::vector<int32_t> by(batch);
@@ -309,7 +328,8 @@ zf_status zf_mlp_train(zf_mlp* n, const float* h_x, const int32_t* h_y, const ui
             const uint32_t B = std::min(batch, count - s0);
             for (uint32_t k = 0; k < B; k++) {
                 const uint32_t r = order[s0 + k];
-                memcpy(&bx[(size_t)k * IN], h_x + (size_t)r * IN, IN * sizeof(float));
+                for (uint32_t f = 0; f < IN; f++)
+                    bx[(size_t)k * IN + f] = (h_x[(size_t)r * IN + f] - n->mean[f]) / n->sd[f];
                 by[k] = h_y[r];
                 memcpy(&bm[(size_t)k * OUT], h_mask + (size_t)r * OUT, OUT);
             }
@@ -353,7 +373,14 @@ zf_status zf_mlp_predict(zf_mlp* n, const float* h_x, const uint8_t* h_mask, uin
         cudaGetLastError();
         return done(ZF_ENOMEM);
     }
-    if (cudaMemcpy(dx, h_x, (size_t)count * IN * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+    std::vector<float> xs;
+    const float* src = h_x;
+    if (n->scaled) {   // the standardization fitted by zf_mlp_train
+        xs.resize((size_t)count * IN);
+        for (size_t i = 0; i < xs.size(); i++) xs[i] = (h_x[i] - n->mean[i % IN]) / n->sd[i % IN];
+        src = xs.data();
+    }
+    if (cudaMemcpy(dx, src, (size_t)count * IN * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(dm, h_mask, (size_t)count * OUT, cudaMemcpyHostToDevice) != cudaSuccess)
         return done(ZF_ECUDA);
     mlp_predict<<<count, HID>>>(n->p, dx, dm, dc);
@@ -361,6 +388,15 @@ zf_status zf_mlp_predict(zf_mlp* n, const float* h_x, const uint8_t* h_mask, uin
     if (cudaMemcpy(h_class, dc, (size_t)count * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
         return done(ZF_ECUDA);
     return done(ZF_OK);
+}
+
+zf_status zf_mlp_get_scaling(const zf_mlp* n, float* mean, float* std_) {
+    if (!n || !mean || !std_) return ZF_EINVAL;
+    for (uint32_t f = 0; f < IN; f++) {
+        mean[f] = n->scaled ? n->mean[f] : 0.0f;
+        std_[f] = n->scaled ? n->sd[f] : 1.0f;
+    }
+    return ZF_OK;
 }
 
 }  // extern "C"

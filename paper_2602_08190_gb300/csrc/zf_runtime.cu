@@ -85,6 +85,7 @@ struct zf_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     zf_mlp* selector = nullptr;       // learned selector (not owned) and its feature scaling
     float sel_mean[32] = {0}, sel_std[32] = {0};
+    bool sel_scaled = false;          // standardize with sel_mean / sel_std (else the network's own scaling)
     bool busy = false;
     zf_status host_err = ZF_OK;
     std::string last_error;
@@ -1023,9 +1024,10 @@ extern "C" zf_status zf_measure_classes(zf_ctx* ctx, const zf_column* col, uint3
 }
 
 extern "C" zf_status zf_ctx_set_selector(zf_ctx* ctx, zf_mlp* net, const float* mean, const float* std_) {
-    if (!ctx || (net && (!mean || !std_))) return ZF_EINVAL;
+    if (!ctx || (!mean) != (!std_)) return ZF_EINVAL;
     ctx->selector = net;
-    if (net) {
+    ctx->sel_scaled = net && mean;
+    if (ctx->sel_scaled) {
         memcpy(ctx->sel_mean, mean, sizeof(ctx->sel_mean));
         memcpy(ctx->sel_std, std_, sizeof(ctx->sel_std));
     }
@@ -1035,12 +1037,13 @@ extern "C" zf_status zf_ctx_set_selector(zf_ctx* ctx, zf_mlp* net, const float* 
 extern "C" zf_status zf_plan(zf_ctx* ctx, const zf_column* col, const zf_plan_opts* opts, zf_plan_t* out) {
     if (!col || !out) return ZF_EINVAL;
     if (col->dtype != ZF_I32 && col->dtype != ZF_I64 && col->dtype != ZF_BYTES && col->dtype != ZF_F64) return ZF_EINVAL;
-    zf_plan_opts o{-1, 0, 0, -1};
+    zf_plan_opts o{-1, 0, 0, -1, 0};
     if (opts) o = *opts;
     if (col->dtype == ZF_F64 && o.scheme < 0) o.selector = 0;   // the selector's classes cover integer and byte columns
     zf_plan_t p{};
     p.label = -1;
     p.offsets_scheme = o.offsets_scheme < 0 ? ZF_DELTA_BP : o.offsets_scheme;
+    p.ans_stream_rows = o.ans_stream_rows;
     p.chunk_rows = col->dtype == ZF_BYTES ? zf::kLzBlock : (o.chunk_rows ? o.chunk_rows : (1u << 20));
     if (col->dtype != ZF_BYTES && (p.chunk_rows % 1024 || p.chunk_rows > (1u << 30))) {
         if (ctx) ctx->last_error = "chunk_rows must be a multiple of 1024 and at most 2^30";
@@ -1068,7 +1071,8 @@ extern "C" zf_status zf_plan(zf_ctx* ctx, const zf_column* col, const zf_plan_op
         float f[32];
         zf_status st = zf_column_features(col, f);
         if (st) return st;
-        for (int i = 0; i < 32; i++) f[i] = (f[i] - ctx->sel_mean[i]) / (ctx->sel_std[i] > 0 ? ctx->sel_std[i] : 1.0f);
+        if (ctx->sel_scaled)
+            for (int i = 0; i < 32; i++) f[i] = (f[i] - ctx->sel_mean[i]) / (ctx->sel_std[i] > 0 ? ctx->sel_std[i] : 1.0f);
         uint8_t mask[ZF_MLP_CLASSES];
         class_mask(*col, mask);
         int32_t label = -1;
@@ -1163,12 +1167,15 @@ extern "C" zf_status zf_tune(zf_ctx* ctx, const zf_compressed* const* cols, uint
     // Columns of one (scheme, dtype, bit-width bucket) class: the result is
     // kept for that class and the context's geometry stays automatic, so
     // later calls give every class its own; otherwise the context takes it.
+    // (a string column's int32 offsets are its second part: the class is
+    // that of its bytes, whose decode dominates)
     int cs = -1, cd = -1, cb = -1;
     bool one = true;
     for (uint32_t c = 0; c < ncols && one; c++)
         for (const zf::ChunkInfo& ch : cols[c]->chunks) {
+            if (ch.part != 0) continue;
             const int b = (int)width_bucket(ch.bmax);
-            if (ch.scheme == ZF_LZ77 || (cs >= 0 && (ch.scheme != cs || ch.dtype != cd || b != cb))) {
+            if (cs >= 0 && (ch.scheme != cs || ch.dtype != cd || b != cb)) {
                 one = false;
                 break;
             }
@@ -1193,6 +1200,14 @@ extern "C" zf_status zf_tune(zf_ctx* ctx, const zf_compressed* const* cols, uint
     *n_points = n;
     if (best) *best = best_k;
     return cleanup(ZF_OK);
+}
+
+extern "C" zf_status zf_ctx_rates(const zf_ctx* ctx, int32_t scheme, int32_t dtype, uint32_t bmax, float* decode_gbs,
+                                  float* link_gbs) {
+    if (!ctx || scheme < 0 || scheme >= ZF_NSCHEMES || dtype < 0 || dtype > ZF_F64 || bmax > 64) return ZF_EINVAL;
+    if (decode_gbs) decode_gbs[0] = ctx->tuned[scheme][dtype][width_bucket(bmax)].gbs;
+    if (link_gbs) link_gbs[0] = ctx->link_gbs;
+    return ZF_OK;
 }
 
 extern "C" zf_status zf_ctx_tuned_geometry(const zf_ctx* ctx, int32_t scheme, int32_t dtype, uint32_t bmax,

@@ -16,8 +16,9 @@ pytestmark = pytest.mark.gpu
 def test_fact_table_40gb_batched_graph():
     import torch
     import bench
-    cols, pieces = bench.build_fact_table(zf, bench.FACT_ROWS)
-    handles = [h for h, _, _, _ in pieces]
+    cfg = bench.build_c4(zf, 1, bench.FACT_ROWS, keep=True)
+    cols = cfg.expects
+    handles = cfg.handles
     try:
         raw = sum(c.nbytes for c in cols)
         assert raw == 40_000_000_000
@@ -26,26 +27,26 @@ def test_fact_table_40gb_batched_graph():
         zf.zf_ctx_set_ring(ctx, 3)
         dev = [torch.empty(c.nbytes, dtype=torch.uint8, device="cuda") for c in cols]
         outs, caps = [], []
-        for h, ci, r0, n in pieces:
-            isz = cols[ci].itemsize
-            outs.append(dev[ci].data_ptr() + r0 * isz)
-            caps.append(n * isz)
+        for parts in cfg.parts:
+            for ci, off, n in parts:
+                outs.append(dev[ci].data_ptr() + off)
+                caps.append(n)
         for rep in range(2):                       # capture, then replay
             for d in dev:
                 d.fill_(0x5A)
             torch.cuda.synchronize()               # the library runs on its own streams
             zf.zf_transfer_decompress(ctx, handles, outs, caps)
             st, stats = zf.zf_sync(ctx)
-            assert stats.raw_bytes == raw and stats.n_chunks == len(pieces)
+            assert stats.raw_bytes == raw and stats.n_chunks == len(handles)
             for ci, c in enumerate(cols):
                 assert np.array_equal(dev[ci].cpu().numpy().view(c.dtype), c), (rep, W.FACT_COLUMNS[ci][0])
         # sampled pieces decoded by the oracle from the library's bytes
         rng = np.random.default_rng(4)
-        for k in rng.choice(len(pieces), 16, replace=False):
-            h, ci, r0, n = pieces[k]
-            ref = oracle.decode(zf.zf_compressed_bytes(h))
-            assert np.array_equal(ref, cols[ci][r0:r0 + n])
+        for k in rng.choice(len(handles), 16, replace=False):
+            (ci, off, n), = cfg.parts[k]
+            isz = cols[ci].itemsize
+            ref = oracle.decode(zf.zf_compressed_bytes(handles[k]))
+            assert np.array_equal(ref, cols[ci][off // isz:(off + n) // isz])
         zf.zf_ctx_destroy(ctx)
     finally:
-        for h in handles:
-            zf.zf_compressed_free(h)
+        cfg.free(zf)

@@ -104,3 +104,88 @@ def test_float2int_full_size_column(gpu):
             assert np.array_equal(_bits(ref), _bits(got[r0:r0 + rows]))
     finally:
         zf.zf_compressed_free(h)
+
+
+def _f2i_column(e: int, d: np.ndarray) -> bytes:
+    """A one-chunk Float2Int column of the integers d at exponent e (no
+    exceptions), written from the container layout: FOR reference = min(d),
+    packed d - min at b = bits(max - min)."""
+    import struct
+    ref = int(d.min())
+    u = [int(v) - ref for v in d]
+    b = max(u).bit_length()
+    acc = 0
+    for i, v in enumerate(u):
+        acc |= v << (i * b)
+    packed = acc.to_bytes((len(u) * b + 7) // 8, "little")
+    rows = len(d)
+    s0 = 64
+    s1 = (s0 + len(packed) + 15) // 16 * 16
+    blob = bytearray(s1)
+    struct.pack_into("<IBBBBIIq", blob, 0, 0x4B48435A, zf.ZF_FLOAT2INT, zf.ZF_F64, b, 0, rows, 0, ref)
+    struct.pack_into("<3I3I", blob, 24, s0, s1, s1, len(packed), 0, 0)
+    blob[48] = e
+    blob[s0:s0 + len(packed)] = packed
+    col = bytearray(64 + 32)
+    cr = (rows + 1023) // 1024 * 1024
+    struct.pack_into("<IHBBIIQQQI", col, 0, 0x4C4F435A, 1, zf.ZF_FLOAT2INT, zf.ZF_F64, 1, cr, rows, 8 * rows,
+                     96 + len(blob), 0)
+    struct.pack_into("<QQQII", col, 64, 96, len(blob), 0, rows, 0)
+    return bytes(col + blob)
+
+
+def _hard_integers(e: int, rng) -> np.ndarray:
+    """Random magnitudes up to 2^53, exact multiples of 5^e, the bounds, and
+    the integers nearest to d / 5^e being halfway between two doubles."""
+    n = 4000
+    bits = rng.integers(1, 54, n)
+    a = [int(v) for v in (rng.integers(0, 2**62, n, dtype=np.int64) >> (62 - bits)) + 1]
+    p = 5 ** e
+    a += [int(k) * p for k in rng.integers(1, max(2, 2**53 // p), 500)]
+    a += [1, 2**53, 2**53 - 1, 2**52 + 1] + [10**k for k in range(16)]
+    if e:
+        for _ in range(1500):
+            E = int(rng.integers(-20, 53))
+            if 2**E * p > 2**53:
+                continue
+            num = (2 * int(rng.integers(2**52, 2**53)) + 1) * p
+            sh = 53 - E
+            base = num >> sh if sh > 0 else num << -sh
+            a += [v for v in (base - 1, base, base + 1) if 0 < v <= 2**53]
+    a = np.array([min(v, 2**53) for v in a], np.int64)
+    sign = rng.integers(0, 2, len(a)) * 2 - 1
+    return a * sign
+
+
+@pytest.mark.parametrize("e", range(19))
+def test_float2int_every_exponent_against_the_oracle(gpu, e):
+    """The integer-multiply decode equals the oracle's IEEE division d / 10^e
+    at every exponent, on the integers where rounding is hardest."""
+    d = _hard_integers(e, np.random.default_rng(900 + e))
+    buf = _f2i_column(e, d)
+    ref = oracle.decode(buf)
+    assert np.array_equal(_bits(ref), _bits(d.astype(np.float64) / 10.0 ** e))
+    h = zf.zf_compressed_from_bytes(buf)
+    try:
+        for resident in (False, True):
+            got, = gpu.decode([h], [(np.float64, len(d))], resident=resident)
+            assert np.array_equal(_bits(got), _bits(ref)), (e, resident)
+    finally:
+        zf.zf_compressed_free(h)
+
+
+def test_float2int_integer_beyond_2_53_is_corrupt(gpu):
+    for d in (np.array([2**53 + 1, 5], np.int64), np.array([-(2**53) - 1, 0], np.int64)):
+        buf = _f2i_column(2, d)
+        with pytest.raises(oracle.OracleError):
+            oracle.decode(buf)
+        h = zf.zf_compressed_from_bytes(buf)
+        try:
+            gpu.decode([h], [(np.float64, len(d))], expect=zf.ZF_ECORRUPT)
+            ok = np.array([2**53, -(2**53)], np.int64)   # the bounds themselves decode
+            h2 = zf.zf_compressed_from_bytes(_f2i_column(2, ok))
+            got, = gpu.decode([h2], [(np.float64, 2)])
+            zf.zf_compressed_free(h2)
+            assert np.array_equal(_bits(got), _bits(ok.astype(np.float64) / 100.0))
+        finally:
+            zf.zf_compressed_free(h)

@@ -171,6 +171,32 @@ def test_strdict_device_detects_corrupt_streams(gpu):
         zf.zf_compressed_free(h)
 
 
+@pytest.mark.parametrize("stream_rows", [32, 64, 128, 256, 512, 1024, 2048, 4096])
+def test_ans_stream_lengths(gpu, stream_rows):
+    """Every stream length of the format (2^5..2^12 rows per rANS stream,
+    header byte 48): library bytes equal the oracle's, and the GPU decode of
+    both equals the column, on ragged chunks whose last stream is short, an
+    int64 column of 256 values, and a chunk with fewer rows than a stream."""
+    rng = np.random.default_rng(700 + stream_rows)
+    cases = [
+        (rng.choice([65, 78, 82], 130003, p=[0.25, 0.5, 0.25]).astype(np.int32), 1 << 16),
+        (rng.integers(-(1 << 63), (1 << 63) - 1, 256, dtype=np.int64)[rng.integers(0, 256, 40001)], 8192),
+        (rng.integers(0, 3, 17).astype(np.int32), 1024),
+    ]
+    for x, cr in cases:
+        col = zf.Column(x)
+        h = zf.zf_compress_host(zf.zf_plan(None, col, scheme=zf.ZF_ANS, chunk_rows=cr,
+                                           ans_stream_rows=stream_rows), col)
+        try:
+            ob = oracle.encode(x, oracle.ANS, cr, ans_stream_rows=stream_rows)
+            assert zf.zf_compressed_bytes(h) == ob
+            for resident in (False, True):
+                got, = gpu.decode([h], out_specs(x), resident=resident)
+                assert np.array_equal(got, x), (stream_rows, cr, resident)
+        finally:
+            zf.zf_compressed_free(h)
+
+
 def test_ans_columns(gpu):
     """Dictionary + ANS: library- and oracle-encoded low-cardinality columns
     (ragged chunks and streams, one value, 256 values, type extremes) through

@@ -104,3 +104,32 @@ def test_tune_of_one_class_is_kept_for_that_class(columns):
             assert np.array_equal(got, x2)
     finally:
         g.close()
+
+
+def test_measured_rates_for_johnsons_rule(columns):
+    """zf_measure_copy records the link rate of the call's own pieces and a
+    resident zf_tune of one class records that class's decode rate: the rates
+    the transfer's Johnson ordering (Section 3.3) reads; a transfer in that
+    order, in the order given and in reverse all decode exactly."""
+    cols, hs = columns
+    g = Gpu()
+    try:
+        assert zf.zf_ctx_rates(g.ctx, zf.ZF_DELTA_BP, zf.ZF_I64, 8) == (0.0, 0.0)
+        ms = zf.zf_measure_copy(g.ctx, hs, 3)
+        comp = sum(zf.zf_compressed_info(h)[1] for h in hs)
+        dec, link = zf.zf_ctx_rates(g.ctx, zf.ZF_DELTA_BP, zf.ZF_I64, 8)
+        assert dec == 0.0 and link == pytest.approx(comp / (ms * 1e6), rel=1e-3) and link > 1.0
+        (x, s, cr), h = cols[0], hs[0]
+        buf = g.alloc(out_specs(x))[0]
+        pts, best = zf.zf_tune(g.ctx, [h], [buf.data_ptr()], [buf.numel()], transfer=False, reps=2)
+        raw = zf.zf_compressed_info(h)[0]
+        rates = [zf.zf_ctx_rates(g.ctx, zf.ZF_DELTA_BP, zf.ZF_I64, w)[0] for w in (8, 16, 32, 64)]
+        assert any(r == pytest.approx(raw / (min(p.ms for p in pts) * 1e6), rel=1e-3) for r in rates)
+        specs = [sp for x2, s2, cr2 in cols for sp in out_specs(x2)]
+        for flags, order in ((0, [0, 1, 2]), (zf.ZF_KCFG_KEEP_ORDER, [0, 1, 2]), (zf.ZF_KCFG_KEEP_ORDER, [2, 1, 0])):
+            zf.zf_ctx_set_kcfg(g.ctx, 0, 0, 0, 1 << 20, flags)
+            got = g.decode([hs[i] for i in order], [specs[i] for i in order])
+            for i, y in zip(order, got):
+                assert np.array_equal(y, cols[i][0]), (flags, order)
+    finally:
+        g.close()

@@ -36,8 +36,14 @@ def test_selector_trained_on_measured_labels_beats_the_heuristic():
                 if tt[k] >= 0:
                     heur.append((tt[k] - tt[tt >= 0].min()) / tt[tt >= 0].min())
             assert res["regret"] < np.mean(heur)
-            # zf_plan with the attached network makes the same choice as the batch prediction
-            zf.zf_ctx_set_selector(ctx, net, res["mean"], res["std"])
+            # the network standardizes its inputs with the training rows' statistics
+            mean, std = zf.zf_mlp_get_scaling(net)
+            Ftr = F[:n_train].astype(np.float64)
+            assert np.allclose(mean, Ftr.mean(0), rtol=1e-4, atol=1e-5)
+            sd = Ftr.std(0)
+            assert np.allclose(std, np.where(sd > 0, sd, 1.0), rtol=1e-3, atol=1e-5)
+            # zf_plan with the attached network (its own scaling) makes the same choice as the batch prediction
+            zf.zf_ctx_set_selector(ctx, net)
             for i in (0, 1, 3):
                 x, o, meta = W.selector_column(n_train + 1 + i, cap)
                 p = zf.zf_plan(ctx, zf.Column(x, o), selector=1)

@@ -266,6 +266,26 @@ def test_ans_bytes_equal_the_oracle():
     assert e.value.status == zf.ZF_EINVAL
 
 
+@pytest.mark.parametrize("stream_rows", [32, 64, 128, 256, 1024, 2048, 4096])
+def test_ans_stream_lengths_bytes_equal_the_oracle(stream_rows):
+    """Every stream length (header byte 48): the library's bytes equal the
+    oracle's; a length that is not a power of two in 32..4096 is refused."""
+    for x in _ans_cases()[:3]:
+        for cr in (1024, 65536):
+            col = zf.Column(x)
+            h = zf.zf_compress_host(zf.zf_plan(None, col, scheme=zf.ZF_ANS, chunk_rows=cr,
+                                               ans_stream_rows=stream_rows), col)
+            try:
+                assert zf.zf_compressed_bytes(h) == oracle.encode(x, oracle.ANS, cr, ans_stream_rows=stream_rows)
+            finally:
+                zf.zf_compressed_free(h)
+    col = zf.Column(_ans_cases()[0])
+    for bad in (16, 48, 8192):
+        with pytest.raises(zf.ZfError) as e:
+            zf.zf_compress_host(zf.zf_plan(None, col, scheme=zf.ZF_ANS, ans_stream_rows=bad), col)
+        assert e.value.status == zf.ZF_EINVAL
+
+
 def test_ans_host_checks():
     x = _ans_cases()[0]
     b = oracle.encode(x, oracle.ANS, 65536)
@@ -277,6 +297,8 @@ def test_ans_host_checks():
     bb = bytearray(b); struct.pack_into("<H", bb, o1, struct.unpack_from("<H", b, o1)[0] + 1); bad.append(bb)  # sum
     bb = bytearray(b); struct.pack_into("<I", bb, o1 + 8 + 4, 2); bad.append(bb)              # stream of 2 bytes
     bb = bytearray(b); bb[off + 6] = 11; bad.append(bb)                                       # scale bits
+    for k in (4, 13, 8):                                                                      # stream length byte
+        bb = bytearray(b); bb[off + 48] = k; bad.append(bb)
     for bb in bad:
         with pytest.raises(zf.ZfError) as e:
             zf.zf_compressed_from_bytes(bytes(bb))

@@ -144,11 +144,11 @@ def dates_rle(seed: int, n: int, mean_bits: int = 3) -> np.ndarray:
     uniformly from the 2,557 TPC-H days, each run independent of the last."""
     est = n // (1 << mean_bits) + 1024
     while True:
-        lens = run_lengths_geometric(seed, 201, 0, est, mean_bits)
+        lens = parallel_rows(lambda a, c: run_lengths_geometric(seed, 201, a, c, mean_bits), est, piece=1 << 22)
         if lens.sum() >= n:
             break
         est *= 2
-    vals = uniform_int(seed, 202, 0, est, DATE_LO, DATE_HI + 1)
+    vals = parallel_rows(lambda a, c: uniform_int(seed, 202, a, c, DATE_LO, DATE_HI + 1), est, piece=1 << 22)
     out = np.repeat(vals.astype(np.int32), lens)
     return np.ascontiguousarray(out[:n])
 
