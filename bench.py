@@ -71,7 +71,7 @@ FACT_WORKLOAD = ("batched: 16-column fact table x {rows:,} rows (2 int32 uniform
 # Committed ncu summaries that give each roofline kernel's DRAM traffic per
 # launch; a figure is used only while the kernel sources hash as recorded.
 KERNEL_SOURCES = ("paper_2602_08190_gb300/csrc/zf_device.cuh", "paper_2602_08190_gb300/csrc/zf_kernels.cu",
-                  "paper_2602_08190_gb300/csrc/zf_f2i.h")
+                  "paper_2602_08190_gb300/csrc/zf_f2i.h", "paper_2602_08190_gb300/csrc/zf_strdict.cuh")
 TRAFFIC_PROFILES = {"c4": "profiles/batched_fact_table_decode.md", "c2": "profiles/delta_i64_decode_64M_rows.md"}
 
 
@@ -144,7 +144,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
             # nvidia-smi takes a moment to start: wait for its first sample so
@@ -266,12 +266,13 @@ class Cfg:
     (stride, array of every stride-th element))."""
 
     def __init__(self, name, workload, handles, buf_bytes, parts, expects, kernel, kernel_idx=None,
-                 batched=False, stage_mb=64):
+                 batched=False, stage_mb=64, compare_batched=False):
         self.name, self.workload, self.handles = name, workload, handles
         self.buf_bytes, self.parts, self.expects = buf_bytes, parts, expects
         self.kernel = kernel
         self.kernel_idx = list(range(len(handles))) if kernel_idx is None else kernel_idx
         self.batched, self.stage_mb = batched, stage_mb
+        self.compare_batched = compare_batched     # also time the resident decode in the batched kernel
 
     def free(self, zf):
         for h in self.handles:
@@ -311,10 +312,12 @@ def build_c1(zf, seed):
 def build_c2(zf, seed, rows):
     import zf_workloads as W
     keys, dates = W.sorted_keys(seed, rows), W.dates_rle(seed, rows)
-    return single(zf, "c2", f"group_parallel: {rows:,} int64 sorted keys (gaps geometric mean 4; delta + bit-packing, "
-                  f"1024-row blocks) + {rows:,} int32 dates (2,557 days, runs geometric mean 8; RLE), 1M-row chunks, "
-                  "double-buffered transfer", [(keys, zf.ZF_DELTA_BP, CHUNK_ROWS), (dates, zf.ZF_RLE, CHUNK_ROWS)],
-                  "tiles_kernel<DELTA_BP, int64> (the keys)", kernel_idx=[0])
+    cfg = single(zf, "c2", f"group_parallel: {rows:,} int64 sorted keys (gaps geometric mean 4; delta + bit-packing, "
+                 f"1024-row blocks) + {rows:,} int32 dates (2,557 days, runs geometric mean 8; RLE), 1M-row chunks, "
+                 "double-buffered transfer", [(keys, zf.ZF_DELTA_BP, CHUNK_ROWS), (dates, zf.ZF_RLE, CHUNK_ROWS)],
+                 "tiles_kernel<DELTA_BP, int64> (the keys)", kernel_idx=[0])
+    cfg.compare_batched = True
+    return cfg
 
 
 def build_c3(zf, seed, text, scheme, chunk_mb):
@@ -420,6 +423,39 @@ def measure(zf, torch, cfg: Cfg, args, local: int, streams, flush, barrier=None,
     zf.zf_transfer_decompress(ctx, cfg.handles, outs, caps)
     zf.zf_sync(ctx)
     verify(cfg, bufs)
+    tuned = None
+    if not args.no_tune:
+        # the geometry: zf_tune's exhaustive search of the resident decode (tile rows x threads, 15
+        # points), then the pipeline stage size by timing the transfer at each candidate
+        t0 = time.perf_counter()
+        # one search per output column (each a single class: the context keeps a geometry per class)
+        by_col = {}
+        for i, p in enumerate(cfg.parts):
+            by_col.setdefault(p[0][0], []).append(i)
+        npts, per_class = 0, []
+        for b, idx in by_col.items():
+            oo = [bufs[bb].data_ptr() + off for i in idx for bb, off, n in cfg.parts[i]]
+            cc = [n for i in idx for bb, off, n in cfg.parts[i]]
+            pts, best = zf.zf_tune(ctx, [cfg.handles[i] for i in idx], oo, cc, transfer=False, reps=args.tune_reps)
+            npts += len(pts)
+            per_class.append((best.tile_rows, best.threads))
+        stage_ms = {}
+        for st_mb in (4, 8, 16, 32, 64, 128):
+            zf.zf_ctx_set_kcfg(ctx, 0, 0, args.ctas_per_sm, st_mb << 20, flags & ~zf.ZF_KCFG_GRAPH)
+            tt = []
+            for _ in range(1 + max(1, args.tune_reps)):
+                zf.zf_transfer_decompress(ctx, cfg.handles, outs, caps)
+                st, stats = zf.zf_sync(ctx)
+                tt.append(stats.total_ms)
+            stage_ms[st_mb] = float(np.median(tt[1:]))
+        st_best = min(stage_ms, key=stage_ms.get)
+        zf.zf_ctx_set_kcfg(ctx, 0, 0, args.ctas_per_sm, st_best << 20, flags)
+        tuned = {"per_column_tile_rows_threads": sorted(set(per_class)), "stage_bytes": st_best << 20,
+                 "resident_points": npts, "stage_ms": {str(k): round(v, 4) for k, v in stage_ms.items()},
+                 "search_s": round(time.perf_counter() - t0, 2)}
+        zf.zf_transfer_decompress(ctx, cfg.handles, outs, caps)
+        zf.zf_sync(ctx)
+        verify(cfg, bufs)
     res = [zf.zf_upload(ctx, h) for h in cfg.handles]
     kres = [res[i] for i in cfg.kernel_idx]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -439,6 +475,19 @@ def measure(zf, torch, cfg: Cfg, args, local: int, streams, flush, barrier=None,
         st, stats = zf.zf_sync(ctx)
         return (time.perf_counter() - t0) * 1e3, stats.n_launches
 
+    # the raw link at the call's own pieces, measured on a second context
+    # (so the measured rate does not reorder the timed context's graph) and
+    # interleaved with the end-to-end steps, so both see the same host
+    lctx = zf.zf_ctx_create(local, copy_s.cuda_stream, comp_s.cuda_stream)
+    stage = tuned["stage_bytes"] if tuned else int(cfg.stage_mb * (1 << 20))
+    zf.zf_ctx_set_kcfg(lctx, args.tile_rows, args.threads, args.ctas_per_sm, stage, flags | zf.ZF_KCFG_KEEP_ORDER)
+    link_acc = []
+
+    def e2e_and_link():
+        ms, nl = e2e()
+        link_acc.append(zf.zf_measure_copy(lctx, cfg.handles, 1))
+        return ms, nl
+
     for _ in range(args.warmup):
         resident(res, outs, caps)
         resident(kres, kouts, kcaps)
@@ -446,7 +495,7 @@ def measure(zf, torch, cfg: Cfg, args, local: int, streams, flush, barrier=None,
     launches = 0
     t_res, t_k, t_e = [], [], []
     for loop, fn, acc in ((0, lambda: resident(res, outs, caps), t_res), (1, lambda: resident(kres, kouts, kcaps), t_k),
-                          (2, e2e, t_e)):
+                          (2, e2e_and_link, t_e)):
         if barrier:
             barrier()
         if clk:
@@ -461,9 +510,22 @@ def measure(zf, torch, cfg: Cfg, args, local: int, streams, flush, barrier=None,
             clk.window_end()
     # the decode after timing is still exact (graph replays included)
     verify(cfg, bufs)
-    link_ms = zf.zf_measure_copy(ctx, cfg.handles, 5)
+    link_ms = float(np.mean(link_acc))
+    link_med = float(np.median(link_acc))
+    batched_ms = None
+    if cfg.compare_batched:
+        # the same resident decode through the batched work-queue kernel
+        zf.zf_ctx_set_kcfg(ctx, args.tile_rows, args.threads, args.ctas_per_sm, stage, zf.ZF_KCFG_BATCHED)
+        bt = []
+        for i in range(args.warmup + args.steps):
+            ms, nl = resident(res, outs, caps)
+            if i >= args.warmup:
+                bt.append(ms)
+        batched_ms = float(np.mean(bt))
+        verify(cfg, bufs)
     for r in res:
         zf.zf_resident_free(r)
+    zf.zf_ctx_destroy(lctx)
     zf.zf_ctx_destroy(ctx)
     del bufs
     hbm, kind = peaks()
@@ -476,14 +538,23 @@ def measure(zf, torch, cfg: Cfg, args, local: int, streams, flush, barrier=None,
         "e2e": {"gbs": round(raw / (te * 1e-3) / 1e9, 2), "ms": round(te, 4),
                 "ms_min_median_max": [round(float(np.min(t_e)), 4), round(float(np.median(t_e)), 4),
                                       round(float(np.max(t_e)), 4)],
+                "gbs_median_step": round(raw / (float(np.median(t_e)) * 1e-3) / 1e9, 2),
                 "raw_h2d_link_gbs": round(link, 2), "link_ms": round(link_ms, 4),
-                "link_x_cr_gbs": round(link * cr, 2), "frac_of_link_x_cr": round(raw / (te * 1e-3) / 1e9 / (link * cr), 4)},
+                "link_ms_min_median_max": [round(float(np.min(link_acc)), 4), round(link_med, 4),
+                                           round(float(np.max(link_acc)), 4)],
+                "link_x_cr_gbs": round(link * cr, 2), "frac_of_link_x_cr": round(link_ms / te, 4),
+                "frac_of_link_x_cr_medians": round(link_med / float(np.median(t_e)), 4),
+                "link_sampling": "one copy-only pass of the same pieces after every timed end-to-end step"},
         "kernel": {"name": cfg.kernel, "algorithmic_bytes_per_launch": kraw + kcomp, "launch_ms": round(tk, 4),
                    "achieved_gbs": round((kraw + kcomp) / (tk * 1e-3) / 1e9, 1), "peak_gbs": hbm, "peak_kind": kind,
                    "frac": round((kraw + kcomp) / (tk * 1e-3) / 1e9 / hbm, 4)},
         "parity": "decode equals the generator's columns before and after timing",
         "launches": launches,
     }
+    rec["geometry"] = tuned if tuned else "built-in (no search)"
+    if batched_ms is not None:
+        rec["resident_batched"] = {"gbs": round(raw / (batched_ms * 1e-3) / 1e9, 2), "ms": round(batched_ms, 4),
+                                   "vs_single_scheme": round(tr / batched_ms, 4)}
     return rec, (tr, tk, te), (raw, comp, kraw + kcomp, link)
 
 
@@ -557,16 +628,25 @@ SELECTOR_METRIC = "learned selector: mean regret vs exhaustive class search on h
 
 def selector_dataset(zf, ctx, seeds, cap_rows: int, reps: int = 2):
     """Features and measured per-class transfer+decode times of the columns
-    with the given seeds."""
+    with the given seeds (columns are generated a few ahead on host threads
+    while the GPU measures the current one)."""
+    import concurrent.futures
     import zf_workloads as W
     F, T, fam, dts = [], [], [], []
-    for s in seeds:
-        x, o, meta = W.selector_column(s, cap_rows)
+    seeds = list(seeds)
+    ex = concurrent.futures.ThreadPoolExecutor(4)
+    ahead = [ex.submit(W.selector_column, s, cap_rows) for s in seeds[:8]]
+    for i, s in enumerate(seeds):
+        x, o, meta = ahead[i].result()
+        ahead[i] = None
+        if i + 8 < len(seeds):
+            ahead.append(ex.submit(W.selector_column, seeds[i + 8], cap_rows))
         col = zf.Column(x, o)
         F.append(zf.zf_column_features(col))
         T.append(zf.zf_measure_classes(ctx, col, reps))
         fam.append(meta["family"])
         dts.append(meta.get("dtype", "bytes"))
+    ex.shutdown()
     return np.array(F, np.float32), np.array(T, np.float32), fam, dts
 
 
@@ -896,6 +976,8 @@ def main():
     ap.add_argument("--stage-mb", type=float, default=0)
     ap.add_argument("--slots", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--no-tune", action="store_true", help="time the built-in geometry (no zf_tune search first)")
+    ap.add_argument("--tune-reps", type=int, default=1, help="timed runs per point of the geometry search")
     ap.add_argument("--profile", choices=["keys", "dates", "both", "for", "float", "ans", "strdict", "lz77", "fact"],
                     default=None,
                     help="only decode the resident column(s) --steps times (for ncu captures)")
@@ -1003,7 +1085,12 @@ def main():
                     "raw_link_at": "the call's own pieces (zf_measure_copy: the same copies, no decode)",
                     "link_x_cr_gbs": rec["e2e"]["link_x_cr_gbs"],
                     "target_0.9_link_x_cr_gbs": round(0.9 * rec["e2e"]["link_x_cr_gbs"], 2),
-                    "frac_of_link_x_cr": round(e2e / world / rec["e2e"]["link_x_cr_gbs"], 4)},
+                    "frac_of_link_x_cr": round(e2e / world / rec["e2e"]["link_x_cr_gbs"], 4),
+                    "ms_min_median_max": rec["e2e"]["ms_min_median_max"],
+                    "gbs_median_step": rec["e2e"]["gbs_median_step"],
+                    "frac_of_link_x_cr_medians": rec["e2e"]["frac_of_link_x_cr_medians"],
+                    "link_ms_min_median_max": rec["e2e"]["link_ms_min_median_max"],
+                    "link_sampling": rec["e2e"]["link_sampling"]},
             "roofline": {"bound": "hbm", "kernel": rec["kernel"]["name"], "achieved": round(achieved, 1), "peak": hbm,
                          "peak_kind": kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
                          "traffic": rec["kernel"].get("traffic"), "traffic_note": rec["kernel"].get("traffic_note"),

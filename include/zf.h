@@ -314,6 +314,17 @@ zf_status zf_tune(zf_ctx* ctx, const zf_compressed* const* cols, uint32_t ncols,
                   const uint64_t* d_out_bytes, int32_t transfer, uint32_t reps, zf_tune_point* points,
                   uint32_t max_points, uint32_t* n_points, zf_kcfg* best);
 
+/* The chunk-size dimension of the search (the C of Section 4's <L,S,C> plus
+ * the chunk size the transfer moves): encode the host column `col` with
+ * `scheme` at each of the n candidate chunk sizes chunk_rows[i] (rows per
+ * chunk; bytes per chunk for a string dictionary), time the transfer +
+ * decode of each (`reps` runs after one warm-up, 0 = 3; median of zf_sync's
+ * total_ms) into ms[i], -1 where the scheme or size does not fit the column,
+ * and set *best (nullable) to the index of the fastest.  ZF_EINVAL if none
+ * fits.  The context's geometry and ring are used as they are. */
+zf_status zf_tune_chunk_rows(zf_ctx* ctx, const zf_column* col, int32_t scheme, const uint32_t* chunk_rows,
+                             uint32_t n, uint32_t reps, float* ms, uint32_t* best);
+
 /* The geometry a launch of one class would use now: the context's
  * tile_rows / threads where set, else the class's tuned entry, else the
  * built-in values (128 threads; warp jobs of 2048 rows for delta, 4096 for

@@ -23,7 +23,7 @@ __all__ = [
     "zf_ctx_set_ring", "zf_plan", "zf_compress_host", "zf_compressed_info", "zf_compressed_free",
     "zf_compressed_bytes", "zf_compressed_from_bytes", "zf_transfer_decompress", "zf_sync", "zf_upload",
     "zf_resident_free", "zf_decompress_resident", "zf_decompress_device_noalloc", "zf_tune", "zf_tune_point",
-    "zf_ctx_tuned_geometry", "zf_measure_copy", "zf_johnson_order", "ZF_KCFG_KEEP_ORDER", "zf_ctx_rates", "zf_mlp_get_scaling",
+    "zf_ctx_tuned_geometry", "zf_measure_copy", "zf_johnson_order", "ZF_KCFG_KEEP_ORDER", "zf_ctx_rates", "zf_mlp_get_scaling", "zf_tune_chunk_rows",
     "zf_column_features", "zf_measure_classes", "zf_ctx_set_selector", "zf_mlp_create", "zf_mlp_destroy",
     "zf_mlp_get_params", "zf_mlp_set_params", "zf_mlp_forward", "zf_mlp_grad", "zf_mlp_adam", "zf_mlp_train",
     "zf_mlp_predict", "ZF_MLP_PARAMS", "ZF_MLP_CLASSES", "EXPORTED", "LIB_PATH",
@@ -111,6 +111,8 @@ _SIGS = {
     "zf_ctx_rates": [_vp, ctypes.c_int32, ctypes.c_int32, _u32, ctypes.POINTER(ctypes.c_float),
                      ctypes.POINTER(ctypes.c_float)],
     "zf_mlp_get_scaling": [_vp, _vp, _vp],
+    "zf_tune_chunk_rows": [_vp, ctypes.POINTER(zf_column), ctypes.c_int32, _vp, _u32, _u32, _vp,
+                           ctypes.POINTER(_u32)],
     "zf_johnson_order": [_vp, _vp, _u32, _vp],
     "zf_tune": [_vp, ctypes.POINTER(_vp), _u32, ctypes.POINTER(_vp), ctypes.POINTER(_u64), ctypes.c_int32, _u32,
                 ctypes.POINTER(zf_tune_point), _u32, ctypes.POINTER(_u32), ctypes.POINTER(zf_kcfg)],
@@ -377,3 +379,13 @@ def zf_mlp_get_scaling(net: int) -> tuple[np.ndarray, np.ndarray]:
     m, sd = np.zeros(32, np.float32), np.zeros(32, np.float32)
     _check(_L.zf_mlp_get_scaling(net, m.ctypes.data, sd.ctypes.data), "zf_mlp_get_scaling")
     return m, sd
+
+
+def zf_tune_chunk_rows(ctx: int, col: Column, scheme: int, chunk_rows, reps: int = 3) -> tuple[np.ndarray, int]:
+    """(ms per candidate chunk size, -1 where it does not fit; index of the fastest)."""
+    cr = np.ascontiguousarray(chunk_rows, np.uint32)
+    ms = np.zeros(len(cr), np.float32)
+    best = _u32()
+    _check(_L.zf_tune_chunk_rows(ctx, ctypes.byref(col.c), scheme, cr.ctypes.data, len(cr), reps, ms.ctypes.data,
+                                 ctypes.byref(best)), "zf_tune_chunk_rows", ctx)
+    return ms, best.value

@@ -194,10 +194,15 @@ __host__ __device__ inline uint32_t stage_bytes_for(uint32_t bmax) { return ((kW
 // FLOAT2INT (T = int64 bits of the doubles): the integer d = reference + u
 // becomes the double nearest d / 10^e, built with integer multiplies
 // (zf::f2i_bits; `e` and its reciprocal row `rr` are the chunk's).
-template <class T, int SCHEME, bool NARROW>
+// WIN: 1 = NARROW (b <= 8, four int32 values from one two-word window),
+// 0 = one extraction per value, 2 = Float2Int chunk whose integers all lie in
+// [0, 2^32) with e >= 1 (32-bit extraction and zf::f2i_bits_u32, `kexp` the
+// chunk's exponent constant).
+template <class T, int SCHEME, int WIN>
 __device__ __forceinline__ bool fp_rows(const ZfDevChunk& c, const Hdr& h, T* dst, const uint32_t* wsm, uint32_t nr,
                                         uint32_t b, uint32_t lane, uint32_t e = 0,
-                                        const zf::F2IRecip& rr = zf::F2IRecip{0, 0, 0, 0}, bool chk = true) {
+                                        const zf::F2IRecip& rr = zf::F2IRecip{0, 0, 0, 0}, bool chk = true,
+                                        int32_t kexp = 0) {
     // Float2Int: four values (a 32-byte sector) per lane per step
     constexpr int V = SCHEME == ZF_FLOAT2INT ? 4 : 16 / sizeof(T);
     const T* dict = reinterpret_cast<const T*>(c.blob + h.off[0]);
@@ -206,8 +211,26 @@ __device__ __forceinline__ bool fp_rows(const ZfDevChunk& c, const Hdr& h, T* ds
     bool bad = false;
 #pragma unroll 2
     for (uint32_t i0 = lane * V; i0 < nr; i0 += 32 * V) {
+        if constexpr (WIN == 2) {
+            const uint32_t m32 = b >= 32 ? 0xFFFFFFFFu : (1u << b) - 1u, ref32 = (uint32_t)h.ref;
+            T v[V];
+#pragma unroll
+            for (int k = 0; k < V; k++) {
+                const uint32_t pos = (i0 + k) * b, w = pos >> 5;
+                const uint32_t u = __funnelshift_r(wsm[w], wsm[w + 1], pos & 31) & m32;
+                v[k] = (T)zf::f2i_bits_u32(ref32 + u, e, rr, kexp);
+            }
+            if (i0 + V <= nr) {
+                store_vec<T, V>(dst + i0, v, al32);
+            } else {
+#pragma unroll
+                for (int k = 0; k < V; k++)
+                    if (i0 + k < nr) dst[i0 + k] = v[k];
+            }
+            continue;
+        }
         uint64_t u[V];
-        if constexpr (NARROW && V == 4) {
+        if constexpr (WIN == 1 && V == 4) {
             uint32_t w4[4];
             extract4<true, uint32_t>(wsm, i0 * b, b, w4);
 #pragma unroll
@@ -298,6 +321,7 @@ __device__ void fp_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t 
         uint32_t e = 0;
         zf::F2IRecip rr{0, 0, 0, 0};
         bool chk = true;   // Float2Int: whether an integer of the chunk can pass 2^53
+        bool u32 = false;  // Float2Int: e >= 1 and every integer of the chunk in [0, 2^32)
         if constexpr (SCHEME == ZF_FLOAT2INT) {
             e = c.blob[48];
             if (e > (uint32_t)zf::kF2IMaxExp) {
@@ -308,6 +332,7 @@ __device__ void fp_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t 
             const int64_t ref = (int64_t)h.ref;
             if (b <= 54 && ref >= -zf::kF2IDMax && ref <= zf::kF2IDMax)
                 chk = ref + (int64_t)((1ull << b) - 1) > zf::kF2IDMax;
+            u32 = e >= 1 && b <= 32 && ref >= 0 && ref + (int64_t)((1ull << b) - 1) < ((int64_t)1 << 32);
         }
         if (b > 8 * sizeof(T) || (SCHEME == ZF_DICT_BP && b > 16)) {
             if (lane == 0) report(err, ZF_ECORRUPT, c.chunk_id);
@@ -333,8 +358,11 @@ __device__ void fp_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t 
             __syncwarp();
             const uint32_t nr = min(kWarpRows, nrows - i * kWarpRows);
             const uint32_t* buf = wsm + (i & 1) * sb;
-            if (V == 4 && b <= 8) bad |= fp_rows<T, SCHEME, true>(c, h, dst + i * kWarpRows, buf, nr, b, lane);
-            else bad |= fp_rows<T, SCHEME, false>(c, h, dst + i * kWarpRows, buf, nr, b, lane, e, rr, chk);
+            if (V == 4 && b <= 8) bad |= fp_rows<T, SCHEME, 1>(c, h, dst + i * kWarpRows, buf, nr, b, lane);
+            else if (SCHEME == ZF_FLOAT2INT && u32)
+                fp_rows<T, SCHEME, 2>(c, h, dst + i * kWarpRows, buf, nr, b, lane, e, rr, false,
+                                      1052 - (int32_t)rr.s - (int32_t)e);
+            else bad |= fp_rows<T, SCHEME, 0>(c, h, dst + i * kWarpRows, buf, nr, b, lane, e, rr, chk);
             __syncwarp();
         }
         if (bad) report(err, ZF_ECORRUPT, c.chunk_id);
@@ -789,6 +817,7 @@ __device__ void rle_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t
 
 // ---------------------------------------------------------------- string dictionary sizes
 // (the decoder is in zf_strdict.cuh)
+constexpr uint32_t kStrCodeBuf = (1024u * 16u / 8u) + 32u;   // one tile of codes at b <= 16, plus the reader's overrun
 constexpr uint32_t kStrWin = 32u * zf::kStrTokenMax + 32u;    // 32 tokens of at most 64 bytes, at the output's alignment
 
 // ---------------------------------------------------------------- single-tile entry points
@@ -816,7 +845,7 @@ __host__ __device__ inline uint32_t warp_smem(int scheme, uint32_t value_bytes, 
     case ZF_FOR_BP: case ZF_DICT_BP: case ZF_FLOAT2INT: return 2 * stage_bytes_for(bmax);
     case ZF_DELTA_BP: return 2 * stage_bytes_for(bmax) + 4096;   // + the store transpose buffer
     case ZF_RLE: return 128 + kRleStages * rle_buf_bytes(value_bytes);   // row bitmask + staging buffers
-    case ZF_STRDICT: return kStrWin;                                    // the output window (codes are read from L1/L2)
+    case ZF_STRDICT: return kStrCodeBuf + kStrWin;                      // one tile of codes + the output window
     }
     return 0;
 }

@@ -97,4 +97,40 @@ ZF_F2I_HD uint64_t f2i_bits(int64_t d, uint32_t e, const F2IRecip& r) {
     return sign | (m + ((uint64_t)(E + 1022) << 52));
 }
 
+// The same double for a chunk whose integers all lie in [0, 2^32), e >= 1:
+// with a < 2^32 the normalized A = A32 * 2^32 (A32 = a shifted until bit 31
+// is set), so the top word of A * R is A32 * R_hi + mulhi32(A32, R_lo), one
+// wide multiply-add, and every shift is a 32-bit one.  `kexp` is the chunk's
+// 1052 - s - e: the biased exponent of the result is kexp + ub - clz32(a).
+// Equal to f2i_bits(a, e, r) for every such a (the rare undecided rounding
+// takes the general path).
+ZF_F2I_HD uint64_t f2i_bits_u32(uint32_t a, uint32_t e, const F2IRecip& r, int32_t kexp) {
+#if defined(__CUDA_ARCH__)
+    const int lz = __clz((int)a);                 // 32 for a = 0 (the result is then replaced by +0.0)
+#else
+    const int lz = a ? __builtin_clz(a) : 32;
+#endif
+    const uint32_t A32 = a << (lz & 31);
+#if defined(__CUDA_ARCH__)
+    const uint32_t hi32 = __umulhi(A32, (uint32_t)r.r64);
+#else
+    const uint32_t hi32 = (uint32_t)(((uint64_t)A32 * (uint32_t)r.r64) >> 32);
+#endif
+    const uint64_t H = (uint64_t)A32 * (r.r64 >> 32) + hi32;
+    const uint32_t ub = (uint32_t)(H >> 63);
+    const uint32_t t = (uint32_t)H >> ub;
+    if (((t & 0x3FFu) - 0x1FFu) < 2u) return a ? f2i_bits((int64_t)a, e, r) : 0ull;
+    // m = H >> (10 + ub) rounded on bit 9 + ub (t's bit 9)
+    const uint32_t sh = 10u + ub;
+    const uint32_t hi = (uint32_t)(H >> 32), lo = (uint32_t)H;
+#if defined(__CUDA_ARCH__)
+    const uint32_t mlo = __funnelshift_r(lo, hi, sh);
+#else
+    const uint32_t mlo = (lo >> sh) | (hi << (32 - sh));
+#endif
+    const uint64_t m = (((uint64_t)(hi >> sh) << 32) | mlo) + ((t >> 9) & 1u);
+    const uint64_t bits = m + ((uint64_t)(uint32_t)(kexp + (int)ub - lz) << 52);
+    return a ? bits : 0ull;
+}
+
 }  // namespace zf

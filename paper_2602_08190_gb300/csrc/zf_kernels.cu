@@ -25,8 +25,35 @@ struct LaunchArgs {
     uint32_t job_rows;     // rows of one warp job (a multiple of 1024)
     uint32_t warp_smem;    // bytes of shared memory per warp
     uint32_t* err;
-    uint32_t* queue;       // [0] next job, [1] CTAs done; batched launches only
+    uint32_t* queue;       // [0] next job, [1] CTAs done, [2 + s] blocks taken near SM s (zf::kQueueWords)
+    uint32_t nsm;          // SMs of the device (string-dictionary launches: SM ranges, at most kAffinitySms)
 };
+
+// The block of a string-dictionary launch this CTA decodes.  The launch's
+// blocks are cut into one contiguous range per SM, and a CTA first takes the
+// next untaken block of the range of the SM it runs on, then of the ranges
+// after it: consecutive blocks decode tokens of the same chunk, so the CTAs
+// sharing an SM read one chunk's dictionary and keep it in that SM's L1.
+// Every CTA gets a block and every block is taken once: there are as many
+// blocks as CTAs, and a CTA that finds every range taken would leave fewer
+// takers than blocks.  Each range counter is raised at most once per CTA, so
+// the search ends after at most nsm atomics.
+__device__ uint32_t claim_near_sm(uint32_t* q, uint32_t nsm) {
+    uint32_t smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    const uint32_t nblk = gridDim.x, per = (nblk + nsm - 1) / nsm;
+    const uint32_t s0 = smid % nsm;
+    for (uint32_t i = 0; i < nsm; i++) {
+        const uint32_t s = s0 + i < nsm ? s0 + i : s0 + i - nsm;
+        const uint64_t lo64 = (uint64_t)s * per;
+        if (lo64 >= nblk) continue;
+        const uint32_t lo = (uint32_t)lo64, cnt = min(per, nblk - lo);
+        if (*reinterpret_cast<volatile uint32_t*>(q + 2 + s) >= cnt) continue;
+        const uint32_t j = atomicAdd(q + 2 + s, 1u);
+        if (j < cnt) return lo + j;
+    }
+    return blockIdx.x;   // not reached (see above)
+}
 
 __device__ __forceinline__ uint32_t find_chunk(const ZfDevChunk* ch, uint32_t n, uint32_t job) {
     uint32_t a = 0, z = n;
@@ -115,7 +142,25 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) tiles_kernel(LaunchAr
     constexpr uint32_t NW = THREADS / 32;
     const uint32_t warp = threadIdx.x >> 5;
     uint32_t* wsm = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(smem4) + warp * a.warp_smem);
-    if constexpr (SCHEME >= 0) {
+    if constexpr (SCHEME == ZF_STRDICT) {
+        __shared__ uint32_t s_blk;
+        if (threadIdx.x == 0) s_blk = a.queue ? claim_near_sm(a.queue, a.nsm) : blockIdx.x;
+        __syncthreads();
+        const uint32_t job = s_blk * NW + warp;
+        if (job < a.njobs) run_job<SCHEME, DT>(a, job, wsm);
+        if (a.queue) {
+            // the last CTA to finish clears the range counters for the next launch on this queue
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                if (atomicAdd(&a.queue[1], 1u) == gridDim.x - 1) {
+                    for (uint32_t s = 0; s < a.nsm; s++) a.queue[2 + s] = 0;
+                    a.queue[1] = 0;
+                    __threadfence();
+                }
+            }
+        }
+    } else if constexpr (SCHEME >= 0) {
         const uint32_t job = blockIdx.x * NW + warp;
         if (job < a.njobs) run_job<SCHEME, DT>(a, job, wsm);
     } else {
@@ -221,7 +266,9 @@ cudaError_t launch_tiles(const TileLaunch& L, cudaStream_t s) {
         if (grid > resident) grid = resident;
     }
     if (grid == 0) return cudaSuccess;
-    LaunchArgs a{L.chunks, L.nchunks, L.ntiles, L.tile_rows, L.smem / nw, L.err, L.scheme < 0 ? L.queue : nullptr};
+    const bool affinity = L.scheme == ZF_STRDICT && L.num_sms > 0 && L.num_sms <= (int)kAffinitySms;
+    LaunchArgs a{L.chunks, L.nchunks, L.ntiles, L.tile_rows, L.smem / nw, L.err,
+                 (L.scheme < 0 || affinity) ? L.queue : nullptr, (uint32_t)L.num_sms};
     fn<<<(unsigned)grid, L.threads, L.smem, s>>>(a);
     return cudaGetLastError();
 }

@@ -6,6 +6,12 @@
 
 namespace zf {
 
+// Words of one decode stream's work queue: [0] next job, [1] CTAs done,
+// [2, 2 + kAffinitySms) blocks taken from each SM's range (string-dictionary
+// launches), zero between launches.
+constexpr uint32_t kAffinitySms = 256;
+constexpr uint32_t kQueueWords = 2 + kAffinitySms + 6;
+
 struct TileLaunch {
     const ZfDevChunk* chunks;   // device descriptors of this launch
     uint32_t nchunks;
@@ -17,7 +23,7 @@ struct TileLaunch {
     uint32_t smem;              // dynamic shared memory: threads/32 slices of equal size
     int num_sms;
     uint32_t* err;
-    uint32_t* queue;
+    uint32_t* queue;            // kQueueWords zeroed words owned by the launching stream
 };
 
 uint32_t warp_smem_bytes(int scheme, int dtype, uint32_t bmax);

@@ -53,7 +53,7 @@ struct zf_ctx {
     uint64_t slot_cap = 0;
     cudaEvent_t ev_copied[kMaxSlots] = {}, ev_free[kMaxSlots] = {};
     cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;
-    uint32_t* d_err = nullptr;     // [2 + 2s, 3 + 2s]: work queue of decode stream s
+    uint32_t* d_err = nullptr;     // [s * kQueueWords, (s + 1) * kQueueWords): work queue of decode stream s
     // The decoders' error word, [0] status bits and [1] first failing chunk, in
     // mapped pinned host memory: the host resets it before a call and reads it
     // after the call's last event, and the kernels write it only when a stream
@@ -467,7 +467,8 @@ zf_status zf_ctx_create(int device, void* copy_stream, void* compute_stream, zf_
         cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess)
         return fail(ZF_ECUDA);
-    if (cudaMalloc(&ctx->d_err, 128) != cudaSuccess || cudaMemset(ctx->d_err, 0, 128) != cudaSuccess)
+    if (cudaMalloc(&ctx->d_err, 4 * zf::kQueueWords * kMaxSlots) != cudaSuccess ||
+        cudaMemset(ctx->d_err, 0, 4 * zf::kQueueWords * kMaxSlots) != cudaSuccess)
         return fail(ZF_ENOMEM);
     if (cudaHostAlloc(&ctx->h_err, 64, cudaHostAllocMapped) != cudaSuccess) return fail(ZF_ENOMEM);
     memset(ctx->h_err, 0, 64);
@@ -732,7 +733,7 @@ zf_status zf_transfer_decompress(zf_ctx* ctx, const zf_compressed* const* cols, 
             ZF_CAP(cudaMemcpyAsync(ctx->slots[slot] + p.slot_off, p.src, p.bytes, cudaMemcpyHostToDevice, ctx->copy));
         ZF_CAP(cudaEventRecord(ctx->ev_copied[slot], ctx->copy));
         ZF_CAP(cudaStreamWaitEvent(ctx->lane[slot], ctx->ev_copied[slot], 0));
-        st = launch_groups(ctx, groups[s], d_desc, k, ctx->lane[slot], ctx->d_err + 2 + 2 * slot);
+        st = launch_groups(ctx, groups[s], d_desc, k, ctx->lane[slot], ctx->d_err + zf::kQueueWords * slot);
         if (st) return abort_capture(st);
         ZF_CAP(cudaEventRecord(ctx->ev_free[slot], ctx->lane[slot]));
     }
@@ -906,7 +907,7 @@ zf_status zf_decompress_resident(zf_ctx* ctx, const zf_resident* const* cols, ui
         ctx->resident_cache = desc;
     }
     if (groups.size() <= 1) {
-        st = launch_groups(ctx, groups, ctx->d_desc, k, ctx->compute, ctx->d_err + 2);
+        st = launch_groups(ctx, groups, ctx->d_desc, k, ctx->compute, ctx->d_err);
     } else {
         // one launch per (scheme, dtype) group, each on its own decode stream,
         // so a launch's tail overlaps the next launch's start
@@ -916,7 +917,7 @@ zf_status zf_decompress_resident(zf_ctx* ctx, const zf_resident* const* cols, ui
         for (size_t gi = 0; gi < groups.size() && st == ZF_OK; gi++) {
             const size_t q = gi % nl;
             st = launch_groups(ctx, std::vector<Group>{groups[gi]}, ctx->d_desc, k, ctx->lane[q],
-                               ctx->d_err + 2 + 2 * q);
+                               ctx->d_err + zf::kQueueWords * q);
         }
         for (size_t q = 0; q < nl; q++) {
             ZF_CU(ctx, cudaEventRecord(ctx->ev_free[q], ctx->lane[q]));
@@ -1020,6 +1021,73 @@ extern "C" zf_status zf_measure_classes(zf_ctx* ctx, const zf_column* col, uint3
     }
     for (void* q : dbuf)
         if (q) cudaFree(q);
+    return result;
+}
+
+// The chunk-size dimension of the search: the column encoded with each
+// candidate chunk size, then timed through the whole transfer + decode.
+extern "C" zf_status zf_tune_chunk_rows(zf_ctx* ctx, const zf_column* col, int32_t scheme, const uint32_t* chunk_rows,
+                                        uint32_t n, uint32_t reps, float* ms, uint32_t* best) {
+    zf::KeepDevice keep_device;
+    if (!ctx || !col || !chunk_rows || !n || !ms || scheme < 0 || scheme >= ZF_NSCHEMES) return ZF_EINVAL;
+    if (ctx->busy) return ZF_EBUSY;
+    if (!reps) reps = 3;
+    uint64_t outs[2] = {0, 0};
+    void* dbuf[2] = {nullptr, nullptr};
+    if (col->dtype == ZF_BYTES) {
+        if (!col->offsets) return ZF_EINVAL;
+        outs[0] = std::max<uint64_t>((uint64_t)(uint32_t)col->offsets[col->n], 16);
+        outs[1] = 4 * (col->n + 1);
+    } else {
+        outs[0] = std::max<uint64_t>(col->n * zf::dtype_size(col->dtype), 16);
+    }
+    cudaSetDevice(ctx->device);
+    for (int o = 0; o < 2; o++)
+        if (outs[o] && cudaMalloc(&dbuf[o], outs[o]) != cudaSuccess) {
+            cudaGetLastError();
+            for (void* q : dbuf)
+                if (q) cudaFree(q);
+            return ZF_ENOMEM;
+        }
+    zf_status result = ZF_OK;
+    int32_t bi = -1;
+    for (uint32_t i = 0; i < n && !result; i++) {
+        ms[i] = -1.0f;
+        zf_plan_t p{};
+        p.scheme = scheme;
+        p.chunk_rows = chunk_rows[i];
+        p.offsets_scheme = ZF_DELTA_BP;
+        p.label = -1;
+        zf_compressed* c = nullptr;
+        std::string why;
+        zf_status st = zf::encode_column(p, *col, &c, &why);
+        if (st == ZF_EINVAL) continue;          // the scheme or the size does not fit this column
+        if (st) {
+            result = st;
+            break;
+        }
+        std::vector<float> t;
+        for (uint32_t r = 0; r < reps + 1 && !result; r++) {
+            const zf_compressed* cc = c;
+            st = zf_transfer_decompress(ctx, &cc, 1, dbuf, outs);
+            if (!st) {
+                zf_stats sts;
+                st = zf_sync(ctx, &sts);
+                if (r) t.push_back(sts.total_ms);
+            }
+            if (st) result = st;
+        }
+        zf::free_compressed(c);
+        if (!result) {
+            std::sort(t.begin(), t.end());
+            ms[i] = t[t.size() / 2];
+            if (bi < 0 || ms[i] < ms[bi]) bi = (int32_t)i;
+        }
+    }
+    for (void* q : dbuf)
+        if (q) cudaFree(q);
+    if (!result && bi < 0) result = ZF_EINVAL;
+    if (!result && best) *best = (uint32_t)bi;
     return result;
 }
 

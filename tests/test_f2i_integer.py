@@ -31,7 +31,10 @@ int main(int argc, char** argv) {
     FILE* fo = fopen(argv[2], "wb");
     int64_t rec[2];
     while (fread(rec, 8, 2, fi) == 2) {
-        uint64_t bits = zf::f2i_bits(rec[0], (uint32_t)rec[1], kTab[rec[1]]);
+        const zf::F2IRecip& r = kTab[rec[1]];
+        uint64_t bits = argv[3][0] == '1'
+            ? zf::f2i_bits_u32((uint32_t)rec[0], (uint32_t)rec[1], r, 1052 - (int32_t)r.s - (int32_t)rec[1])
+            : zf::f2i_bits(rec[0], (uint32_t)rec[1], r);
         fwrite(&bits, 8, 1, fo);
     }
     fclose(fi);
@@ -49,11 +52,11 @@ def harness(tmp_path_factory):
     exe = d / "h"
     subprocess.run(["g++", "-O2", "-std=c++17", "-I", CSRC, "-o", str(exe), str(src)], check=True)
 
-    def run(dv: np.ndarray, ev: np.ndarray) -> np.ndarray:
+    def run(dv: np.ndarray, ev: np.ndarray, u32: bool = False) -> np.ndarray:
         inp = d / "in.bin"
         out = d / "out.bin"
         np.stack([dv.astype(np.int64), ev.astype(np.int64)], 1).tofile(inp)
-        subprocess.run([str(exe), str(inp), str(out)], check=True)
+        subprocess.run([str(exe), str(inp), str(out), "1" if u32 else "0"], check=True)
         return np.fromfile(out, np.uint64)
     return run
 
@@ -63,10 +66,12 @@ def definition(dv: np.ndarray, ev: np.ndarray) -> np.ndarray:
     return (dv.astype(np.float64) / p[ev]).view(np.uint64)
 
 
-def check(run, dv, ev):
+def check(run, dv, ev, u32=False):
     dv = np.asarray(dv, np.int64)
     ev = np.asarray(ev, np.int64)
-    got, want = run(dv, ev), definition(dv, ev)
+    if u32:   # the 32-bit path: integers in [0, 2^32), e >= 1
+        assert dv.min() >= 0 and dv.max() < 2**32 and ev.min() >= 1
+    got, want = run(dv, ev, u32), definition(dv, ev)
     bad = np.nonzero(got != want)[0]
     assert bad.size == 0, [(int(dv[i]), int(ev[i]), hex(int(got[i])), hex(int(want[i]))) for i in bad[:5]]
 
@@ -145,3 +150,45 @@ def test_quotients_next_to_halfway_points(harness):
                     e.append(ee)
     assert len(d) > 50_000
     check(harness, d, e)
+
+
+def test_u32_path_small_integers_every_exponent(harness):
+    a = np.arange(0, 200_001, dtype=np.int64)
+    for e in range(1, 19):
+        check(harness, a, np.full(a.size, e), u32=True)
+
+
+def test_u32_path_random_and_extreme_magnitudes(harness):
+    rng = np.random.default_rng(12)
+    n = 400_000
+    bits = rng.integers(1, 33, n)
+    a = rng.integers(0, 2**32, n, dtype=np.int64) >> (32 - bits)
+    e = rng.integers(1, 19, n)
+    ext = [2**32 - 1, 2**32 - 2, 2**31, 2**31 - 1, 2**31 + 1, 1, 2, 3] + [10**k for k in range(10)] + \
+          [5**k for k in range(14)]
+    d = np.concatenate([a, np.repeat(ext, 18)])
+    e = np.concatenate([e, np.tile(np.arange(1, 19), len(ext))])
+    check(harness, d, e, u32=True)
+
+
+def test_u32_path_next_to_halfway_points(harness):
+    # integers below 2^32 whose quotient lies closest to a halfway point: the
+    # cases the 32-bit path hands to the general one
+    rng = np.random.default_rng(4)
+    d, e = [], []
+    for ee in range(1, 19):
+        p = 5 ** ee
+        for _ in range(4000):
+            E = int(rng.integers(-45, 32))
+            if 2 ** E * p > 2 ** 32:
+                continue
+            n = int(rng.integers(2 ** 52, 2 ** 53))
+            num = (2 * n + 1) * p
+            sh = 53 - E
+            base = num >> sh if sh > 0 else num << -sh
+            for a in (base - 1, base, base + 1, base + 2):
+                if 0 <= a < 2 ** 32:
+                    d.append(a)
+                    e.append(ee)
+    assert len(d) > 20_000
+    check(harness, d, e, u32=True)

@@ -189,3 +189,39 @@ def test_float2int_integer_beyond_2_53_is_corrupt(gpu):
             assert np.array_equal(_bits(got), _bits(ok.astype(np.float64) / 100.0))
         finally:
             zf.zf_compressed_free(h)
+
+
+def _hard_u32(e: int, rng) -> np.ndarray:
+    """Integers in [0, 2^32) (so the chunk takes the decoder's 32-bit path):
+    random magnitudes, 0, the top of the range, and the integers whose
+    quotient by 5^e lies next to a halfway point between two doubles."""
+    a = [int(v) for v in rng.integers(0, 2**32, 3000, dtype=np.int64) >> rng.integers(0, 32, 3000)]
+    a += [0, 1, 2**32 - 1, 2**31, 5**min(e, 13)]
+    p = 5 ** e
+    for _ in range(3000):
+        E = int(rng.integers(-45, 32))
+        if 2**E * p > 2**32:
+            continue
+        num = (2 * int(rng.integers(2**52, 2**53)) + 1) * p
+        sh = 53 - E
+        base = num >> sh if sh > 0 else num << -sh
+        a += [v for v in (base - 1, base, base + 1) if 0 <= v < 2**32]
+    return np.array(a[:4093], np.int64)    # not a multiple of four: a ragged last step
+
+
+@pytest.mark.parametrize("e", range(1, 19))
+def test_float2int_32_bit_path_every_exponent(gpu, e):
+    """Chunks whose integers all lie in [0, 2^32) decode through the 32-bit
+    integer path; the result equals the oracle's division at every exponent."""
+    d = _hard_u32(e, np.random.default_rng(1900 + e))
+    assert d.min() == 0 and d.max() == 2**32 - 1
+    buf = _f2i_column(e, d)
+    ref = oracle.decode(buf)
+    assert np.array_equal(_bits(ref), _bits(d.astype(np.float64) / 10.0 ** e))
+    h = zf.zf_compressed_from_bytes(buf)
+    try:
+        for resident in (False, True):
+            got, = gpu.decode([h], [(np.float64, len(d))], resident=resident)
+            assert np.array_equal(_bits(got), _bits(ref)), (e, resident)
+    finally:
+        zf.zf_compressed_free(h)

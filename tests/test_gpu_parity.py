@@ -41,6 +41,55 @@ def _cases():
 CASES = list(_cases())
 
 
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+def test_for_every_bit_width(gpu, dtype):
+    """FOR + bit-packing at every width b (0..32 for int32, 0..64 for int64),
+    each chunk spanning its full range so that b = bits(max - min); ragged
+    chunk and tile ends; every width path of the decoder (two-word, three-word
+    window, one extraction per value) against the column and the oracle."""
+    rng = np.random.default_rng(61)
+    top = 32 if dtype == np.int32 else 64
+    parts = []
+    for b in range(0, top + 1):
+        n = 3000 + 37 * b
+        lo = -(1 << (top - 1))
+        span = (1 << b) - 1
+        v = rng.integers(0, 1 << min(b, 62), n, dtype=np.uint64) if b else np.zeros(n, np.uint64)
+        if b > 62:
+            v = v * (1 << (b - 62)) + rng.integers(0, 1 << (b - 62), n, dtype=np.uint64)
+        v[0], v[-1] = 0, span
+        parts.append((np.uint64(lo & ((1 << 64) - 1)) + v).view(np.int64).astype(dtype) if top == 64 else
+                     (v.astype(np.int64) + lo).astype(dtype))
+    for b, x in enumerate(parts):
+        h = compress(x, zf.ZF_FOR_BP, 1024 * (1 + b % 3))
+        try:
+            from oracle_pins import chunks_of
+            assert chunks_of(oracle.default(), zf.zf_compressed_bytes(h))[0][4]["bw"] == b
+            for resident in (False, True):
+                got, = gpu.decode([h], out_specs(x), resident=resident)
+                assert np.array_equal(got, x), (b, resident)
+        finally:
+            zf.zf_compressed_free(h)
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+def test_dict_every_code_width(gpu, dtype):
+    """Dictionary + bit-packing with 2^(b-1) + 1 distinct values, so the
+    codes are b = 1..16 bits wide, on ragged chunks, against the column."""
+    rng = np.random.default_rng(62)
+    for b in range(1, 17):
+        nd = (1 << (b - 1)) + 1
+        vals = rng.integers(-(1 << 31), 1 << 31, nd).astype(dtype) * (3 if dtype == np.int64 else 1)
+        vals = np.unique(vals)
+        x = vals[np.concatenate([np.arange(len(vals)), rng.integers(0, len(vals), 5000 + 41 * b)])]
+        h = compress(x, zf.ZF_DICT_BP, 1 << 20)
+        try:
+            got, = gpu.decode([h], out_specs(x))
+            assert np.array_equal(got, x), b
+        finally:
+            zf.zf_compressed_free(h)
+
+
 @pytest.mark.parametrize("scheme", ["raw", "for_bp", "dict_bp", "delta_bp", "rle"])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: c[0])
 def test_decode_equals_oracle(gpu, scheme, case):
@@ -137,6 +186,39 @@ def test_strdict_strings(gpu):
     finally:
         zf.zf_compressed_free(h)
         g.close()
+
+
+def test_strdict_dictionary_too_large_for_shared_memory(gpu):
+    """The string-dictionary launch keeps a chunk's dictionary in shared
+    memory when it fits (about 160 KB): a chunk of 30,000 distinct 12-byte
+    words (a dictionary of about 500 KB) takes the global-memory path, and a
+    column mixing such chunks with small-dictionary chunks decodes exactly on
+    the transfer, resident and batched paths."""
+    rng = np.random.default_rng(44)
+    letters = rng.integers(97, 123, (30000, 11)).astype(np.uint8)
+    words = np.concatenate([letters, np.full((30000, 1), 32, np.uint8)], 1)   # 12-byte tokens "xxxxxxxxxxx "
+    big = words[rng.permutation(30000)].reshape(-1)[: 1 << 20]                 # 1 MiB: every word about once
+    small, so = W.text_column(10, 1 << 20)
+    t = np.concatenate([big, small])
+    o = np.concatenate([np.arange(0, big.size, 120, dtype=np.int64), big.size + so.astype(np.int64)]).astype(np.int32)
+    o = np.unique(o)
+    col = zf.Column(t, o)
+    h = zf.zf_compress_host(zf.zf_plan(None, col, scheme=zf.ZF_STRDICT, chunk_rows=1 << 20), col)
+    try:
+        from oracle_pins import chunks_of
+        chs = chunks_of(oracle.default(), zf.zf_compressed_bytes(h))
+        assert chs[0][4]["n_aux"] > 20000 and chs[-1][4]["n_aux"] < 20000
+        for resident in (False, True):
+            got_t, got_o = gpu.decode([h], out_specs(t, o), resident=resident)
+            assert np.array_equal(got_t, t) and np.array_equal(got_o, o), resident
+        g = Gpu(flags=zf.ZF_KCFG_BATCHED)
+        try:
+            got_t, got_o = g.decode([h], out_specs(t, o))
+            assert np.array_equal(got_t, t) and np.array_equal(got_o, o)
+        finally:
+            g.close()
+    finally:
+        zf.zf_compressed_free(h)
 
 
 def test_strdict_device_detects_corrupt_streams(gpu):

@@ -133,3 +133,26 @@ def test_measured_rates_for_johnsons_rule(columns):
                 assert np.array_equal(y, cols[i][0]), (flags, order)
     finally:
         g.close()
+
+
+def test_tune_chunk_rows_times_every_candidate(columns):
+    """The chunk-size dimension of the search: every candidate chunk size is
+    encoded and timed through the transfer, one that does not fit (not a
+    multiple of 1024 rows) gets -1, the fastest is reported, and the column
+    encoded at that size decodes exactly."""
+    cols, hs = columns
+    (x, s, cr) = cols[1]                                   # the RLE dates
+    g = Gpu()
+    try:
+        cand = [65536, 262144, 1000, 1 << 20]
+        ms, best = zf.zf_tune_chunk_rows(g.ctx, zf.Column(x), s, cand, reps=2)
+        assert ms[2] == -1.0 and all(ms[i] > 0 for i in (0, 1, 3))
+        assert best in (0, 1, 3) and ms[best] == min(ms[i] for i in (0, 1, 3))
+        h = compress(x, s, cand[best])
+        try:
+            got, = g.decode([h], out_specs(x))
+            assert np.array_equal(got, x)
+        finally:
+            zf.zf_compressed_free(h)
+    finally:
+        g.close()
