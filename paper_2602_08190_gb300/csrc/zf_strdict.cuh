@@ -19,10 +19,13 @@ namespace zfd {
 // Destination word j holds source bytes a0 - (w0 mod 4) + 4j .. + 3: one
 // funnel shift of two consecutive source words, read as whole words, four
 // destination words per step.  Source words before the entry start are
-// inside the chunk (the section starts at byte 64 or later) and those past
-// the section's end are clamped to its last word: both only feed bytes the
-// masks drop.  Every word is merged with an atomic OR, so entries that share
-// a word need no ordering.
+// inside the chunk (the section starts at byte 64 or later).  Words past the
+// section's end only feed bytes the masks drop: with SAFE the chunk holds at
+// least 32 bytes after the section (every word read ends within 20 bytes of
+// it) and they are read as they are, otherwise they are clamped to the last
+// word.  Every word is merged with an atomic OR, so entries that share a
+// word need no ordering.
+template <bool SAFE>
 __device__ __forceinline__ void strdict_copy(uint32_t* win, const uint32_t* dw, int last_w, uint32_t a0, uint32_t len,
                                              uint32_t w0) {
     if (len == 0) return;
@@ -36,42 +39,46 @@ __device__ __forceinline__ void strdict_copy(uint32_t* win, const uint32_t* dw, 
     for (uint32_t j0 = 0; j0 < nw; j0 += 4) {
         uint32_t s[5];
 #pragma unroll
-        for (int k = 0; k < 5; k++) s[k] = __ldg(dw + min(ws + (int)j0 + k, last_w));
+        for (int k = 0; k < 5; k++) {
+            const int w = ws + (int)j0 + k;
+            s[k] = __ldg(dw + (SAFE ? w : min(w, last_w)));
+        }
 #pragma unroll
         for (uint32_t jj = 0; jj < 4; jj++) {
             const uint32_t j = j0 + jj;
             if (j < nw) {
-                const uint32_t m = (j == 0 ? head_mask : 0xFFFFFFFFu) & (j + 1 == nw ? tail_mask : 0xFFFFFFFFu);
+                uint32_t m = j + 1 == nw ? tail_mask : 0xFFFFFFFFu;
+                if (j == 0) m &= head_mask;
                 atomicOr(&win[q0 + j], __funnelshift_r(s[jj], s[jj + 1], sh) & m);
             }
         }
     }
 }
 
-// Tokens [r0, r0 + nrows) of the chunk (r0 a multiple of 1024; the chunk may
-// end sooner).  Per tile the codes are staged in shared memory; 32 tokens at
-// a time, lane i takes token t0 + i: its entry's offset and length from the
-// dictionary offsets, one warp scan places the 32 entries, each lane ORs its
-// entry into a zeroed shared-memory window (strdict_copy) and the warp writes
-// the window's whole 16-byte blocks out, zeroing them as they leave.  The
-// window's byte 0 is the output byte at a 16-byte boundary, so every store is
-// a 16-byte vector; the last, partial block carries over to the next 32
-// tokens.  Only the job's first block (whose leading bytes belong to the
-// tokens before the job) and its last partial block leave as single bytes.
-// Codes past the dictionary, entries that are empty, longer than 64 bytes or
-// leave the dictionary, and tiles whose lengths do not reach the next tile's
-// start are reported.
-__device__ inline void strdict_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t nrows, uint32_t* wsm,
-                                   uint32_t* err) {
+// Tokens [r0, r0 + ntok) of the chunk (r0 a multiple of 1024).  Per tile the
+// codes are staged in shared memory; 64 tokens at a time, lane i takes
+// tokens t0 + 2i and t0 + 2i + 1 (both codes from one extraction): their
+// entries' offsets and lengths from the dictionary offsets, one warp scan of
+// the lanes' two-token sums places the 64 entries, each lane ORs its entries
+// into a zeroed shared-memory window (strdict_copy) and the warp writes the
+// window's whole 16-byte blocks out, zeroing them as they leave.  The window
+// holds 32 tokens of the 64-byte maximum (a batch that needs more goes
+// through it in two rounds of 32 tokens), so it stays small and the SM's L1
+// keeps room for the dictionary.  The next 64 tokens' entries are loaded
+// before the current ones are copied.  The window's byte 0 is the output byte
+// at a 16-byte boundary, so every store is a 16-byte vector; the last,
+// partial block carries over to the next batch.
+// Only the job's first block (whose leading bytes belong to the tokens before
+// the job) and its last partial block leave as single bytes.  Codes past the
+// dictionary, entries that are empty, longer than 64 bytes or leave the
+// dictionary, and tiles whose lengths do not reach the next tile's start are
+// reported.
+template <bool SAFE>
+__device__ __forceinline__ void strdict_tokens(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t ntok,
+                                               uint32_t* wsm, uint32_t* err) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t nd = h.n_aux, b = h.b;
     const uint64_t T = h.ref;
-    if (nd == 0 || nd > zf::kStrDictMax || b > 16 || T > h.rows || r0 >= T ||
-        (uint64_t)h.len[0] < 4ull * (nd + 1 + (T + zf::kStrTile - 1) / zf::kStrTile) || h.len[1] == 0) {
-        if (lane == 0) report(err, ZF_ECORRUPT, c.chunk_id);
-        return;
-    }
-    const uint32_t ntok = (uint32_t)min((unsigned long long)nrows, (unsigned long long)(T - r0));
     const uint32_t ntiles = (uint32_t)((T + zf::kStrTile - 1) / zf::kStrTile);
     const uint32_t* doff = reinterpret_cast<const uint32_t*>(c.blob + h.off[0]);
     const uint32_t* tstart = doff + nd + 1;
@@ -79,6 +86,7 @@ __device__ inline void strdict_job(const ZfDevChunk& c, const Hdr& h, uint32_t r
     const uint8_t* codes = c.blob + h.off[2];
     const uint32_t dlen = h.len[1];
     const int last_w = (int)((dlen - 1) >> 2);
+    const uint32_t cmask = (1u << b) - 1u;                 // b <= 16
     uint32_t* cbuf = wsm;
     uint32_t* win = wsm + kStrCodeBuf / 4;
     const uint8_t* winb = reinterpret_cast<const uint8_t*>(win);
@@ -100,61 +108,81 @@ __device__ inline void strdict_job(const ZfDevChunk& c, const Hdr& h, uint32_t r
         bad = o0 != op || o0 > o1 || o1 > h.rows;
         __pipeline_wait_prior(0);
         __syncwarp();
-        // entry (offset, end) of token k of the staged tile; the next 32 tokens'
-        // loads are issued before the current 32 are copied
-        auto entry = [&](uint32_t k, uint32_t& a0, uint32_t& a1, bool& cbad) {
-            a0 = a1 = 0;
+        // entries [a0, e0) and [a1, e1) of tokens k and k + 1 of the staged tile
+        auto entry2 = [&](uint32_t k, uint32_t& a0, uint32_t& e0, uint32_t& a1, uint32_t& e1, bool& cbad) {
+            a0 = e0 = a1 = e1 = 0;
             cbad = false;
             if (k < nt) {
-                const uint32_t code = b ? (uint32_t)extract(cbuf, k * b, b) : 0u;
-                cbad = code >= nd;
+                const uint32_t pair = b ? (uint32_t)extract(cbuf, k * b, 2 * b) : 0u;
+                const uint32_t c0 = pair & cmask, c1 = pair >> b;
+                const bool two = k + 1 < nt;
+                cbad = c0 >= nd || (two && c1 >= nd);
                 if (!cbad) {
-                    a0 = __ldg(doff + code);
-                    a1 = __ldg(doff + code + 1);
+                    a0 = __ldg(doff + c0);
+                    e0 = __ldg(doff + c0 + 1);
+                    if (two) {
+                        a1 = __ldg(doff + c1);
+                        e1 = __ldg(doff + c1 + 1);
+                    }
                 }
             }
         };
-        uint32_t na0, na1;
+        uint32_t na0, ne0, na1, ne1;
         bool ncbad;
-        entry(lane, na0, na1, ncbad);
-        for (uint32_t t = 0; t < nt && !bad; t += 32) {
-            const uint32_t a0 = na0, a1 = na1;
-            uint32_t len = a1 - a0;
-            const bool lbad = ncbad || (t + lane < nt && (len - 1u >= zf::kStrTokenMax || a1 > dlen));   // 1 <= len <= 64
-            if (lbad) len = 0;
-            entry(t + 32 + lane, na0, na1, ncbad);
-            const uint32_t incl = warp_incl_sum<uint32_t>(len, lane);
-            const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31), start = incl - len;
+        entry2(2 * lane, na0, ne0, na1, ne1, ncbad);
+        for (uint32_t t = 0; t < nt && !bad; t += 64) {
+            const uint32_t a0 = na0, a1 = na1, k = t + 2 * lane;
+            uint32_t len0 = ne0 - na0, len1 = ne1 - na1;
+            // 1 <= len <= 64 and inside the dictionary, for every token of the tile
+            const bool lbad = ncbad || (k < nt && (len0 - 1u >= zf::kStrTokenMax || ne0 > dlen)) ||
+                              (k + 1 < nt && (len1 - 1u >= zf::kStrTokenMax || ne1 > dlen));
+            if (lbad) len0 = len1 = 0;
+            entry2(k + 64, na0, ne0, na1, ne1, ncbad);
+            const uint32_t s2 = len0 + len1;
+            const uint32_t incl = warp_incl_sum<uint32_t>(s2, lane);
+            const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31), start = incl - s2;
             if (__any_sync(0xFFFFFFFFu, lbad) || total > o1 - op) {
                 bad = true;
                 break;
             }
-            strdict_copy(win, dw, last_w, a0, len, a + start);
-            __syncwarp();
-            // whole blocks out (zeroed behind), block 0 keeping its leading bytes that are not this job's
-            const uint32_t e = a + total, x1 = e & ~15u;
-            if (x1) {
-                if (head) {
-                    if (lane >= head && lane < 16) base[lane] = winb[lane];
+            // the batch's bytes go through the window in one round, or, when they
+            // would not fit (more than 32 tokens' worth of the 64-byte maximum), in
+            // two: tokens t..t+31 (lanes 0-15), then t+32..t+63 (lanes 16-31)
+            const uint32_t totA = __shfl_sync(0xFFFFFFFFu, incl, 15);
+            const uint32_t rounds = a + total + 16u > kStrWin ? 2u : 1u;
+            for (uint32_t r = 0; r < rounds; r++) {
+                const uint32_t before = rounds == 2 && r == 1 ? totA : 0u;   // batch bytes of earlier rounds
+                const uint32_t rtot = rounds == 1 ? total : (r == 0 ? totA : total - totA);
+                if (rounds == 1 || (lane >> 4) == r) {
+                    strdict_copy<SAFE>(win, dw, last_w, a0, len0, a + start - before);
+                    strdict_copy<SAFE>(win, dw, last_w, a1, len1, a + start - before + len0);
+                }
+                __syncwarp();
+                // whole blocks out (zeroed behind), block 0 keeping its leading bytes that are not this job's
+                const uint32_t e = a + rtot, x1 = e & ~15u;
+                if (x1) {
+                    if (head) {
+                        if (lane >= head && lane < 16) base[lane] = winb[lane];
+                        __syncwarp();
+                        if (lane < 4) win[lane] = 0;
+                    }
+                    uint4* wv = reinterpret_cast<uint4*>(win);
+                    for (uint32_t q = (head ? 1u : 0u) + lane; q < (x1 >> 4); q += 32) {
+                        reinterpret_cast<uint4*>(base)[q] = wv[q];
+                        wv[q] = make_uint4(0, 0, 0, 0);
+                    }
+                    head = 0;
                     __syncwarp();
-                    if (lane < 4) win[lane] = 0;
+                    // the partial block [x1, e) becomes block 0 (its old place is zeroed)
+                    if (x1 < e && lane < 4) {
+                        win[lane] = win[(x1 >> 2) + lane];
+                        win[(x1 >> 2) + lane] = 0;
+                    }
+                    __syncwarp();
                 }
-                uint4* wv = reinterpret_cast<uint4*>(win);
-                for (uint32_t q = (head ? 1u : 0u) + lane; q < (x1 >> 4); q += 32) {
-                    reinterpret_cast<uint4*>(base)[q] = wv[q];
-                    wv[q] = make_uint4(0, 0, 0, 0);
-                }
-                head = 0;
-                __syncwarp();
-                // the partial block [x1, e) becomes block 0 (its old place is zeroed)
-                if (x1 < e && lane < 4) {
-                    win[lane] = win[(x1 >> 2) + lane];
-                    win[(x1 >> 2) + lane] = 0;
-                }
-                __syncwarp();
+                base += x1;
+                a = e - x1;
             }
-            base += x1;
-            a = e - x1;
             op += total;
         }
         bad = bad || op != o1;
@@ -162,6 +190,20 @@ __device__ inline void strdict_job(const ZfDevChunk& c, const Hdr& h, uint32_t r
     // the job's last partial block, byte by byte
     if (!bad && lane >= head && lane < a) base[lane] = winb[lane];
     if (bad && lane == 0) report(err, ZF_ECORRUPT, c.chunk_id);
+}
+
+__device__ inline void strdict_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t nrows, uint32_t* wsm,
+                                   uint32_t* err) {
+    const uint32_t nd = h.n_aux, b = h.b;
+    const uint64_t T = h.ref;
+    if (nd == 0 || nd > zf::kStrDictMax || b > 16 || T > h.rows || r0 >= T ||
+        (uint64_t)h.len[0] < 4ull * (nd + 1 + (T + zf::kStrTile - 1) / zf::kStrTile) || h.len[1] == 0) {
+        if ((threadIdx.x & 31) == 0) report(err, ZF_ECORRUPT, c.chunk_id);
+        return;
+    }
+    const uint32_t ntok = (uint32_t)min((unsigned long long)nrows, (unsigned long long)(T - r0));
+    if ((uint64_t)h.off[1] + h.len[1] + 32u <= c.blob_bytes) strdict_tokens<true>(c, h, r0, ntok, wsm, err);
+    else strdict_tokens<false>(c, h, r0, ntok, wsm, err);
 }
 
 }  // namespace zfd

@@ -160,8 +160,15 @@ def test_strdict_strings(gpu):
     resident and batched paths."""
     rng = np.random.default_rng(12)
     raw = rng.integers(0, 256, 150000).astype(np.uint8)
+    # 64-byte tokens (63 letters and a space) between short ones: batches of 64
+    # tokens whose bytes pass the 2,080-byte output window
+    lw = rng.integers(97, 123, (3000, 64)).astype(np.uint8)
+    lw[:, 63] = 32
+    lw[::7, 3] = 32                                   # every seventh word cut short
+    longs = lw.reshape(-1)
     cases = [(W.text_column(7, 1000003), 1 << 20), (W.text_column(8, 300001), 65536),
              ((raw, np.array([0, 70000, 70000, 150000], np.int32)), 131072),
+             ((longs, np.array([0, 5, 64 * 1000 + 1, longs.size], np.int32)), 65536),
              ((np.frombuffer(b"xyz", np.uint8).copy(), np.array([0, 3], np.int32)), 65536)]
     for (t, o), cb in cases:
         for enc in ("library", "oracle"):
@@ -188,12 +195,10 @@ def test_strdict_strings(gpu):
         g.close()
 
 
-def test_strdict_dictionary_too_large_for_shared_memory(gpu):
-    """The string-dictionary launch keeps a chunk's dictionary in shared
-    memory when it fits (about 160 KB): a chunk of 30,000 distinct 12-byte
-    words (a dictionary of about 500 KB) takes the global-memory path, and a
-    column mixing such chunks with small-dictionary chunks decodes exactly on
-    the transfer, resident and batched paths."""
+def test_strdict_dictionary_larger_than_l1(gpu):
+    """A chunk of 30,000 distinct 12-byte words (a dictionary of about
+    500 KB, far more than an SM's L1) in a column with small-dictionary
+    chunks decodes exactly on the transfer, resident and batched paths."""
     rng = np.random.default_rng(44)
     letters = rng.integers(97, 123, (30000, 11)).astype(np.uint8)
     words = np.concatenate([letters, np.full((30000, 1), 32, np.uint8)], 1)   # 12-byte tokens "xxxxxxxxxxx "
