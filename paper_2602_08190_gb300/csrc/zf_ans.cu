@@ -33,6 +33,10 @@ struct AnsSmem {
 // word holding a byte of the stream lies inside the blob).  Per row: the
 // slot entry of x mod M gives the value and x = f (x >> 12) + (slot - c);
 // then zero, one or two bytes enter while x < L (after a step x >= 2^11).
+// One refill per row keeps enough bytes buffered: a refill runs when 0 or 8
+// bits are left and adds at least one byte, and 0 bits are left only after
+// a row that took two bytes from 16 -- which leaves x >= 2^27, so the next
+// step gives x >= 2^15 and takes at most one byte.
 // Eight int32 or four int64 rows leave as one 32-byte sector.  Returns true
 // if the stream is malformed: it must use exactly its bytes and end at x = L.
 template <class T>

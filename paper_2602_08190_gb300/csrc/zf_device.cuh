@@ -818,7 +818,7 @@ __device__ void rle_job(const ZfDevChunk& c, const Hdr& h, uint32_t r0, uint32_t
 // ---------------------------------------------------------------- string dictionary sizes
 // (the decoder is in zf_strdict.cuh)
 constexpr uint32_t kStrCodeBuf = (1024u * 16u / 8u) + 32u;   // one tile of codes at b <= 16, plus the reader's overrun
-constexpr uint32_t kStrWin = 32u * zf::kStrTokenMax + 32u;    // 32 tokens of at most 64 bytes, at the output's alignment
+constexpr uint32_t kStrWin = 16u * zf::kStrTokenMax + 32u;    // 16 tokens of at most 64 bytes, at the output's alignment
 
 // ---------------------------------------------------------------- single-tile entry points
 // (used by the allocation-free kernel; 16-byte stores only)

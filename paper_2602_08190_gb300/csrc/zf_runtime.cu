@@ -363,7 +363,10 @@ void johnson_order(const zf_ctx* ctx, std::vector<Work>& work) {
 // Stages and copy pieces of a transfer.  Stages: consecutive chunks up to
 // stage_bytes of compressed bytes, cut from the end so that the last stages
 // are small (1/8, 1/4, 1/2 of stage_bytes): the decode left after the last
-// copy is short.  Copy plan: runs of chunks contiguous in one host buffer
+// copy is short.  (Cutting the first stages the same way measured slower:
+// while decode outruns the link the copy engine is busy from the start
+// anyway, and small copies run below the link rate.)  Copy plan: runs of
+// chunks contiguous in one host buffer
 // become one copy, started at a 128-byte aligned host address (on GB300 an
 // H2D copy from an address that is not runs about 15% slower): up to 112
 // bytes before the run (never before its buffer) come along, and the run

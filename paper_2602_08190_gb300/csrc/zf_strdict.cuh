@@ -62,9 +62,9 @@ __device__ __forceinline__ void strdict_copy(uint32_t* win, const uint32_t* dw, 
 // the lanes' two-token sums places the 64 entries, each lane ORs its entries
 // into a zeroed shared-memory window (strdict_copy) and the warp writes the
 // window's whole 16-byte blocks out, zeroing them as they leave.  The window
-// holds 32 tokens of the 64-byte maximum (a batch that needs more goes
-// through it in two rounds of 32 tokens), so it stays small and the SM's L1
-// keeps room for the dictionary.  The next 64 tokens' entries are loaded
+// holds 16 tokens of the 64-byte maximum (a batch that needs more goes
+// through it in two or four rounds), so it stays small and the SM's L1 keeps
+// room for the dictionary.  The next 64 tokens' entries are loaded
 // before the current ones are copied.  The window's byte 0 is the output byte
 // at a 16-byte boundary, so every store is a 16-byte vector; the last,
 // partial block carries over to the next batch.
@@ -146,14 +146,17 @@ __device__ __forceinline__ void strdict_tokens(const ZfDevChunk& c, const Hdr& h
                 break;
             }
             // the batch's bytes go through the window in one round, or, when they
-            // would not fit (more than 32 tokens' worth of the 64-byte maximum), in
-            // two: tokens t..t+31 (lanes 0-15), then t+32..t+63 (lanes 16-31)
-            const uint32_t totA = __shfl_sync(0xFFFFFFFFu, incl, 15);
-            const uint32_t rounds = a + total + 16u > kStrWin ? 2u : 1u;
-            for (uint32_t r = 0; r < rounds; r++) {
-                const uint32_t before = rounds == 2 && r == 1 ? totA : 0u;   // batch bytes of earlier rounds
-                const uint32_t rtot = rounds == 1 ? total : (r == 0 ? totA : total - totA);
-                if (rounds == 1 || (lane >> 4) == r) {
+            // would not fit, in two or four rounds of consecutive lanes (a round
+            // of eight lanes, 16 tokens of at most 64 bytes, always fits)
+            const uint32_t half = __shfl_sync(0xFFFFFFFFu, incl, 15);
+            const uint32_t R = a + total + 16u <= kStrWin ? 1u
+                               : max(half, total - half) + 31u <= kStrWin ? 2u : 4u;
+            const uint32_t per = 32u / R;                            // lanes per round
+            for (uint32_t r = 0; r < R; r++) {
+                const uint32_t l0 = r * per;
+                const uint32_t before = l0 ? __shfl_sync(0xFFFFFFFFu, incl, l0 - 1) : 0u;   // batch bytes of earlier rounds
+                const uint32_t rtot = __shfl_sync(0xFFFFFFFFu, incl, l0 + per - 1) - before;
+                if (lane - l0 < per) {
                     strdict_copy<SAFE>(win, dw, last_w, a0, len0, a + start - before);
                     strdict_copy<SAFE>(win, dw, last_w, a1, len1, a + start - before + len0);
                 }

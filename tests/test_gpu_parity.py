@@ -161,14 +161,19 @@ def test_strdict_strings(gpu):
     rng = np.random.default_rng(12)
     raw = rng.integers(0, 256, 150000).astype(np.uint8)
     # 64-byte tokens (63 letters and a space) between short ones: batches of 64
-    # tokens whose bytes pass the 2,080-byte output window
+    # tokens that go through the output window in four rounds
     lw = rng.integers(97, 123, (3000, 64)).astype(np.uint8)
     lw[:, 63] = 32
     lw[::7, 3] = 32                                   # every seventh word cut short
     longs = lw.reshape(-1)
+    # words of 12-40 bytes: 64-token batches of 1-2.5 KB (two rounds through the window)
+    wl = rng.integers(12, 41, 6000)
+    mids = rng.integers(97, 123, int(wl.sum())).astype(np.uint8)
+    mids[np.cumsum(wl) - 1] = 32
     cases = [(W.text_column(7, 1000003), 1 << 20), (W.text_column(8, 300001), 65536),
              ((raw, np.array([0, 70000, 70000, 150000], np.int32)), 131072),
              ((longs, np.array([0, 5, 64 * 1000 + 1, longs.size], np.int32)), 65536),
+             ((mids, np.array([0, mids.size], np.int32)), 65536),
              ((np.frombuffer(b"xyz", np.uint8).copy(), np.array([0, 3], np.int32)), 65536)]
     for (t, o), cb in cases:
         for enc in ("library", "oracle"):
