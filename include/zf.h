@@ -147,8 +147,9 @@ typedef struct {
     uint32_t threads;         /* 128, 256 or 512 (0 = the class's tuned value, else 128) */
     uint32_t ctas_per_sm;     /* batched launch: persistent grid = ctas_per_sm x SM count (0 = occupancy limit) */
     uint32_t stage_bytes;     /* pipeline stage: compressed bytes per H2D copy + decode step (default 64 MiB) */
-    uint32_t flags;           /* ZF_KCFG_BATCHED: one work-queue launch per stage for all schemes
-                                 (else one launch per (scheme, dtype) group);
+    uint32_t flags;           /* ZF_KCFG_BATCHED: one work-queue launch per stage for the chunks of
+                                 every Fully- and Group-Parallel scheme (LZ77 and ANS chunks keep
+                                 their own kernels); else one launch per (scheme, dtype) group;
                                  ZF_KCFG_GRAPH: capture repeated transfers in a CUDA graph;
                                  ZF_KCFG_KEEP_ORDER: copy columns in the order given */
 } zf_kcfg;
