@@ -28,78 +28,89 @@ struct AnsSmem {
 };
 
 // Stream k of the chunk, rows [k L, k L + n), decoded by one lane.  The
-// stream's bytes [a0, a1) of s2 come through a 64-bit buffer refilled with
-// aligned 8-byte loads (s2 starts on a 16-byte boundary of the blob, so a
-// word holding a byte of the stream lies inside the blob).  Per row: the
-// slot entry of x mod M gives the value and x = f (x >> 12) + (slot - c);
-// then zero, one or two bytes enter while x < L (after a step x >= 2^11).
-// One refill per row keeps enough bytes buffered: a refill runs when 0 or 8
-// bits are left and adds at least one byte, and 0 bits are left only after
-// a row that took two bytes from 16 -- which leaves x >= 2^27, so the next
-// step gives x >= 2^15 and takes at most one byte.
+// stream's bytes [a0, a1) of s2 come through a 64-bit buffer, next byte in
+// the top bits.  Per row: the slot entry of x mod M gives the value and
+// x = f (x >> 12) + (slot - c); then zero, one or two bytes enter while
+// x < L (after a step x >= 2^11): one funnel shift of x over the buffer's
+// top word, and the buffer moves up by as many bytes.  A row takes at most
+// two bytes, so the buffer is topped up to 64 bits before every four rows,
+// by every lane at once (no lane waits on another's refill): two aligned
+// 8-byte loads from the word holding the next byte (words past the stream's
+// last one read as zero; s2 starts on a 16-byte boundary of the blob, so a
+// word holding a stream byte lies inside the blob).  Bytes past the stream
+// may enter the buffer; a valid stream never takes them.
 // Eight int32 or four int64 rows leave as one 32-byte sector.  Returns true
 // if the stream is malformed: it must use exactly its bytes and end at x = L.
 template <class T>
 __device__ __forceinline__ bool ans_stream(const AnsSmem& sm, const uint8_t* s2, uint32_t a0, uint32_t a1, T* dst,
                                            uint32_t n) {
     const unsigned long long* w8 = reinterpret_cast<const unsigned long long*>(s2);
-    uint32_t pos = a0;                 // next stream byte to enter the buffer
-    unsigned long long bb = 0;         // buffered bytes, the next one lowest
-    uint32_t nbits = 0;                // buffered bits (a multiple of 8, <= 64)
-    auto refill = [&]() {
-        if (pos < a1) {
-            const unsigned long long w = __ldg(w8 + (pos >> 3));
-            const uint32_t sh = pos & 7u, avail = min(8u - sh, (64u - nbits) >> 3);
-            const unsigned long long got = avail == 8 ? w : (w >> (8 * sh)) & ((1ull << (8 * avail)) - 1);
-            bb |= got << nbits;
-            nbits += 8 * avail;
-            pos += avail;
-        }
+    const uint32_t lastw = (a1 - 1) >> 3;   // the last word holding a stream byte (a1 > a0)
+    uint32_t pos = a0;                      // next stream byte to enter the buffer
+    unsigned long long bb = 0;              // buffered bytes, the next one in bits 63..56
+    uint32_t nbits = 0;                     // buffered bits, a multiple of 8 in [0, 64]
+    auto topup = [&]() {
+        const uint32_t need = (64u - nbits) >> 3;
+        const uint32_t wi = pos >> 3, s = 8u * (pos & 7u);
+        const unsigned long long w0 = wi <= lastw ? __ldg(w8 + wi) : 0ull;
+        const unsigned long long w1 = wi + 1 <= lastw ? __ldg(w8 + wi + 1) : 0ull;
+        // the 8 bytes from pos, little-endian: (w1:w0) >> s
+        const bool lo = s < 32;
+        const uint32_t q0 = lo ? (uint32_t)w0 : (uint32_t)(w0 >> 32), q1 = lo ? (uint32_t)(w0 >> 32) : (uint32_t)w1,
+                       q2 = lo ? (uint32_t)w1 : (uint32_t)(w1 >> 32);
+        const uint32_t r0 = __funnelshift_r(q0, q1, s & 31u), r1 = __funnelshift_r(q1, q2, s & 31u);
+        // in stream order from the top, the first `need` of them
+        unsigned long long r = ((unsigned long long)__byte_perm(r0, 0, 0x0123) << 32) | __byte_perm(r1, 0, 0x0123);
+        r = need ? r & (~0ull << (64u - 8u * need)) : 0ull;
+        bb |= nbits < 64 ? r >> nbits : 0ull;
+        nbits += 8u * need;
+        pos += need;
     };
-    refill();
-    if (nbits < 32) refill();
-    uint32_t x = (uint32_t)bb;         // the state: bytes a0 .. a0 + 3, little-endian
-    bb >>= 32;
+    topup();
+    // the state: bytes a0 .. a0 + 3, little-endian
+    uint32_t x = __byte_perm((uint32_t)(bb >> 32), 0, 0x0123);
+    bb <<= 32;
     nbits -= 32;
-    uint32_t used = 4;                 // stream bytes consumed
+    const uint32_t* val32 = reinterpret_cast<const uint32_t*>(sm.val);
+    auto step = [&]() -> T {
+        const uint32_t t = sm.slot[x & (zf::kAnsM - 1u)];
+        T v;
+        if constexpr (sizeof(T) == 4) v = (T)val32[2 * (t >> 24)];   // the low word of the 64-bit pattern
+        else v = (T)sm.val[t >> 24];
+        x = ((t & 0xFFFu) + 1u) * (x >> zf::kAnsScale) + ((t >> 12) & 0xFFFu);
+        const uint32_t s = (x < zf::kAnsL ? 8u : 0u) + (x < (zf::kAnsL >> 8) ? 8u : 0u);
+        x = __funnelshift_l((uint32_t)(bb >> 32), x, s);
+        bb <<= s;
+        nbits -= s;
+        return v;
+    };
     constexpr uint32_t V = 32 / sizeof(T);
     const bool al32 = (reinterpret_cast<uintptr_t>(dst) & 31) == 0;
-    for (uint32_t i0 = 0; i0 < n; i0 += V) {
+    uint32_t i0 = 0;
+    for (; i0 + V <= n; i0 += V) {
         T v[V];
 #pragma unroll
         for (uint32_t e = 0; e < V; e++) {
-            v[e] = T(0);
-            if (i0 + e < n) {
-                if (nbits < 16) refill();
-                const uint32_t t = sm.slot[x & (zf::kAnsM - 1u)];
-                v[e] = (T)sm.val[t >> 24];
-                x = ((t & 0xFFFu) + 1u) * (x >> zf::kAnsScale) + ((t >> 12) & 0xFFFu);
-                const uint32_t k = (x < zf::kAnsL ? 1u : 0u) + (x < (zf::kAnsL >> 8) ? 1u : 0u);
-                const uint32_t lo = (uint32_t)bb;
-                x = k == 2 ? (x << 16) | __byte_perm(lo, 0, 0x4401) : k == 1 ? (x << 8) | (lo & 0xFFu) : x;
-                bb >>= 8 * k;
-                nbits = nbits >= 8 * k ? nbits - 8 * k : 0u;
-                used += k;
-            }
+            if (e % 4 == 0) topup();
+            v[e] = step();
         }
-        if (i0 + V <= n) {
-            if (al32) {
-                if constexpr (sizeof(T) == 4)
-                    zfd::store32(dst + i0, ((unsigned long long)(uint32_t)v[1] << 32) | (uint32_t)v[0],
-                                 ((unsigned long long)(uint32_t)v[3] << 32) | (uint32_t)v[2],
-                                 ((unsigned long long)(uint32_t)v[5] << 32) | (uint32_t)v[4],
-                                 ((unsigned long long)(uint32_t)v[7] << 32) | (uint32_t)v[6]);
-                else
-                    zfd::store32(dst + i0, (uint64_t)v[0], (uint64_t)v[1], (uint64_t)v[2], (uint64_t)v[3]);
-            } else {
-                zfd::store_vec<T, V>(dst + i0, v);
-            }
+        if (al32) {
+            if constexpr (sizeof(T) == 4)
+                zfd::store32(dst + i0, ((unsigned long long)(uint32_t)v[1] << 32) | (uint32_t)v[0],
+                             ((unsigned long long)(uint32_t)v[3] << 32) | (uint32_t)v[2],
+                             ((unsigned long long)(uint32_t)v[5] << 32) | (uint32_t)v[4],
+                             ((unsigned long long)(uint32_t)v[7] << 32) | (uint32_t)v[6]);
+            else
+                zfd::store32(dst + i0, (uint64_t)v[0], (uint64_t)v[1], (uint64_t)v[2], (uint64_t)v[3]);
         } else {
-#pragma unroll
-            for (uint32_t e = 0; e < V; e++)
-                if (i0 + e < n) dst[i0 + e] = v[e];
+            zfd::store_vec<T, V>(dst + i0, v);
         }
     }
+    for (uint32_t e = 0; i0 < n; i0++, e++) {
+        if (e % 4 == 0) topup();
+        dst[i0] = step();
+    }
+    const uint32_t used = (pos - a0) - nbits / 8;   // bytes the rows took
     return used != a1 - a0 || x != zf::kAnsL;
 }
 
