@@ -6,9 +6,10 @@ rows (2 int32 uniform 1-50 in FOR, 7 int64 log-normal cents in FOR, 2 int64
 sorted keys in delta, 3 int32 RLE dates, 2 int32 25-value Zipf codes in
 dictionary; 100 B/row, 40 GB), cut into 1,771 uneven pieces of 4-64 MB
 uncompressed, each piece a pinned single-chunk compressed column, all decoded
-by the persistent work-queue kernel (one launch per 64 MiB stage on the
-transfer path, one launch for everything when resident), replayed from a
-captured CUDA graph.
+by the persistent work-queue kernel (one launch per stage on the transfer
+path, one launch for everything when resident).  Each configuration's stage
+size, and whether the transfer is replayed from a captured CUDA graph or
+launched plainly, are chosen by timing the transfer on the host clock.
 
   value   uncompressed GB/s of the decode with the compressed pieces already
           resident in HBM (zf_decompress_resident), CUDA events on the
@@ -66,7 +67,7 @@ FACT_SCHEMES = {"uniform_1_50": "for_bp", "lognormal_cents": "for_bp", "sorted_k
 FACT_WORKLOAD = ("batched: 16-column fact table x {rows:,} rows (2 int32 uniform 1-50 FOR, 7 int64 log-normal "
                  "cents FOR, 2 int64 sorted keys delta, 3 int32 RLE dates, 2 int32 25-value Zipf codes dictionary; "
                  "100 B/row), {pieces} uneven pieces of 4-64 MB uncompressed in pinned memory, one persistent "
-                 "work-queue kernel per stage, CUDA graph")
+                 "work-queue kernel per stage")
 
 # Committed ncu summaries that give each roofline kernel's DRAM traffic per
 # launch; a figure is used only while the kernel sources hash as recorded.
@@ -393,7 +394,7 @@ def measure(zf, torch, cfg: Cfg, args, local: int, streams, flush, barrier=None,
     """Time one configuration: resident decode (CUDA events on the decode
     stream, L2 flushed before each step), its dominant launch alone, the end
     to end transfer (host wall clock around zf_transfer_decompress +
-    zf_sync, replayed from a CUDA graph) and the raw link at the call's own
+    zf_sync, graph replay on or off as the sweep chose) and the raw link at the call's own
     pieces (zf_measure_copy).  `clk` (a Clocks) records the timed loops as
     its sampling windows.  Returns (record, step times in ms, sizes) for the
     caller's reduction over ranks."""
@@ -441,18 +442,25 @@ def measure(zf, torch, cfg: Cfg, args, local: int, streams, flush, barrier=None,
             per_class.append((best.tile_rows, best.threads))
         stage_ms = {}
         for st_mb in [m for m in (2, 4, 8, 16, 32, 64, 128) if comp <= 1500 * (m << 20) or m == 128]:
-            zf.zf_ctx_set_kcfg(ctx, 0, 0, args.ctas_per_sm, st_mb << 20, flags)   # replayed from a graph, as timed
-            tt = []
-            for _ in range(1 + max(3, args.tune_reps)):
-                t0 = time.perf_counter()
-                zf.zf_transfer_decompress(ctx, cfg.handles, outs, caps)
-                st, stats = zf.zf_sync(ctx)
-                tt.append((time.perf_counter() - t0) * 1e3)   # host wall clock, as the e2e steps are timed
-            stage_ms[st_mb] = float(np.min(tt[1:]))   # the fastest repeat: host hiccups only ever add time
-        st_best = min(stage_ms, key=stage_ms.get)
+            # each stage size with and without graph replay: a replayed graph costs the host less,
+            # plain launches let the copies start while the host still enqueues
+            for graph in (True, False):
+                fl = flags if graph else flags & ~zf.ZF_KCFG_GRAPH
+                zf.zf_ctx_set_kcfg(ctx, 0, 0, args.ctas_per_sm, st_mb << 20, fl)
+                tt = []
+                for _ in range(1 + max(3, args.tune_reps)):
+                    t1 = time.perf_counter()
+                    zf.zf_transfer_decompress(ctx, cfg.handles, outs, caps)
+                    st, stats = zf.zf_sync(ctx)
+                    tt.append((time.perf_counter() - t1) * 1e3)   # host wall clock, as the e2e steps are timed
+                stage_ms[(st_mb, graph)] = float(np.min(tt[1:]))   # the fastest repeat: host hiccups only add time
+        st_best, graph_best = min(stage_ms, key=stage_ms.get)
+        if not graph_best:
+            flags &= ~zf.ZF_KCFG_GRAPH
         zf.zf_ctx_set_kcfg(ctx, 0, 0, args.ctas_per_sm, st_best << 20, flags)
         tuned = {"per_column_tile_rows_threads": sorted(set(per_class)), "stage_bytes": st_best << 20,
-                 "resident_points": npts, "stage_ms": {str(k): round(v, 4) for k, v in stage_ms.items()},
+                 "graph_replay": graph_best, "resident_points": npts,
+                 "stage_ms": {f"{k[0]}{'' if k[1] else ' no graph'}": round(v, 4) for k, v in stage_ms.items()},
                  "search_s": round(time.perf_counter() - t0, 2)}
         zf.zf_transfer_decompress(ctx, cfg.handles, outs, caps)
         zf.zf_sync(ctx)
@@ -513,7 +521,7 @@ def measure(zf, torch, cfg: Cfg, args, local: int, streams, flush, barrier=None,
         if clk:
             clk.window_end()
     gc.enable()
-    # the decode after timing is still exact (graph replays included)
+    # the decode after timing is still exact (graph replays included, when used)
     verify(cfg, bufs)
     link_ms = float(np.mean(link_acc))
     link_med = float(np.median(link_acc))
