@@ -289,7 +289,7 @@ zf_status zf_decompress_resident(zf_ctx* ctx, const zf_resident* const* cols, ui
 /* One measured point of the search: the geometry and its median time. */
 typedef struct {
     zf_kcfg kcfg;
-    float ms;                 /* median of `reps` runs: zf_stats.total_ms */
+    float ms;                 /* median of `reps` runs: zf_stats.total_ms (resident) or host wall clock (transfer) */
 } zf_tune_point;
 
 /* Exhaustive search of the kernel geometry for these columns, the
@@ -297,8 +297,10 @@ typedef struct {
  * {1024, 2048, 4096, 8192, 16384} (L = 1..16 tiles per warp job) x threads in
  * {128, 256, 512} (S) is run once to warm up and `reps` times (0 = 3); with
  * `transfer` != 0 the full transfer is timed and stage_bytes in
- * {4, 8, 16, 32, 64} MiB is searched too (75 points), otherwise the decode of
- * the columns uploaded to HBM (15 points).  C is fixed by the store width.
+ * {4, 8, 16, 32, 64} MiB and graph replay (ZF_KCFG_GRAPH off, then on) are
+ * searched too (150 points, each timed on the host clock around the call and
+ * zf_sync, as a caller sees it), otherwise the decode of the columns uploaded
+ * to HBM (15 points, timed by device events).  C is fixed by the store width.
  * Writes up to max_points points (every point is visited once, in that
  * order), sets *n_points to the number visited and stores the fastest
  * geometry in *best (nullable).  When all chunks of the columns are of one

@@ -258,12 +258,12 @@ def zf_decompress_device_noalloc(d_column: int, column_bytes: int, d_out: int, o
 def zf_tune(ctx: int, cols: list[int], outs: list[int], caps: list[int], transfer: bool = False,
             reps: int = 3) -> tuple[list[zf_tune_point], zf_kcfg]:
     c, o, k = _arrays(cols, outs, caps)
-    pts = (zf_tune_point * 128)()
+    pts = (zf_tune_point * 256)()
     n = _u32()
     best = zf_kcfg()
-    _check(_L.zf_tune(ctx, c, len(cols), o, k, 1 if transfer else 0, reps, pts, 128, ctypes.byref(n),
+    _check(_L.zf_tune(ctx, c, len(cols), o, k, 1 if transfer else 0, reps, pts, 256, ctypes.byref(n),
                       ctypes.byref(best)), "zf_tune", ctx)
-    return [pts[i] for i in range(min(n.value, 128))], best
+    return [pts[i] for i in range(min(n.value, 256))], best
 
 
 def zf_ctx_tuned_geometry(ctx: int, scheme: int, dtype: int, bmax: int) -> zf_kcfg:

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <atomic>
 #include <cstring>
 #include <mutex>
@@ -1203,27 +1204,34 @@ extern "C" zf_status zf_tune(zf_ctx* ctx, const zf_compressed* const* cols, uint
         }
     }
     const uint32_t nstage = transfer ? (uint32_t)(sizeof(kTuneStageMiB) / sizeof(kTuneStageMiB[0])) : 1;
+    const uint32_t ngraph = transfer ? 2u : 1u;
     uint32_t n = 0;
     float best_ms = 3.0e38f;
     zf_kcfg best_k = saved;
+    for (uint32_t gi = 0; gi < ngraph; gi++)
     for (uint32_t si = 0; si < nstage; si++)
         for (uint32_t tr : kTuneTileRows)
             for (uint32_t th : kTuneThreads) {
                 zf_kcfg k = saved;
                 k.tile_rows = tr;
                 k.threads = th;
-                k.flags = saved.flags & ~ZF_KCFG_GRAPH;
+                k.flags = (saved.flags & ~ZF_KCFG_GRAPH) | (gi ? ZF_KCFG_GRAPH : 0u);
                 k.stage_bytes = transfer ? (kTuneStageMiB[si] << 20) : (saved.stage_bytes ? saved.stage_bytes : 64u << 20);
                 ctx->kcfg = k;
                 std::vector<float> ms;
-                for (uint32_t rep = 0; rep < reps + 1; rep++) {   // first run warms up
+                for (uint32_t rep = 0; rep < reps + 1; rep++) {   // first run warms up (and captures a graph)
+                    const auto t0 = std::chrono::steady_clock::now();
                     zf_status s = transfer ? zf_transfer_decompress(ctx, cols, ncols, d_out, d_out_bytes)
                                            : zf_decompress_resident(ctx, res.data(), ncols, d_out, d_out_bytes);
                     if (s) return cleanup(s);
                     zf_stats stt;
                     s = zf_sync(ctx, &stt);
                     if (s) return cleanup(s);
-                    if (rep) ms.push_back(stt.total_ms);
+                    // a transfer is timed as its caller sees it, on the host clock around the call
+                    // and zf_sync (graph replay costs the host less but each stage more on the device);
+                    // a resident decode by the device events
+                    const float wall = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+                    if (rep) ms.push_back(transfer ? wall : stt.total_ms);
                 }
                 std::sort(ms.begin(), ms.end());
                 const float med = ms[ms.size() / 2];
@@ -1234,7 +1242,7 @@ extern "C" zf_status zf_tune(zf_ctx* ctx, const zf_compressed* const* cols, uint
                     best_k = k;
                 }
             }
-    best_k.flags = saved.flags;
+    best_k.flags = (saved.flags & ~ZF_KCFG_GRAPH) | (transfer ? (best_k.flags & ZF_KCFG_GRAPH) : (saved.flags & ZF_KCFG_GRAPH));
     // Columns of one (scheme, dtype, bit-width bucket) class: the result is
     // kept for that class and the context's geometry stays automatic, so
     // later calls give every class its own; otherwise the context takes it.
@@ -1264,7 +1272,10 @@ extern "C" zf_status zf_tune(zf_ctx* ctx, const zf_compressed* const* cols, uint
         }
         ctx->tuned_gen++;
         ctx->kcfg = saved;
-        if (transfer) ctx->kcfg.stage_bytes = best_k.stage_bytes;
+        if (transfer) {
+            ctx->kcfg.stage_bytes = best_k.stage_bytes;
+            ctx->kcfg.flags = best_k.flags;
+        }
     } else {
         ctx->kcfg = best_k;
     }

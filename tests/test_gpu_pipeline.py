@@ -50,7 +50,7 @@ def test_graph_replay(columns, flags):
         g.close()
 
 
-@pytest.mark.parametrize("transfer,npts", [(False, 15), (True, 75)])
+@pytest.mark.parametrize("transfer,npts", [(False, 15), (True, 150)])
 def test_tune_visits_every_point_and_keeps_the_fastest(columns, transfer, npts):
     cols, hs = columns
     specs = [sp for x, s, cr in cols for sp in out_specs(x)]
@@ -60,12 +60,15 @@ def test_tune_visits_every_point_and_keeps_the_fastest(columns, transfer, npts):
         outs, caps = [b.data_ptr() for b in bufs], [b.numel() for b in bufs]
         pts, best = zf.zf_tune(g.ctx, hs, outs, caps, transfer=transfer, reps=2)
         assert len(pts) == npts
-        seen = {(p.kcfg.tile_rows, p.kcfg.threads, p.kcfg.stage_bytes) for p in pts}
+        seen = {(p.kcfg.tile_rows, p.kcfg.threads, p.kcfg.stage_bytes, p.kcfg.flags & zf.ZF_KCFG_GRAPH) for p in pts}
         assert len(seen) == npts
         fastest = min(pts, key=lambda p: p.ms)
         assert (best.tile_rows, best.threads) == (fastest.kcfg.tile_rows, fastest.kcfg.threads)
         if transfer:
+            # stage size and graph replay are searched too, the transfer timed as its caller sees it
             assert best.stage_bytes == fastest.kcfg.stage_bytes
+            assert best.flags & zf.ZF_KCFG_GRAPH == fastest.kcfg.flags & zf.ZF_KCFG_GRAPH
+            assert {p.kcfg.flags & zf.ZF_KCFG_GRAPH for p in pts} == {0, zf.ZF_KCFG_GRAPH}
         # the context now decodes with the chosen geometry, bit-exact
         for b in bufs:
             b.fill_(0)
