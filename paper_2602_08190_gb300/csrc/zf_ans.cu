@@ -41,7 +41,11 @@ struct AnsSmem {
 // may enter the buffer; a valid stream never takes them.
 // Eight int32 or four int64 rows leave as one 32-byte sector.  Returns true
 // if the stream is malformed: it must use exactly its bytes and end at x = L.
-template <class T>
+// SMALL (a chunk of at most four values): the symbol of a slot is found by
+// comparing it with the cumulative frequencies, held in registers with the
+// frequencies and values, so a row's dependent chain has no shared-memory
+// lookup (whose address is the previous row's state).
+template <class T, bool SMALL>
 __device__ __forceinline__ bool ans_stream(const AnsSmem& sm, const uint8_t* s2, uint32_t a0, uint32_t a1, T* dst,
                                            uint32_t n) {
     const unsigned long long* w8 = reinterpret_cast<const unsigned long long*>(s2);
@@ -72,12 +76,38 @@ __device__ __forceinline__ bool ans_stream(const AnsSmem& sm, const uint8_t* s2,
     bb <<= 32;
     nbits -= 32;
     const uint32_t* val32 = reinterpret_cast<const uint32_t*>(sm.val);
+    // SMALL: cumulative frequencies c1..c3 (M past the last symbol), frequencies and values
+    uint32_t c1 = 0, c2 = 0, c3 = 0, f0 = 0, f1 = 0, f2 = 0, f3 = 0;
+    T v0 = 0, v1 = 0, v2 = 0, v3 = 0;
+    if constexpr (SMALL) {
+        c1 = sm.cum[1];
+        c2 = c1 < zf::kAnsM ? sm.cum[2] : zf::kAnsM;
+        c3 = c2 < zf::kAnsM ? sm.cum[3] : zf::kAnsM;
+        const uint32_t c4 = c3 < zf::kAnsM ? sm.cum[4] : zf::kAnsM;
+        f0 = c1;
+        f1 = c2 - c1;
+        f2 = c3 - c2;
+        f3 = c4 - c3;
+        v0 = (T)sm.val[0];
+        v1 = c1 < zf::kAnsM ? (T)sm.val[1] : v0;
+        v2 = c2 < zf::kAnsM ? (T)sm.val[2] : v0;
+        v3 = c3 < zf::kAnsM ? (T)sm.val[3] : v0;
+    }
     auto step = [&]() -> T {
-        const uint32_t t = sm.slot[x & (zf::kAnsM - 1u)];
         T v;
-        if constexpr (sizeof(T) == 4) v = (T)val32[2 * (t >> 24)];   // the low word of the 64-bit pattern
-        else v = (T)sm.val[t >> 24];
-        x = ((t & 0xFFFu) + 1u) * (x >> zf::kAnsScale) + ((t >> 12) & 0xFFFu);
+        if constexpr (SMALL) {
+            const uint32_t slot = x & (zf::kAnsM - 1u);
+            const bool b1 = slot >= c1, b2 = slot >= c2, b3 = slot >= c3;
+            const uint32_t c = b3 ? c3 : b2 ? c2 : b1 ? c1 : 0u;
+            const uint32_t f = b3 ? f3 : b2 ? f2 : b1 ? f1 : f0;
+            v = b3 ? v3 : b2 ? v2 : b1 ? v1 : v0;
+            x = f * (x >> zf::kAnsScale) + slot - c;
+        } else {
+            const uint32_t t = sm.slot[x & (zf::kAnsM - 1u)];
+            if constexpr (sizeof(T) == 4) v = (T)val32[2 * (t >> 24)];   // the low word of the 64-bit pattern
+            else v = (T)sm.val[t >> 24];
+            x = ((t & 0xFFFu) + 1u) * (x >> zf::kAnsScale) + ((t >> 12) & 0xFFFu);
+        }
         const uint32_t s = (x < zf::kAnsL ? 8u : 0u) + (x < (zf::kAnsL >> 8) ? 8u : 0u);
         x = __funnelshift_l((uint32_t)(bb >> 32), x, s);
         bb <<= s;
@@ -174,8 +204,9 @@ __global__ void __launch_bounds__(kWarps * 32) ans_kernel(const ZfDevChunk* chun
                             : (unsigned long long)(uint32_t)__ldg(reinterpret_cast<const int32_t*>(c.blob + h.off[0]) + k);
     __syncthreads();
     // slot entries: thread t fills slots [t * 32, t * 32 + 32), walking the
-    // symbols from the one holding its first slot (binary search on cum)
-    {
+    // symbols from the one holding its first slot (binary search on cum);
+    // chunks of at most four values decode from the cumulative frequencies
+    if (nd > 4) {
         constexpr uint32_t per = zf::kAnsM / (kWarps * 32);
         const uint32_t first = tid * per;
         uint32_t lo = 0, hi = nd - 1;   // the last symbol whose cum is <= first
@@ -206,9 +237,11 @@ __global__ void __launch_bounds__(kWarps * 32) ans_kernel(const ZfDevChunk* chun
         if (a1 < a0 || a1 - a0 < 4u || a1 > h.len[2]) {
             bad = true;
         } else if (sz == 8) {
-            bad = ans_stream<int64_t>(sm, c.blob + h.off[2], a0, a1, reinterpret_cast<int64_t*>(c.dst) + r0, n);
+            bad = nd <= 4 ? ans_stream<int64_t, true>(sm, c.blob + h.off[2], a0, a1, reinterpret_cast<int64_t*>(c.dst) + r0, n)
+                          : ans_stream<int64_t, false>(sm, c.blob + h.off[2], a0, a1, reinterpret_cast<int64_t*>(c.dst) + r0, n);
         } else {
-            bad = ans_stream<int32_t>(sm, c.blob + h.off[2], a0, a1, reinterpret_cast<int32_t*>(c.dst) + r0, n);
+            bad = nd <= 4 ? ans_stream<int32_t, true>(sm, c.blob + h.off[2], a0, a1, reinterpret_cast<int32_t*>(c.dst) + r0, n)
+                          : ans_stream<int32_t, false>(sm, c.blob + h.off[2], a0, a1, reinterpret_cast<int32_t*>(c.dst) + r0, n);
         }
     }
     if (bad) zfd::report(err, ZF_ECORRUPT, c.chunk_id);

@@ -301,6 +301,10 @@ def test_ans_columns(gpu):
         (np.full(5000, 7, np.int64), 4096),
         (np.array([-2**31, 2**31 - 1] * 3001, np.int32), 2048),
         ((rng.geometric(0.05, 200003) % 256).astype(np.int32), 1 << 20),
+        # four values (the largest alphabet decoded from cumulative frequencies
+        # in registers, one of them rare) and five (the first with the slot table)
+        (np.array([-2**63, 2**63 - 1, 0, 77], np.int64)[rng.choice(4, 90001, p=[0.6, 0.3, 0.0995, 0.0005])], 32768),
+        (np.array([3, 1, 4, 1 << 30, -5], np.int32)[rng.integers(0, 5, 70001)], 16384),
     ]
     for x, cr in cases:
         for enc in ("library", "oracle"):
